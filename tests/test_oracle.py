@@ -1,0 +1,380 @@
+"""Pins of the FP64 oracle against facts fixed by the mathematics (no GPU).
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term,
+a wrong sign, a transposed operand, a swapped index, a wrong scalar) fails at
+least one of them.  None of them re-types the oracle's own loop.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import script as oscript
+
+ALPHA, BETA = 1.5, 1.2
+
+
+def U(shape, tid, seed=0):
+    return synth.uniform(shape, seed, tid).numpy().astype(np.float64)
+
+
+# ------------------------------------------------------------------ BiCGK
+
+@pytest.mark.parametrize("m,n", [(4, 4), (3, 5), (5, 3)])
+def test_bicgk_one_hot_pins_index_mapping(m, n):
+    """A = E_kl (one at row k, column l): q = p_l e_k and s = r_k e_l.
+    Every (k, l) pins one index mapping; a transposed operand fails."""
+    p = np.arange(1, n + 1, dtype=np.float64) * 1.25
+    r = np.arange(1, m + 1, dtype=np.float64) * -0.5
+    for k in range(m):
+        for l in range(n):
+            A = np.zeros((m, n)); A[k, l] = 1.0
+            q, s = oracle.bicgk(A, p, r)
+            qe = np.zeros(m); qe[k] = p[l]
+            se = np.zeros(n); se[l] = r[k]
+            assert np.array_equal(q, qe) and np.array_equal(s, se), (k, l)
+
+
+def test_bicgk_identity_bitwise():
+    n = 37
+    p, r = U((n,), 3), U((n,), 4)
+    q, s = oracle.bicgk(np.eye(n), p, r)
+    assert np.array_equal(q, p) and np.array_equal(s, r)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (31, 33), (33, 31), (64, 100)])
+def test_bicgk_rank_one_closed_form(m, n):
+    """A = u v^T: A p = u (v.p) and A^T r = v (u.r)."""
+    u, v = U((m,), 5), U((n,), 6)
+    p, r = U((n,), 3), U((m,), 4)
+    q, s = oracle.bicgk(np.outer(u, v), p, r)
+    np.testing.assert_allclose(q, u * float(np.sum(v * p)), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(s, v * float(np.sum(u * r)), rtol=1e-12, atol=1e-13)
+
+
+def test_bicgk_duality_invariant():
+    """r^T (A p) = (A^T r)^T p for any A, p, r."""
+    m, n = 57, 43
+    A, p, r = U((m, n), 1), U((n,), 3), U((m,), 4)
+    q, s = oracle.bicgk(A, p, r)
+    lhs, rhs = float(r @ q), float(s @ p)
+    assert abs(lhs - rhs) <= 1e-12 * (np.abs(A).sum())
+
+
+def test_bicgk_integer_exact():
+    """Integer inputs: every partial sum is an integer below 2^53, so the
+    result is exact; compare with integer arithmetic in Python ints."""
+    m, n = 9, 7
+    A = synth.integers((m, n), 0, 1).numpy().astype(np.int64)
+    p = synth.integers((n,), 0, 3).numpy().astype(np.int64)
+    r = synth.integers((m,), 0, 4).numpy().astype(np.int64)
+    q, s = oracle.bicgk(A.astype(np.float64), p, r)
+    for i in range(m):
+        assert q[i] == sum(int(A[i, j]) * int(p[j]) for j in range(n))
+    for j in range(n):
+        assert s[j] == sum(int(A[i, j]) * int(r[i]) for i in range(m))
+
+
+# ------------------------------------------------------------------ GEMVER
+
+def test_gemver_rank_one_closed_form():
+    """A = 0, u2 = v2 = 0: B = u1 v1^T, x = beta v1 (u1.y) + z,
+    w = alpha u1 (v1.x)."""
+    n = 23
+    u1, v1, y, z = U((n,), 5), U((n,), 6), U((n,), 4), U((n,), 9)
+    zero = np.zeros(n)
+    B, x, w = oracle.gemver(np.zeros((n, n)), u1, v1, zero, zero, y, z, ALPHA, BETA)
+    np.testing.assert_allclose(B, np.outer(u1, v1), rtol=0, atol=1e-15)
+    xe = BETA * v1 * float(u1 @ y) + z
+    np.testing.assert_allclose(x, xe, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(w, ALPHA * u1 * float(v1 @ xe), rtol=1e-12, atol=1e-13)
+
+
+def test_gemver_one_hot_updates_pin_indices():
+    """u1 = e_a, v1 = e_b (u2 = e_c, v2 = e_d): B = A + E_ab + E_cd."""
+    n = 5
+    A = U((n, n), 1)
+    y, z = U((n,), 4), U((n,), 9)
+    for a, b, c, d in [(0, 3, 4, 1), (2, 2, 1, 0)]:
+        e = np.eye(n)
+        B, x, w = oracle.gemver(A, e[a], e[b], e[c], e[d], y, z, ALPHA, BETA)
+        Be = A.copy(); Be[a, b] += 1; Be[c, d] += 1
+        assert np.array_equal(B, Be)
+        # x_j = beta * (column j of B) . y + z_j : pin with B = identity-like
+    Bi = np.zeros((n, n)); e = np.eye(n)
+    B, x, w = oracle.gemver(Bi, e[1], e[3], np.zeros(n), np.zeros(n), y, z, ALPHA, BETA)
+    xe = z.copy(); xe[3] += BETA * y[1]          # B^T y has y_1 at position 3
+    assert np.allclose(x, xe, rtol=0, atol=1e-15)
+    we = np.zeros(n); we[1] = ALPHA * xe[3]      # B x has x_3 at position 1
+    assert np.allclose(w, we, rtol=0, atol=1e-15)
+
+
+def test_gemver_invariant():
+    """y^T w / alpha = (x - z)^T x / beta, since both equal y^T B x."""
+    n = 31
+    args = [U((n, n), 1)] + [U((n,), t) for t in (5, 6, 7, 8, 4, 9)]
+    B, x, w = oracle.gemver(*args, ALPHA, BETA)
+    y, z = args[5], args[6]
+    lhs = float(y @ w) / ALPHA
+    rhs = float((x - z) @ x) / BETA
+    assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(lhs))
+
+
+# ------------------------------------------------------------------ GESUMMV
+
+def test_gesummv_special_cases():
+    m, n = 19, 26
+    A, x = U((m, n), 1), U((n,), 3)
+    y = oracle.gesummv(A, A, x, ALPHA, BETA)
+    np.testing.assert_allclose(y, (ALPHA + BETA) * (A @ x), rtol=1e-12, atol=1e-13)
+    k = 21
+    y = oracle.gesummv(np.eye(k), np.eye(k), U((k,), 3), ALPHA, BETA)
+    np.testing.assert_allclose(y, (ALPHA + BETA) * U((k,), 3), rtol=1e-15)
+    Ai = synth.integers((m, n), 0, 1).numpy().astype(np.float64)
+    xi = synth.integers((n,), 0, 3).numpy().astype(np.float64)
+    y = oracle.gesummv(Ai, -Ai, xi, 2.0, 2.0)
+    assert np.array_equal(y, np.zeros(m))
+    # alpha only sees A, beta only sees B: B = 0 gives alpha * A x
+    y = oracle.gesummv(Ai, np.zeros((m, n)), xi, 3.0, 7.0)
+    assert np.array_equal(y, 3.0 * (Ai @ xi))
+
+
+# ------------------------------------------------------------------ ATAX
+
+def _hadamard(n):
+    H = np.array([[1.0]])
+    while H.shape[0] < n:
+        H = np.block([[H, H], [H, -H]])
+    return H
+
+
+def test_atax_permutation_and_hadamard():
+    n = 16
+    x = synth.integers((n,), 0, 3).numpy().astype(np.float64)
+    P = np.eye(n)[np.roll(np.arange(n), 5)]
+    y, t = oracle.atax(P, x)
+    assert np.array_equal(y, x)
+    y, t = oracle.atax(_hadamard(n), x)
+    assert np.array_equal(y, n * x)
+
+
+def test_atax_invariant_and_rectangular():
+    m, n = 13, 29
+    A, x = U((m, n), 1), U((n,), 3)
+    y, t = oracle.atax(A, x)
+    assert abs(float(x @ y) - float(t @ t)) <= 1e-12 * max(1.0, float(t @ t))
+    # one-hot rectangular A = E_kl: A x = x_l e_k, A^T A x = x_l e_l
+    A = np.zeros((m, n)); A[4, 17] = 1.0
+    y, t = oracle.atax(A, x)
+    ye = np.zeros(n); ye[17] = x[17]
+    assert np.array_equal(y, ye)
+
+
+# ------------------------------------------------------------------ AXPYDOT
+
+def test_axpydot_cases():
+    n = 1000
+    w, v, u = U((n,), 10), U((n,), 11), U((n,), 12)
+    z, r = oracle.axpydot(w, np.zeros(n), u, ALPHA)
+    assert np.array_equal(z, w)
+    z, r = oracle.axpydot(w, v, np.eye(n)[17], ALPHA)
+    assert r == z[17]
+    assert z[17] == w[17] - ALPHA * v[17]
+    z, r = oracle.axpydot(w, v, u, ALPHA)
+    lin = float(np.sum(w * u)) - ALPHA * float(np.sum(v * u))
+    assert abs(r - lin) <= 1e-12 * float(np.sum(np.abs(z * u)))
+
+
+def test_waxpby_cases():
+    n = 333
+    x, y = U((n,), 3), U((n,), 4)
+    assert np.array_equal(oracle.waxpby(1.0, x, 0.0, y), x)
+    assert np.array_equal(oracle.waxpby(ALPHA, x, ALPHA, -x), np.zeros(n))
+    w = oracle.waxpby(2.0, np.ones(n), 0.5, np.full(n, 4.0))
+    assert np.array_equal(w, np.full(n, 4.0))
+    w = oracle.waxpby(0.0, x, 1.0, y)
+    assert np.array_equal(w, y)
+
+
+# ------------------------------------------------------------------ scripts
+
+def test_script_matches_sequences():
+    n = 12
+    A = U((n, n), 1)
+    env = {"A": A, "p": U((n,), 3), "r": U((n,), 4)}
+    E = oscript.run([("GEMV", ["q"], ["A", "p"], [1, 0]),
+                     ("GEMVT", ["s"], ["A", "r"], [1, 0])], env)
+    q, s = oracle.bicgk(A, env["p"], env["r"])
+    assert np.array_equal(E["q"], q) and np.array_equal(E["s"], s)
+    # GEMVER as a script of GER, GER, GEMVT, GEMV
+    vs = {k: U((n,), t) for k, t in [("u1", 5), ("v1", 6), ("u2", 7), ("v2", 8), ("y", 4), ("z", 9)]}
+    env = {"A": A, **vs}
+    E = oscript.run([("GER", ["B"], ["A", "u1", "v1"], [1]),
+                     ("GER", ["B"], ["B", "u2", "v2"], [1]),
+                     ("GEMVT", ["x"], ["B", "y", "z"], [BETA, 1]),
+                     ("GEMV", ["w"], ["B", "x"], [ALPHA, 0])], env)
+    B, x, w = oracle.gemver(A, vs["u1"], vs["v1"], vs["u2"], vs["v2"], vs["y"], vs["z"], ALPHA, BETA)
+    np.testing.assert_allclose(E["B"], B, rtol=0, atol=4e-16)
+    np.testing.assert_allclose(E["x"], x, rtol=1e-14)
+    np.testing.assert_allclose(E["w"], w, rtol=1e-13)
+
+
+def test_script_in_place_semantics():
+    """AXPY in place: y <- a x + y applied twice equals y + 2 a x."""
+    n = 8
+    x, y = U((n,), 3), U((n,), 4)
+    E = oscript.run([("AXPBY", ["y"], ["x", "y"], [0.5, 1.0]),
+                     ("AXPBY", ["y"], ["x", "y"], [0.5, 1.0]),
+                     ("DOT", ["d"], ["y", "x"], [])], {"x": x, "y": y})
+    np.testing.assert_allclose(E["y"], y + x, rtol=1e-15)
+    assert abs(E["d"] - float((y + x) @ x)) < 1e-12
+
+
+# ------------------------------------------------------------------ low precision
+
+def test_bf16_codes_match_round_to_nearest_even():
+    """bf16 RNE against torch's own float32 -> bfloat16 conversion."""
+    vals = torch.cat([synth.uniform((4000,), 1, 1), torch.tensor([
+        1.0, -1.0, 1.00390625, 1.01171875, 1.0 + 2 ** -8 + 2 ** -9, 0.0, 2 ** -126, 3.0e-5])])
+    ref = vals.to(torch.bfloat16).view(torch.int16).numpy().astype(np.uint16)
+    got = np.array([oracle.bf16_code(float(v)) for v in vals], dtype=np.uint16)
+    assert np.array_equal(got, ref)
+    # ties: 1 + 2^-8 is halfway between 1 and 1 + 2^-7 -> even (1.0)
+    assert oracle.bf16_code(1.0 + 2 ** -8) == 0x3F80
+    assert oracle.bf16_code(1.0 + 3 * 2 ** -8) == 0x3F82
+
+
+def test_e4m3_format_definition():
+    """Values fixed by the E4M3 definition (bias 7, 3 mantissa bits, max 448)."""
+    assert oracle.e4m3_code(448.0) == 0x7E
+    assert oracle.e4m3_code(1000.0) == 0x7E            # saturates
+    assert oracle.e4m3_code(-1000.0) == 0xFE
+    assert oracle.e4m3_code(1.0) == 0x38
+    assert oracle.e4m3_code(0.5) == 0x30
+    assert oracle.e4m3_code(2.0 ** -6) == 0x08          # smallest normal
+    assert oracle.e4m3_code(2.0 ** -9) == 0x01          # smallest subnormal
+    assert oracle.e4m3_code(2.0 ** -10) == 0x00         # tie to even -> 0
+    assert oracle.e4m3_code(1.0625) == 0x38             # tie 1 | 1.125 -> even 1
+    assert oracle.e4m3_code(1.1875) == 0x3A             # tie 1.125 | 1.25 -> even 1.25
+    for c in range(0, 0x7F):
+        v = oracle.e4m3_value(c)
+        assert oracle.e4m3_code(v) == c                 # decode/encode round trip
+
+
+def test_e4m3_matches_torch_in_range():
+    vals = synth.uniform((5000,), 2, 1) * 460.0
+    ref = vals.to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    got = np.array([oracle.e4m3_code(float(v)) for v in vals], dtype=np.uint8)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("fmt", [oracle.FMT_BF16, oracle.FMT_E4M3])
+def test_quantize_exact_rows_are_lossless(fmt):
+    """Rows of powers of two (in range) quantise and dequantise exactly."""
+    m, n = 6, 20
+    e = synth.integers((m, n), 0, 1, lo=-6, hi=0).numpy()
+    sgn = np.where(synth.integers((m, n), 0, 2, lo=0, hi=1).numpy() > 0, 1.0, -1.0)
+    A = (sgn * np.exp2(e)).astype(np.float32)
+    # row maximum chosen so that s_i = amax / QMAX is a power of two:
+    # 1 for BF16 (QMAX 1), 1.75 = 448 * 2^-8 for E4M3
+    A[:, 0] = 1.0 if fmt == oracle.FMT_BF16 else 1.75
+    A[3, :] = 0.0                                      # an all-zero row
+    codes, scale = oracle.quantize_rows(A, fmt)
+    assert scale[3] == 1.0
+    Ahat = oracle.dequantize_rows(codes, scale, fmt)
+    assert np.array_equal(Ahat, A.astype(np.float64))
+
+
+@pytest.mark.parametrize("fmt,rel", [(oracle.FMT_BF16, 2 ** -8), (oracle.FMT_E4M3, 2 ** -4)])
+def test_quantize_error_bound(fmt, rel):
+    """|Ahat - A| <= half a unit of the format's precision relative to
+    max(|A_ij|, smallest normal * s_i)."""
+    m, n = 16, 64
+    A = synth.uniform((m, n), 0, 1).numpy()
+    codes, scale = oracle.quantize_rows(A, fmt)
+    Ahat = oracle.dequantize_rows(codes, scale, fmt)
+    floor = (2.0 ** -6 if fmt == oracle.FMT_E4M3 else 2.0 ** -126) * scale[:, None].astype(np.float64)
+    bound = rel * np.maximum(np.abs(A.astype(np.float64)), floor) * 1.0001
+    assert np.all(np.abs(Ahat - A) <= bound)
+    # the largest element of each row maps to +-QMAX
+    qmax = 448.0 if fmt == oracle.FMT_E4M3 else 1.0
+    amax = np.abs(A).max(axis=1)
+    assert np.allclose(scale, (amax / np.float32(qmax)).astype(np.float32), rtol=0)
+
+
+# ------------------------------------------------------------------ MLP
+
+def _mlp_setup(d=7, H=5, B=11):
+    from oracle import mlp
+    P = mlp.init_params(d, H, synth.uniform((mlp.n_params(d, H),), 0, synth.TID["mlp"]).numpy())
+    for k in P:                      # nonzero biases to exercise every term
+        if k.startswith("b"):
+            P[k] = synth.uniform(P[k].shape, 1, synth.TID["mlp"]).numpy().astype(np.float64) * 0.3
+    X = synth.uniform((B, d), 2, synth.TID["mlp"]).numpy()
+    y = synth.uniform((B,), 3, synth.TID["mlp"]).numpy()
+    return mlp, P, X, y
+
+
+def test_mlp_gradient_central_differences():
+    mlp, P, X, y = _mlp_setup()
+    L, G = mlp.grad(P, X, y)
+    h = 1e-6
+    for k in P:
+        flat = P[k].reshape(-1)
+        for idx in range(flat.size):
+            old = flat[idx]
+            flat[idx] = old + h; lp = mlp.loss(P, X, y)
+            flat[idx] = old - h; lm = mlp.loss(P, X, y)
+            flat[idx] = old
+            num = (lp - lm) / (2 * h)
+            ana = G[k].reshape(-1)[idx]
+            assert abs(num - ana) <= 1e-6 * max(1.0, abs(num)), (k, idx, num, ana)
+
+
+def test_mlp_linear_region_closed_form():
+    """With all pre-activations positive the net is affine:
+    f = W3 W2 W1 x + W3 W2 b1 + W3 b2 + b3."""
+    from oracle import mlp
+    d, H = 3, 4
+    P = {"W1": np.full((H, d), 0.1), "b1": np.ones(H), "W2": np.full((H, H), 0.2),
+         "b2": np.ones(H), "W3": np.full((1, H), 0.5), "b3": np.array([0.25])}
+    X = np.abs(synth.uniform((6, d), 0, 1).numpy())
+    f, _ = mlp.forward(P, X)
+    fe = (X @ (P["W3"] @ P["W2"] @ P["W1"]).T)[:, 0] + (P["W3"] @ P["W2"] @ P["b1"])[0] \
+        + (P["W3"] @ P["b2"])[0] + P["b3"][0]
+    np.testing.assert_allclose(f, fe, rtol=1e-13)
+
+
+def test_adam_first_step_closed_form():
+    """At t = 1 bias correction gives mhat = g, vhat = g^2, so the step is
+    -lr * g / (|g| + eps)."""
+    mlp, P, X, y = _mlp_setup()
+    _, G = mlp.grad(P, X, y)
+    P0 = {k: v.copy() for k, v in P.items()}
+    M = {k: np.zeros_like(v) for k, v in P.items()}
+    V = {k: np.zeros_like(v) for k, v in P.items()}
+    mlp.adam_step(P, G, M, V, 1, lr=0.01)
+    for k in P:
+        np.testing.assert_allclose(P[k] - P0[k], -0.01 * G[k] / (np.abs(G[k]) + 1e-8),
+                                   rtol=1e-9, atol=1e-15)
+
+
+# ------------------------------------------------------------------ generator
+
+def test_generator_grid_range_and_subsets():
+    v = synth.uniform((100000,), 0, 1)
+    assert float(v.min()) >= -1.0 and float(v.max()) < 1.0
+    k = (v.double() + 1.0) * 2 ** 23
+    assert torch.equal(k, torch.round(k))
+    m, n = 37, 53
+    A = synth.uniform((m, n), 0, 1)
+    assert torch.equal(synth.matrix_rows(m, n, [0, 5, 36], 0, 1), A[[0, 5, 36]])
+    assert torch.equal(synth.matrix_cols(m, n, [0, 52], 0, 1), A[:, [0, 52]].T)
+    assert not torch.equal(synth.uniform((50,), 0, 1), synth.uniform((50,), 0, 2))
+    assert not torch.equal(synth.uniform((50,), 0, 1), synth.uniform((50,), 1, 1))
+    s = synth.log_uniform_int(32, 2048, 0, synth.TID["sizes"], 4096)
+    assert int(s.min()) >= 32 and int(s.max()) <= 2048
+    ls = torch.log(s.double())
+    assert abs(float(ls.mean()) - (np.log(32) + np.log(2048)) / 2) < 0.1
