@@ -1,0 +1,588 @@
+"""Benchmark of the fused BLAS-1/BLAS-2 sequence suite on one or more GPUs.
+
+One step = one pass of every fused sequence of the at-scale FP32 suite:
+BiCGK 16384 x 16384, GEMVER n = 8192, GESUMMV n = 8192, ATAX 8192 x 8192,
+AXPYDOT and WAXPBY n = 2^26 (alpha = 1.5, beta = 1.2, entries uniform in
+[-1, 1) from the seeded generator).  Every input is larger than the 129 MB L2
+or a vector that a fused kernel keeps on chip, so each step streams from HBM.
+
+Reported value: algorithmic bytes of the suite (bytes each sequence must move
+at least once: matrices read/written once, vectors once) / device time, in
+GB/s.  Beside it: per-sequence GB/s and fraction of the measured HBM copy
+bandwidth, the unfused per-call kernel chain on the same GPU and its speedup,
+the dominant kernel's roofline, an end-to-end number through host buffers,
+and the FP64 CPU oracle's throughput on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU runs (torchrun) are independent replicas: the suite does not shard
+into an exchange; every rank runs its own copy and the value is the sum of
+bytes over ranks divided by the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+ALPHA, BETA = 1.5, 1.2
+METRIC = "fused-sequence HBM GB/s, % of GB300 peak, speedup vs unfused chain"
+WORKLOAD = ("FP32 sequence suite at scale: GEMVER n=8192, GESUMMV n=8192, ATAX 8192x8192, "
+            "BiCGK 16384x16384, AXPYDOT and WAXPBY n=2^26; entries uniform[-1,1), seed 0")
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6800.0
+
+FULL = dict(bicgk=(16384, 16384), gemver=8192, gesummv=8192, atax=(8192, 8192), axpydot=1 << 26,
+            waxpby=1 << 26)
+SMALL = dict(bicgk=(2048, 2048), gemver=1024, gesummv=1024, atax=(1024, 1024), axpydot=1 << 20,
+             waxpby=1 << 20)
+
+
+# ---------------------------------------------------------------- byte model
+
+def algorithmic_bytes(seq: str, size) -> int:
+    """Bytes the sequence must move at least once (FP32), per the counting of
+    the paper's Section 4.2: only data really transferred to or from memory."""
+    f = 4
+    if seq == "bicgk":
+        m, n = size
+        return f * (m * n + 2 * (m + n))             # A; p, r in; q, s out
+    if seq == "gemver":
+        n = size
+        return f * (3 * n * n + 9 * n)               # A read, B written, B read; 9 vectors
+    if seq == "gesummv":
+        n = size
+        return f * (2 * n * n + 2 * n)               # A, B read; x in; y out
+    if seq == "atax":
+        m, n = size
+        return f * (m * n + 2 * n)                   # A read once; x in; y out
+    if seq == "axpydot":
+        return f * (4 * size + 1)                    # w, v, u in; z, r out
+    if seq == "waxpby":
+        return f * 3 * size                          # x, y in; w out
+    raise KeyError(seq)
+
+
+def unfused_bytes(seq: str, size) -> int:
+    """Bytes of the one-kernel-per-call chain (for the ideal speedup)."""
+    f = 4
+    if seq == "bicgk":
+        m, n = size
+        return f * (2 * m * n + 2 * (m + n))
+    if seq == "gemver":
+        n = size
+        return f * (6 * n * n + 14 * n)
+    if seq == "gesummv":
+        n = size
+        return f * (2 * n * n + 7 * n)
+    if seq == "atax":
+        m, n = size
+        return f * (2 * m * n + 2 * n + 2 * m)
+    if seq == "axpydot":
+        return f * (5 * size)
+    if seq == "waxpby":
+        return f * 5 * size
+    raise KeyError(seq)
+
+
+def algorithmic_flops(seq: str, size) -> int:
+    if seq == "bicgk":
+        m, n = size
+        return 4 * m * n
+    if seq == "gemver":
+        return 8 * size * size
+    if seq == "gesummv":
+        return 4 * size * size
+    if seq == "atax":
+        m, n = size
+        return 4 * m * n
+    if seq == "axpydot":
+        return 4 * size
+    if seq == "waxpby":
+        return 3 * size
+    raise KeyError(seq)
+
+
+# ---------------------------------------------------------------- suite
+
+class Suite:
+    """Device-resident inputs and outputs of every sequence, plus the calls."""
+
+    def __init__(self, kf, sizes, device, seed=0):
+        self.kf = kf
+        self.sizes = sizes
+        d = device
+        g = lambda shape, tid: synth.uniform(shape, seed, tid, device=d)  # noqa: E731
+        m, n = sizes["bicgk"]
+        self.bicgk = dict(A=g((m, n), synth.TID["A"]), p=g((n,), synth.TID["p"]), r=g((m,), synth.TID["r"]),
+                          q=torch.empty(m, device=d), s=torch.empty(n, device=d),
+                          ws=kf.workspace(kf.KF_SEQ_BICGK, m, n))
+        n = sizes["gemver"]
+        self.gemver = dict(A=g((n, n), synth.TID["A"]), **{k: g((n,), synth.TID[k]) for k in
+                                                         ("u1", "v1", "u2", "v2", "y", "z")},
+                           B=torch.empty(n, n, device=d), x=torch.empty(n, device=d),
+                           w=torch.empty(n, device=d), t=torch.empty(n, device=d),
+                           ws=kf.workspace(kf.KF_SEQ_GEMVER, n, n))
+        n = sizes["gesummv"]
+        self.gesummv = dict(A=g((n, n), synth.TID["A"]), B=g((n, n), synth.TID["B"]), x=g((n,), synth.TID["x"]),
+                            y=torch.empty(n, device=d), t1=torch.empty(n, device=d),
+                            t2=torch.empty(n, device=d), ws=kf.workspace(kf.KF_SEQ_GESUMMV, n, n))
+        m, n = sizes["atax"]
+        self.atax = dict(A=g((m, n), synth.TID["A"]), x=g((n,), synth.TID["x"]), y=torch.empty(n, device=d),
+                         t=torch.empty(m, device=d), ws=kf.workspace(kf.KF_SEQ_ATAX, m, n))
+        n = sizes["axpydot"]
+        self.axpydot = dict(w=g((n,), synth.TID["w"]), v=g((n,), synth.TID["v"]), u=g((n,), synth.TID["u"]),
+                            z=torch.empty(n, device=d), r=torch.empty(1, device=d),
+                            ws=kf.workspace(kf.KF_SEQ_AXPYDOT, 1, n))
+        n = sizes["waxpby"]
+        self.waxpby = dict(x=g((n,), synth.TID["x"]), y=g((n,), synth.TID["y"]), w=torch.empty(n, device=d),
+                           t=torch.empty(n, device=d))
+        self.mat_ws = kf.workspace(kf.KF_SEQ_BICGK, 16384, 16384)
+
+    # fused: the kernels the library emits for each canonical script
+    def fused(self, seq, st):
+        kf = self.kf
+        if seq == "bicgk":
+            b = self.bicgk
+            kf.kf_bicgk(b["A"], b["p"], b["r"], b["q"], b["s"], b["ws"], stream=st)
+        elif seq == "gemver":
+            b = self.gemver
+            kf.kf_gemver(b["A"], b["u1"], b["v1"], b["u2"], b["v2"], b["y"], b["z"], ALPHA, BETA,
+                         b["B"], b["x"], b["w"], b["ws"], stream=st)
+        elif seq == "gesummv":
+            b = self.gesummv
+            kf.kf_gesummv(b["A"], b["B"], b["x"], ALPHA, BETA, b["y"], b["ws"], stream=st)
+        elif seq == "atax":
+            b = self.atax
+            kf.kf_atax(b["A"], b["x"], b["y"], b["ws"], stream=st)
+        elif seq == "axpydot":
+            b = self.axpydot
+            kf.kf_axpydot(b["w"], b["v"], b["u"], ALPHA, b["z"], b["r"], b["ws"], stream=st)
+        elif seq == "waxpby":
+            b = self.waxpby
+            kf.kf_waxpby(ALPHA, b["x"], BETA, b["y"], b["w"], stream=st)
+
+    # unfused: one out-of-place kernel per call of the canonical script
+    def unfused(self, seq, st):
+        kf = self.kf
+        W = self.mat_ws
+        if seq == "bicgk":
+            b = self.bicgk
+            kf.kf_gemv(b["A"], b["p"], b["q"], W, stream=st)
+            kf.kf_gemvt(b["A"], b["r"], b["s"], W, stream=st)
+        elif seq == "gemver":
+            b = self.gemver
+            kf.kf_ger(b["A"], b["u1"], b["v1"], b["B"], stream=st)
+            kf.kf_ger(b["B"], b["u2"], b["v2"], b["B"], stream=st)
+            kf.kf_gemvt(b["B"], b["y"], b["t"], W, stream=st)
+            kf.kf_axpby(BETA, b["t"], 1.0, b["z"], b["x"], stream=st)
+            kf.kf_gemv(b["B"], b["x"], b["w"], W, alpha=ALPHA, stream=st)
+        elif seq == "gesummv":
+            b = self.gesummv
+            kf.kf_gemv(b["A"], b["x"], b["t1"], W, alpha=ALPHA, stream=st)
+            kf.kf_gemv(b["B"], b["x"], b["t2"], W, alpha=BETA, stream=st)
+            kf.kf_axpby(1.0, b["t1"], 1.0, b["t2"], b["y"], stream=st)
+        elif seq == "atax":
+            b = self.atax
+            kf.kf_gemv(b["A"], b["x"], b["t"], W, stream=st)
+            kf.kf_gemvt(b["A"], b["t"], b["y"], W, stream=st)
+        elif seq == "axpydot":
+            b = self.axpydot
+            kf.kf_axpby(1.0, b["w"], -ALPHA, b["v"], b["z"], stream=st)
+            kf.kf_dot(b["z"], b["u"], b["r"], b["ws"], stream=st)
+        elif seq == "waxpby":
+            b = self.waxpby
+            kf.kf_scal(ALPHA, b["x"], b["t"], stream=st)
+            kf.kf_axpby(BETA, b["y"], 1.0, b["t"], b["w"], stream=st)
+
+    FUSED_LAUNCHES = dict(bicgk=1, gemver=2, gesummv=1, atax=2, axpydot=1, waxpby=1)
+
+    def inputs(self, seq):
+        d = getattr(self, seq)
+        keys = dict(bicgk=["A", "p", "r"], gemver=["A", "u1", "v1", "u2", "v2", "y", "z"],
+                    gesummv=["A", "B", "x"], atax=["A", "x"], axpydot=["w", "v", "u"], waxpby=["x", "y"])[seq]
+        return [d[k] for k in keys]
+
+    def outputs(self, seq):
+        d = getattr(self, seq)
+        keys = dict(bicgk=["q", "s"], gemver=["B", "x", "w"], gesummv=["y"], atax=["y"],
+                    axpydot=["z", "r"], waxpby=["w"])[seq]
+        return [d[k] for k in keys]
+
+
+SEQS = ["bicgk", "gemver", "gesummv", "atax", "axpydot", "waxpby"]
+
+
+# ---------------------------------------------------------------- helpers
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("matprog.cu", "kf_device.cuh", "kf_internal.h"):
+        with open(os.path.join(ROOT, "paper_1305_1183_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the BiCGK matrix pass from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "matprog_bicgk_16384.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    mt = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
+    md = re.search(r"kernel_source_digest:\s*([0-9a-f]+)", txt)
+    if not mt or not md or md.group(1) != kernel_digest():
+        return None
+    return int(mt.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 100 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- timing
+
+def time_suite(suite, mode, steps, warmup, st, seqs):
+    """Warm up, then time `steps` passes; per-sequence CUDA events on `st`."""
+    call = suite.fused if mode == "fused" else suite.unfused
+    with torch.cuda.stream(st):
+        for _ in range(warmup):
+            for s in seqs:
+                call(s, st)
+    st.synchronize()
+    ev = {s: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)] for s in seqs}
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        t0.record(st)
+        for k in range(steps):
+            for s in seqs:
+                ev[s][k][0].record(st)
+                call(s, st)
+                ev[s][k][1].record(st)
+        t1.record(st)
+    st.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    per = {s: float(np.mean([a.elapsed_time(b) for a, b in ev[s]])) for s in seqs}
+    return total_ms, per
+
+
+def time_e2e(suite, steps, warmup, st, seqs):
+    """Same metric through the public API from pinned host buffers: every step
+    copies the inputs host->device, runs the fused suite and reads the results
+    back device->host."""
+    hin = {s: [t.detach().cpu().pin_memory() for t in suite.inputs(s)] for s in seqs}
+    hout = {s: [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in suite.outputs(s)] for s in seqs}
+    h2d = sum(t.numel() * t.element_size() for s in seqs for t in hin[s])
+    d2h = sum(t.numel() * t.element_size() for s in seqs for t in hout[s])
+
+    def one():
+        for s in seqs:
+            for dst, src in zip(suite.inputs(s), hin[s]):
+                dst.copy_(src, non_blocking=True)
+            suite.fused(s, st)
+            for dst, src in zip(hout[s], suite.outputs(s)):
+                dst.copy_(src, non_blocking=True)
+
+    with torch.cuda.stream(st):
+        for _ in range(warmup):
+            one()
+    st.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        a.record(st)
+        for _ in range(steps):
+            one()
+        b.record(st)
+    st.synchronize()
+    return a.elapsed_time(b), h2d, d2h
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(sizes, frac_rows: int):
+    """One pass of the FP64 oracle over a row band (1/frac_rows of every
+    matrix) and a prefix of every vector.  Returns (seconds, algorithmic bytes)."""
+    import oracle
+    t = 0.0
+    nbytes = 0
+    m, n = sizes["bicgk"]
+    mr = max(1, m // frac_rows)
+    A = synth.uniform((mr, n), 0, synth.TID["A"]).numpy()
+    p = synth.uniform((n,), 0, synth.TID["p"]).numpy()
+    r = synth.uniform((m,), 0, synth.TID["r"]).numpy()[:mr]
+    c = time.perf_counter(); oracle.bicgk(A, p, r); t += time.perf_counter() - c
+    nbytes += algorithmic_bytes("bicgk", (mr, n))
+    n = sizes["gemver"]
+    nr = max(1, n // max(1, int(np.sqrt(frac_rows))))
+    A = synth.uniform((nr, nr), 0, synth.TID["A"]).numpy()
+    vs = [synth.uniform((nr,), 0, synth.TID[k]).numpy() for k in ("u1", "v1", "u2", "v2", "y", "z")]
+    c = time.perf_counter(); oracle.gemver(A, *vs, ALPHA, BETA); t += time.perf_counter() - c
+    nbytes += algorithmic_bytes("gemver", nr)
+    n = sizes["gesummv"]
+    mr = max(1, n // frac_rows)
+    A = synth.uniform((mr, n), 0, synth.TID["A"]).numpy()
+    B = synth.uniform((mr, n), 0, synth.TID["B"]).numpy()
+    x = synth.uniform((n,), 0, synth.TID["x"]).numpy()
+    c = time.perf_counter(); oracle.gesummv(A, B, x, ALPHA, BETA); t += time.perf_counter() - c
+    nbytes += 4 * (2 * mr * n + n + mr)
+    m, n = sizes["atax"]
+    mr = max(1, m // frac_rows)
+    A = synth.uniform((mr, n), 0, synth.TID["A"]).numpy()
+    x = synth.uniform((n,), 0, synth.TID["x"]).numpy()
+    c = time.perf_counter(); oracle.atax(A, x); t += time.perf_counter() - c
+    nbytes += algorithmic_bytes("atax", (mr, n))
+    nv = max(4, sizes["axpydot"] // frac_rows)
+    w, v, u = (synth.uniform((nv,), 0, synth.TID[k]).numpy() for k in ("w", "v", "u"))
+    c = time.perf_counter(); oracle.axpydot(w, v, u, ALPHA); t += time.perf_counter() - c
+    nbytes += algorithmic_bytes("axpydot", nv)
+    c = time.perf_counter(); oracle.waxpby(ALPHA, w, BETA, v); t += time.perf_counter() - c
+    nbytes += algorithmic_bytes("waxpby", nv)
+    return t, nbytes
+
+
+def cpu_baseline(sizes, budget_s=12.0, frac_rows=16):
+    """FP64 oracle throughput on repeated 1/frac_rows samples, about budget_s of CPU time."""
+    import oracle
+    oracle.build()
+    t_total, b_total, passes = 0.0, 0, 0
+    while t_total < budget_s and passes < 200:
+        t, b = oracle_sample(sizes, frac_rows)
+        t_total += t
+        b_total += b
+        passes += 1
+    return {"value": b_total / t_total / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{passes} pass(es) of the FP64 C oracle (single thread) over a 1/{frac_rows} "
+                       f"row band of every matrix and a 1/{frac_rows} prefix of every vector "
+                       f"(GEMVER: a {max(1, sizes['gemver'] // int(np.sqrt(frac_rows)))}^2 leading block); "
+                       f"{b_total / 1e9:.2f} GB of algorithmic traffic in {t_total:.1f} s; "
+                       f"host has {os.cpu_count()} cores")}
+
+
+# ---------------------------------------------------------------- main
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    sizes = SMALL if args.small else FULL
+    import oracle
+    oracle.build()
+    frac = 64
+    for _ in range(args.warmup):
+        oracle_sample(sizes, frac)
+    t, b = 0.0, 0
+    for _ in range(args.steps):
+        dt, db = oracle_sample(sizes, frac)
+        t += dt
+        b += db
+    v = b / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded splitmix64 uniform[-1,1))",
+        "config": {"workload": WORKLOAD, "sample": f"1/{frac} row band per step"},
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: the FP64 C oracle over a 1/{frac} row band of every matrix "
+                                   f"and a 1/{frac} prefix of every vector; single thread"},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kf", choices=["kf", "reference"])
+    ap.add_argument("--small", action="store_true", help="small sizes (quick check)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-unfused", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 0 and args.steps >= 1
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    # the CPU baseline runs before any CUDA work (no process forked later)
+    cpu = None
+    sizes = SMALL if args.small else FULL
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sizes)
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1305_1183_gb300 import _build, kf
+    _build.build()
+    kf.lib()
+
+    suite = Suite(kf, sizes, torch.device("cuda", local))
+    st = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    total_ms, per = time_suite(suite, "fused", args.steps, args.warmup, st, SEQS)
+    barrier()
+    clk = clocks.stop()
+
+    unf_total, unf_per = None, {}
+    if not args.no_unfused:
+        unf_total, unf_per = time_suite(suite, "unfused", args.steps, args.warmup, st, SEQS)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms, h2d, d2h = time_e2e(suite, max(1, min(args.steps, 5)), 1, st, SEQS)
+        e2e_steps = max(1, min(args.steps, 5))
+
+    step_bytes = sum(algorithmic_bytes(s, sizes[s]) for s in SEQS)
+    t_max = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_step = t_max / args.steps
+    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    peak, peak_kind = hbm_peak()
+
+    seqinfo = {}
+    for s in SEQS:
+        b = algorithmic_bytes(s, sizes[s])
+        g = b / (per[s] * 1e-3) / 1e9
+        d = {"ms": per[s], "gbs": g, "frac": g / peak, "frac_nominal": g / NOMINAL_HBM_GBS,
+             "gflops": algorithmic_flops(s, sizes[s]) / (per[s] * 1e-3) / 1e9,
+             "ideal_speedup": unfused_bytes(s, sizes[s]) / b}
+        if s in unf_per:
+            d["unfused_ms"] = unf_per[s]
+            d["unfused_gbs_algorithmic"] = b / (unf_per[s] * 1e-3) / 1e9
+            d["speedup_vs_unfused"] = unf_per[s] / per[s]
+        seqinfo[s] = d
+
+    dom = "bicgk"
+    dom_bytes = algorithmic_bytes(dom, sizes[dom])
+    achieved = dom_bytes / (per[dom] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": committed_traffic() if not args.small else None,
+            "kernel": "matprog_kernel (BiCGK q=Ap, s=A^T r, one pass over A)",
+            "algorithmic_bytes_per_launch": dom_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_kind == "measured" else "fallback 6.8 TB/s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded splitmix64 uniform[-1,1), seed 0)",
+        "config": {"workload": WORKLOAD if not args.small else "small suite (quick check)",
+                   "l2": "inputs larger than L2 (every matrix / long vector exceeds 129 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "alpha": ALPHA, "beta": BETA},
+        "frac_of_peak": value / peak, "frac_of_nominal_8TBs": value / NOMINAL_HBM_GBS,
+        "peak_hbm_gbs": peak, "peak_kind": peak_kind,
+        "speedup_vs_unfused": (unf_total / total_ms) if unf_total else None,
+        "sequences": seqinfo,
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": args.steps * sum(Suite.FUSED_LAUNCHES[s] for s in SEQS),
+    }
+    if not args.no_e2e:
+        line["e2e"] = {"value": world * step_bytes / (e2e_ms / e2e_steps * 1e-3) / 1e9, "unit": "GB/s",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": e2e_ms / e2e_steps}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

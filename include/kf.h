@@ -1,0 +1,216 @@
+/*
+ * kf.h -- C ABI of libkf: fused BLAS-1/BLAS-2 sequences on NVIDIA GB300 (sm_103a).
+ *
+ * The library follows the kernel-fusion method of Filipovic, Madzin, Fousek
+ * and Matyska, "Optimizing CUDA Code By Kernel Fusion -- Application on
+ * BLAS": sequences of memory-bound map / reduce / nested map-reduce calls
+ * (Section 3.2) are fused so that data shared between calls is read from
+ * global memory once.
+ *
+ * Conventions for every entry point
+ *   - Matrices are row major; element (i, j) of an m x n matrix A with
+ *     leading dimension lda (elements, lda >= n) is A[i * lda + j].
+ *   - "Ap" has length m and "A^T r" length n.  (Algorithm 3 of Section 3.4
+ *     indexes p, s by column tiles and q, r by row tiles.)
+ *   - All vector/matrix pointers are DEVICE pointers owned by the caller;
+ *     the library never allocates, frees or retains them.  16-byte aligned
+ *     pointers (and leading dimensions that keep rows 16-byte aligned) take
+ *     the vectorised path; others take an element-wise path with the same
+ *     results.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls only enqueue work; they do not synchronise, except the
+ *     ones documented as synchronous (status/autotune/empirical search).
+ *   - `ws` is caller-owned device workspace of at least the size reported by
+ *     kf_workspace_size() for the same call and shape.  It must be zero-filled
+ *     before its first use (kf_workspace_init does that); every call leaves
+ *     its completion counters at zero again, so the same workspace can be
+ *     reused for later calls on the same stream.  Calls that share a
+ *     workspace must not run concurrently.
+ *   - Results are deterministic: cross-block reductions are finished by the
+ *     last block to arrive in a fixed order (Section 3.2.2, option (ii)), not
+ *     by floating-point atomics.
+ *   - Outputs must not alias inputs, except where an entry point says so.
+ *   - Sizes may be zero (nothing is read; outputs that are sums over an empty
+ *     range are written as the epilogue of zero).
+ *   - Every function returns KF_OK (0) or a negative kf_status; on error
+ *     nothing has been enqueued and kf_last_error() describes the cause.
+ */
+#ifndef KF_H
+#define KF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int kf_status;
+#define KF_OK 0
+#define KF_ERR_INVALID_ARG (-1)   /* null pointer, negative size, bad enum   */
+#define KF_ERR_SHAPE (-2)         /* inconsistent sizes or leading dims       */
+#define KF_ERR_DTYPE (-3)         /* unsupported storage format               */
+#define KF_ERR_ALIGN (-4)         /* alignment required by this entry point   */
+#define KF_ERR_CYCLE (-5)         /* script dependency cycle                  */
+#define KF_ERR_UNDEFINED_VAR (-6) /* script reads a variable never written   */
+#define KF_ERR_CUDA (-7)          /* CUDA runtime error (message in last_error) */
+#define KF_ERR_NO_MEM (-8)        /* host allocation failed                   */
+#define KF_ERR_DEVICE_TIMEOUT (-9) /* a bounded device wait ran out          */
+#define KF_ERR_UNSUPPORTED (-10)  /* no kernel instance for this request      */
+#define KF_ERR_WORKSPACE (-11)    /* workspace missing or too small           */
+
+/* Storage format of a matrix operand.  The paper is FP32 only (Section 4.1);
+ * the row-scaled formats store Q_ij with one FP32 scale s_i per row and
+ * represent A_ij ~ s_i * Q_ij. */
+typedef enum {
+  KF_F32 = 0,
+  KF_BF16_ROWSCALE = 1,
+  KF_FP8E4M3_ROWSCALE = 2
+} kf_dtype;
+
+/* Call kinds whose workspace needs differ (kf_workspace_size). */
+typedef enum {
+  KF_SEQ_BICGK = 0,
+  KF_SEQ_GEMVER = 1,
+  KF_SEQ_GESUMMV = 2,
+  KF_SEQ_ATAX = 3,
+  KF_SEQ_AXPYDOT = 4,
+  KF_SEQ_WAXPBY = 5,
+  KF_SEQ_GEMV = 6,
+  KF_SEQ_GEMVT = 7,
+  KF_SEQ_DOT = 8
+} kf_seq;
+
+/* Library version string (static storage). */
+const char* kf_version(void);
+
+/* Message of the last error on the calling thread (valid until the next
+ * libkf call on that thread). */
+const char* kf_last_error(void);
+
+/* Number of SMs of the current device (152 on GB300). */
+kf_status kf_device_sm_count(int* sm_count);
+
+/* Bytes of workspace needed by call kind `seq` on an m x n problem (vectors:
+ * m = 1, n = length) for every tuning the library may pick. */
+kf_status kf_workspace_size(kf_seq seq, int64_t m, int64_t n, kf_dtype fmt, size_t* bytes);
+
+/* Zero `bytes` of workspace on `stream` (required once before first use). */
+kf_status kf_workspace_init(void* ws, size_t bytes, void* stream);
+
+/* Synchronise `stream` and read the device error word at the start of `ws`:
+ * returns KF_ERR_DEVICE_TIMEOUT (and clears the word) if a bounded wait of
+ * an earlier call on this workspace ran out, KF_OK otherwise. */
+kf_status kf_workspace_status(void* ws, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Fused sequences (Table 1 of Section 4.1).  Each is one pass of the fused
+ * kernels the planner emits for the canonical script of the sequence.
+ * ---------------------------------------------------------------------- */
+
+/* BiCGK (Section 3.4, Listing 1, Algorithm 3): q = A p and s = A^T r with a
+ * single read of A.  A: m x n (fmt KF_F32, or row-scaled Q with row_scale of
+ * length m); p, s: length n; q, r: length m.  One kernel launch. */
+kf_status kf_bicgk(int64_t m, int64_t n, const void* A, int64_t lda, kf_dtype fmt,
+                   const float* row_scale, const float* p, const float* r, float* q, float* s,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* GEMVER (Table 1): B = A + u1 v1^T + u2 v2^T; x = beta B^T y + z;
+ * w = alpha B x.  A, B: n x n (B written, ldb >= n); all vectors length n.
+ * Two launches: the second needs all of x (a global barrier, Section 3.2.2). */
+kf_status kf_gemver(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
+                    const float* u2, const float* v2, const float* y, const float* z, float alpha,
+                    float beta, float* B, int64_t ldb, float* x, float* w, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* GESUMMV (Table 1): y = alpha A x + beta B x.  A, B: m x n with the same
+ * leading dimension; x: length n; y: length m.  One launch; x is read once
+ * per column strip for both matrices. */
+kf_status kf_gesummv(int64_t m, int64_t n, const float* A, const float* B, int64_t lda,
+                     const float* x, float alpha, float beta, float* y, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* ATAX (Table 1): y = A^T (A x).  A: m x n; x, y: length n.  One read of A
+ * by blocks that own whole rows (rows staged by bulk asynchronous copies),
+ * plus a small finishing launch; falls back to two passes (t = A x, then
+ * y = A^T t, the paper's form) when rows are not 16-byte aligned or n > 16384.
+ * Device waits are bounded: see kf_workspace_status. */
+kf_status kf_atax(int64_t m, int64_t n, const float* A, int64_t lda, const float* x, float* y,
+                  void* ws, size_t ws_bytes, void* stream);
+
+/* AXPYDOT (Table 1): z = w - alpha v; r = z^T u.  Vectors length n; r is one
+ * device float.  One launch.  The cross-block sum of r is done in double for
+ * n >= 2^26. */
+kf_status kf_axpydot(int64_t n, const float* w, const float* v, const float* u, float alpha,
+                     float* z, float* r, void* ws, size_t ws_bytes, void* stream);
+
+/* WAXPBY (Table 1): w = alpha x + beta y.  One launch, no workspace. */
+kf_status kf_waxpby(int64_t n, float alpha, const float* x, float beta, const float* y, float* w,
+                    void* stream);
+
+/* ------------------------------------------------------------------------
+ * Elementary functions (Section 3.3): one kernel each, out of place unless
+ * stated.  They form the unfused per-call chains.
+ * ---------------------------------------------------------------------- */
+
+/* y = alpha A x + beta y0 (y0 may be NULL when beta == 0).  A: m x n. */
+kf_status kf_gemv(int64_t m, int64_t n, const void* A, int64_t lda, kf_dtype fmt,
+                  const float* row_scale, float alpha, const float* x, float beta,
+                  const float* y0, float* y, void* ws, size_t ws_bytes, void* stream);
+
+/* x = alpha A^T y + beta x0 (x0 may be NULL when beta == 0).  A: m x n. */
+kf_status kf_gemvt(int64_t m, int64_t n, const void* A, int64_t lda, kf_dtype fmt,
+                   const float* row_scale, float alpha, const float* y, float beta,
+                   const float* x0, float* x, void* ws, size_t ws_bytes, void* stream);
+
+/* B = A + alpha u v^T.  u: length m, v: length n.  B may equal A (in place,
+ * then ldb must equal lda). */
+kf_status kf_ger(int64_t m, int64_t n, const float* A, int64_t lda, float alpha, const float* u,
+                 const float* v, float* B, int64_t ldb, void* stream);
+
+/* out = alpha x + beta y (AXPY when out == y and beta == 1; in place allowed). */
+kf_status kf_axpby(int64_t n, float alpha, const float* x, float beta, const float* y, float* out,
+                   void* stream);
+
+/* out = alpha x (SCAL; in place allowed). */
+kf_status kf_scal(int64_t n, float alpha, const float* x, float* out, void* stream);
+
+/* out = w + y + z (VADD of Table 1; in place allowed). */
+kf_status kf_vadd3(int64_t n, const float* w, const float* y, const float* z, float* out,
+                   void* stream);
+
+/* *out = x . y (one device float). */
+kf_status kf_dot(int64_t n, const float* x, const float* y, float* out, void* ws, size_t ws_bytes,
+                 void* stream);
+
+/* ------------------------------------------------------------------------
+ * Row-scaled low-precision storage (not in the paper, which is FP32 only).
+ * ---------------------------------------------------------------------- */
+
+/* Quantise an FP32 matrix row by row: s_i = amax_i / QMAX (QMAX = 1 for
+ * BF16, 448 for E4M3; s_i = 1 for an all-zero row), Q_ij = round-to-nearest-
+ * even of (A_ij / s_i) in the format, saturating at +-448 for E4M3.  Q is
+ * written densely (leading dimension n), 2 bytes per element for BF16, 1 for
+ * E4M3; row_scale gets m floats. */
+kf_status kf_quantize_rows(int64_t m, int64_t n, const float* A, int64_t lda, kf_dtype fmt, void* Q,
+                           float* row_scale, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Tuning (Section 3.2: block size and serial iterations are part of a
+ * fusion implementation).  A tuning applies to matrix passes launched
+ * afterwards in the calling process.  warps in {4, 8}; vec (16-byte chunks
+ * per lane per row) in {1, 2, 4}; unroll (rows per batch) in {1, 2, 4};
+ * groups = row groups per column strip (0 = fill one wave of resident
+ * blocks); stages = depth of each warp's bulk-copy ring (1..8), or 0 for
+ * direct 16-byte loads.  warps = 0 restores the automatic choice (the
+ * default).  A combination without a compiled instance falls back to the
+ * default instance of the same op shape.
+ * ---------------------------------------------------------------------- */
+kf_status kf_set_matrix_tuning(int warps, int vec, int unroll, int groups, int stages);
+kf_status kf_get_matrix_tuning(int* warps, int* vec, int* unroll, int* groups, int* stages);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KF_H */

@@ -1,0 +1,222 @@
+// Single-pass ATAX: y = A^T (A x) with one read of A.
+//
+// The paper (Section 4.1) treats ATAX as unfusable: the row dot t_i = A_i.x
+// is a reduction whose result is needed before A_i^T t_i can be accumulated,
+// and its blocks split rows, so a global barrier (a second kernel) separates
+// the two uses of A.  Section 4.2 notes that reuse of row data needs
+// persistent blocks that own whole rows.  Here a block owns complete rows:
+// each row is staged into a shared-memory ring by bulk asynchronous copies
+// (cp.async.bulk with mbarrier completion, several rows in flight), the block
+// reduces the row dot, and then every thread accumulates t_i * A_ij for its
+// columns from the row still on chip.  Per-block column partials are added
+// in block order by a second small kernel (Section 3.2.2, option (i)),
+// launched with programmatic dependent launch so it is resident before the
+// first kernel ends.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kf_device.cuh"
+#include "kf_internal.h"
+
+namespace kf {
+
+constexpr int ATAX_MAXSTAGES = 8;
+
+namespace {
+
+template <int NT, int VA>
+__global__ void __launch_bounds__(NT) atax_rows_kernel(const float* __restrict__ A, int64_t lda, int64_t m,
+                                                        int64_t n, const float* __restrict__ x,
+                                                        float* __restrict__ ypart, int stages,
+                                                        int64_t rowcap, unsigned* err) {
+  extern __shared__ float4 ring4[];
+  float* ring = reinterpret_cast<float*>(ring4);
+  __shared__ __align__(8) uint64_t full[ATAX_MAXSTAGES];
+  __shared__ float red[2][NT / 32];
+
+  // Let the finishing kernel launch now; it waits for this grid itself.
+  asm volatile("griddepcontrol.launch_dependents;");
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = m * blockIdx.x / gridDim.x;
+  const int64_t r1 = m * (blockIdx.x + 1) / gridDim.x;
+  const int64_t nrows = r1 - r0;
+  const unsigned bytes = (unsigned)(n * sizeof(float));
+  const int64_t n4 = n >> 2;
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < stages && s < nrows; ++s) {
+      mbar_expect_tx(&full[s], bytes);
+      bulk_g2s(ring + s * rowcap, A + (r0 + s) * lda, bytes, &full[s]);
+    }
+  }
+
+  float4 xr[VA], yacc[VA];
+#pragma unroll
+  for (int k = 0; k < VA; ++k) {
+    const int64_t c4 = (int64_t)k * NT + tid;
+    xr[k] = c4 < n4 ? reinterpret_cast<const float4*>(x)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    yacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+
+  for (int64_t j = 0; j < nrows; ++j) {
+    const int s = (int)(j % stages);
+    const unsigned par = (unsigned)((j / stages) & 1);
+    const bool ok = mbar_wait_bounded(&full[s], par);
+    float4 a[VA];
+    float d0 = 0.f, d1 = 0.f;
+    const float4* row = reinterpret_cast<const float4*>(ring + s * rowcap);
+#pragma unroll
+    for (int k = 0; k < VA; ++k) {
+      const int64_t c4 = (int64_t)k * NT + tid;
+      a[k] = (ok && c4 < n4) ? row[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      d0 = fmaf(a[k].x, xr[k].x, d0);
+      d1 = fmaf(a[k].y, xr[k].y, d1);
+      d0 = fmaf(a[k].z, xr[k].z, d0);
+      d1 = fmaf(a[k].w, xr[k].w, d1);
+    }
+    const float d = warp_sum(d0 + d1);
+    if (lane == 0) red[j & 1][warp] = d;
+    if (__syncthreads_or(!ok)) {
+      // A copy never completed: report, let the other copies land (bounded), stop.
+      if (tid == 0) {
+        atomicOr(err, KF_DEVERR_TIMEOUT);
+        for (int64_t q = j; q < nrows && q < j + stages; ++q)
+          (void)mbar_wait_bounded(&full[q % stages], (unsigned)((q / stages) & 1));
+      }
+      __syncthreads();
+      return;
+    }
+    // Every thread has its row values in registers: the stage can be refilled.
+    if (tid == 0 && j + stages < nrows) {
+      fence_proxy_async_smem();
+      mbar_expect_tx(&full[s], bytes);
+      bulk_g2s(ring + s * rowcap, A + (r0 + j + stages) * lda, bytes, &full[s]);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) t += red[j & 1][w];
+#pragma unroll
+    for (int k = 0; k < VA; ++k) {
+      yacc[k].x = fmaf(t, a[k].x, yacc[k].x);
+      yacc[k].y = fmaf(t, a[k].y, yacc[k].y);
+      yacc[k].z = fmaf(t, a[k].z, yacc[k].z);
+      yacc[k].w = fmaf(t, a[k].w, yacc[k].w);
+    }
+  }
+  float4* yp = reinterpret_cast<float4*>(ypart + (int64_t)blockIdx.x * n);
+#pragma unroll
+  for (int k = 0; k < VA; ++k) {
+    const int64_t c4 = (int64_t)k * NT + tid;
+    if (c4 < n4) yp[c4] = yacc[k];
+  }
+}
+
+// y[c] = sum over blocks b (in order) of ypart[b][c].  256 threads = 32
+// float4 columns x 8 slices; slice s adds blocks s, s+8, ...; the slices are
+// added in slice order, so the result is independent of timing.
+__global__ void __launch_bounds__(256) atax_finish_kernel(const float* __restrict__ ypart, int nparts,
+                                                          int64_t n, float* __restrict__ y) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __shared__ float4 sh[8][32];
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  const int64_t n4 = n >> 2;
+  const int64_t c4 = (int64_t)blockIdx.x * 32 + lane;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (c4 < n4) {
+    const float4* p = reinterpret_cast<const float4*>(ypart) + c4;
+    for (int b = slice; b < nparts; b += 8) {
+      const float4 v = __ldcg(p + (int64_t)b * n4);
+      s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+    }
+  }
+  sh[slice][lane] = s;
+  __syncthreads();
+  if (slice == 0 && c4 < n4) {
+    float4 r = sh[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      r.x += sh[q][lane].x; r.y += sh[q][lane].y; r.z += sh[q][lane].z; r.w += sh[q][lane].w;
+    }
+    reinterpret_cast<float4*>(y)[c4] = r;
+  }
+}
+
+struct AEntry {
+  const void* fn;
+  int occ_for_stages[ATAX_MAXSTAGES + 1];
+};
+
+template <int VA>
+const void* atax_fn() {
+  return (const void*)&atax_rows_kernel<512, VA>;
+}
+
+}  // namespace
+
+// Can the single-pass form take this shape?  (16-byte aligned rows, whole
+// row fits the ring, at most 16384 columns.)
+bool atax_single_pass_ok(int64_t m, int64_t n, int64_t lda, const void* A, const void* x, const void* y) {
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  return m > 0 && n > 0 && n % 4 == 0 && lda % 4 == 0 && n <= 16384 && al(A) && al(x) && al(y);
+}
+
+size_t atax_workspace_bytes(int64_t n) {
+  return 256 + (size_t)device_sm_count() * 4 * (size_t)n * sizeof(float);
+}
+
+int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y,
+                       void* ws, size_t ws_bytes, int stages_req, int ctas_per_sm, void* stream,
+                       const char** why) {
+  const int VA = (int)((n / 4 + 511) / 512);
+  const int va = VA <= 1 ? 1 : (VA <= 2 ? 2 : (VA <= 4 ? 4 : 8));
+  const void* fn = va == 1 ? atax_fn<1>() : va == 2 ? atax_fn<2>() : va == 4 ? atax_fn<4>() : atax_fn<8>();
+  const int64_t rowcap = (n + 31) / 32 * 32;  // 128-byte aligned stages
+  const size_t rowbytes = (size_t)rowcap * sizeof(float);
+  const int cps = ctas_per_sm > 0 ? ctas_per_sm : 2;
+  const size_t budget = (size_t)(220 * 1024) / cps;
+  int stages = stages_req > 0 ? stages_req : (int)std::min<size_t>(ATAX_MAXSTAGES, budget / rowbytes);
+  if (stages < 2) stages = std::min<int>(2, (int)((size_t)(220 * 1024) / rowbytes));
+  if (stages < 1) { *why = "row too long for the shared-memory ring"; return -10; }
+  stages = std::min(stages, ATAX_MAXSTAGES);
+  const size_t smem = (size_t)stages * rowbytes;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 512, smem) != cudaSuccess || occ < 1) occ = 1;
+  occ = std::min(occ, cps);
+  int64_t grid = (int64_t)device_sm_count() * occ;
+  grid = std::min<int64_t>(grid, m);
+  grid = std::min<int64_t>(grid, (int64_t)device_sm_count() * 4);
+  unsigned* err = reinterpret_cast<unsigned*>(ws);
+  float* ypart = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
+  if (ws_bytes < 256 + (size_t)grid * n * sizeof(float)) { *why = "workspace too small"; return -11; }
+
+  int nparts = (int)grid;
+  void* args[] = {(void*)&A, (void*)&lda, (void*)&m, (void*)&n, (void*)&x, (void*)&ypart,
+                  (void*)&stages, (void*)&rowcap, (void*)&err};
+  cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(512), args, smem, (cudaStream_t)stream);
+  if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
+
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((n / 4 + 31) / 32));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const float* yp = ypart;
+  e = cudaLaunchKernelEx(&cfg, atax_finish_kernel, yp, nparts, n, y);
+  if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
+  return 0;
+}
+
+}  // namespace kf

@@ -1,0 +1,164 @@
+// Matrix-pass launcher: picks a compiled instance of the kernel template in
+// matprog_impl.cuh for the requested op shape, storage format and tuning,
+// sizes the grid to one wave of resident blocks, and binds the workspace.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "matprog_impl.cuh"
+
+namespace kf {
+namespace mp {
+std::map<Key, Entry>& registry() {
+  static std::map<Key, Entry> r;
+  return r;
+}
+}  // namespace mp
+
+namespace {
+
+std::once_flag g_reg_once;
+void ensure_registry() {
+  std::call_once(g_reg_once, [] {
+    mp::register_f32_staged();
+    mp::register_f32_plain();
+    mp::register_lowp();
+  });
+}
+
+int fmt_ch(int fmt) { return fmt == FMT_F32 ? 4 : (fmt == FMT_BF16 ? 8 : 16); }
+int fmt_bytes(int fmt) { return fmt == FMT_F32 ? 4 : (fmt == FMT_BF16 ? 2 : 1); }
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+int pick_nops(int nops) { return nops <= 1 ? 1 : (nops <= 2 ? 2 : 4); }
+
+// Occupancy per (kernel, dynamic shared memory), cached.
+std::mutex g_occ_mu;
+std::map<std::pair<const void*, size_t>, int> g_occ;
+int occupancy(const void* fn, int threads, size_t smem) {
+  std::lock_guard<std::mutex> g(g_occ_mu);
+  auto key = std::make_pair(fn, smem);
+  auto it = g_occ.find(key);
+  if (it != g_occ.end()) return it->second;
+  // dynamic shared memory may use the opt-in limit minus the static part
+  int dev = 0, optin = 48 * 1024;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, fn);
+  const int maxdyn = optin - (int)fa.sharedSizeBytes;
+  if ((int64_t)smem > (int64_t)maxdyn) { g_occ[key] = 0; return 0; }
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1)
+    occ = 0;
+  g_occ[key] = occ;
+  return occ;
+}
+
+}  // namespace
+
+size_t matprog_workspace_bytes(int64_t m, int64_t n, int nrow_res, int ncol_res, int fmt) {
+  const int64_t ch = fmt_ch(fmt);
+  const int64_t max_strips = n > 0 ? (n + 32 * ch - 1) / (32 * ch) : 1;
+  size_t b = WS_HEADER;
+  b += align256((size_t)(max_strips + MAT_MAXGROUPS) * sizeof(unsigned));
+  b += align256((size_t)nrow_res * max_strips * (size_t)m * sizeof(float));
+  b += (size_t)ncol_res * MAT_MAXGROUPS * (size_t)n * sizeof(float);
+  return b;
+}
+
+// Workspace layout of a matrix pass:
+// [header (error word) | counters | row partials | column partials].
+int matprog_bind_workspace(MatProg& P, void* ws, size_t bytes) {
+  P.errword = ws ? static_cast<unsigned*>(ws) : nullptr;
+  const bool needs_ws = P.nrow_out > 0 || P.ncol_out > 0;
+  if (!needs_ws) return 0;
+  const size_t need = matprog_workspace_bytes(P.m, P.n, P.nrow_res, P.ncol_res, P.fmt);
+  if (ws == nullptr || bytes < need) return -11;
+  const int64_t ch = fmt_ch(P.fmt);
+  const int64_t max_strips = P.n > 0 ? (P.n + 32 * ch - 1) / (32 * ch) : 1;
+  char* b = static_cast<char*>(ws);
+  size_t off = WS_HEADER;
+  P.counters = reinterpret_cast<unsigned*>(b + off);
+  off += align256((size_t)(max_strips + MAT_MAXGROUPS) * sizeof(unsigned));
+  P.rowpart = reinterpret_cast<float*>(b + off);
+  off += align256((size_t)P.nrow_res * max_strips * (size_t)P.m * sizeof(float));
+  P.colpart = reinterpret_cast<float*>(b + off);
+  return 0;
+}
+
+int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** why) {
+  ensure_registry();
+  auto& R = mp::registry();
+  const int nops_k = pick_nops(P.nops);
+  bool vec = true;
+  const int eb = fmt_bytes(P.fmt);
+  for (int t = 0; t < P.nmat; ++t) {
+    if (!aligned16(P.A[t]) || ((P.lda[t] * eb) & 15) != 0) vec = false;
+    if (P.Bout[t] != nullptr && (!aligned16(P.Bout[t]) || ((P.ldb[t] * 4) & 15) != 0)) vec = false;
+  }
+  MatTune t = tune;
+  if (t.warps == 0) {
+    // automatic: the best measured direct-load forms on GB300 (BiCGK 16384^2,
+    // GEMVER/GESUMMV 8192^2): 4 chunks x 2 rows for one matrix, 2 x 4 for two
+    if (P.fmt != FMT_F32) t = MatTune{8, 1, 2, 0, 4};
+    else if (P.nmat == 2) t = MatTune{8, 2, 4, 0, 0};
+    else t = MatTune{8, 4, 2, 0, 0};
+  }
+  bool staged = vec && t.stages > 0;
+  if (!vec) { t.warps = 8; t.vec = 1; t.unroll = 2; staged = false; }
+  auto it = R.find(mp::Key(t.warps, t.vec, t.unroll, nops_k, P.nmat, P.fmt, vec, staged));
+  if (it == R.end()) {
+    // fall back to the default instance of the same op shape and format
+    const int dv = (P.fmt == FMT_F32) ? 2 : 1;
+    it = R.find(mp::Key(8, dv, 2, nops_k, P.nmat, P.fmt, vec, staged));
+    if (it == R.end()) it = R.find(mp::Key(8, dv, 2, nops_k, P.nmat, P.fmt, vec, !staged));
+    if (it == R.end()) it = R.find(mp::Key(8, 1, 2, nops_k, P.nmat, P.fmt, vec, false));
+    if (it == R.end()) { *why = "no kernel instance for this op shape"; return -10; }
+  }
+  const mp::Entry& e = it->second;
+  const int ch = fmt_ch(P.fmt);
+  const int64_t sw = 32LL * e.v * ch;
+  const size_t batch = (size_t)P.nmat * e.u * 32 * e.v * 16;
+  int stages = e.staged ? std::max(1, std::min(MAT_MAXSTAGES, t.stages > 0 ? t.stages : 4)) : 0;
+  size_t smem = (size_t)e.nw * sw * sizeof(float);
+  if (e.staged) {
+    // keep the ring within the per-block limit
+    while (stages > 1 && (size_t)e.nw * stages * batch > 200 * 1024) --stages;
+    smem = std::max(smem, (size_t)e.nw * stages * batch);
+  }
+  const int occ = occupancy(e.fn, e.nw * 32, smem);
+  if (occ < 1) { *why = "kernel does not fit on an SM with this tuning"; return -10; }
+
+  // Geometry: strips by the instance's strip width, groups to fill one wave.
+  const int64_t strips = P.n > 0 ? (P.n + sw - 1) / sw : 1;
+  const int64_t nrb = (P.m + 31) / 32;
+  const int64_t slots = (int64_t)device_sm_count() * occ;
+  int64_t G;
+  if (t.groups > 0) G = t.groups;
+  else G = std::max<int64_t>(1, slots / std::max<int64_t>(1, strips));
+  G = std::min<int64_t>(G, std::max<int64_t>(1, nrb));
+  G = std::min<int64_t>(G, MAT_MAXGROUPS);
+  int64_t bpg = nrb > 0 ? (nrb + G - 1) / G : 0;
+  // keep every warp of a block equally busy when that costs no extra wave
+  if (t.groups <= 0 && bpg > 0 && bpg % e.nw != 0) {
+    const int64_t b2 = ((bpg + e.nw - 1) / e.nw) * e.nw;
+    const int64_t g2 = (nrb + b2 - 1) / b2;
+    if (g2 * strips <= slots) bpg = b2;
+  }
+  G = nrb > 0 ? (nrb + bpg - 1) / bpg : 1;
+  if (strips > 0x7fffffffLL) { *why = "matrix too wide"; return -2; }
+  P.n_strips = (int)strips;
+  P.n_groups = (int)G;
+  P.blocks_per_group = bpg;
+  P.stages = stages;
+  dim3 grid((unsigned)strips, (unsigned)G);
+  void* args[] = {&P};
+  cudaError_t err = cudaLaunchKernel(e.fn, grid, dim3(e.nw * 32), args, smem, (cudaStream_t)stream);
+  if (err != cudaSuccess) { *why = cudaGetErrorString(err); return -7; }
+  return 0;
+}
+
+}  // namespace kf

@@ -1,0 +1,14 @@
+// Instances of the matrix pass: FP32 storage, bulk-copy staged.
+#include "matprog_impl.cuh"
+
+namespace kf {
+namespace mp {
+void register_f32_staged() {
+  reg_shapes<8, 2, 2, FMT_F32, true>();
+  reg_shapes<8, 4, 1, FMT_F32, true>();
+  reg_shapes<8, 2, 1, FMT_F32, true>();
+  reg_shapes<8, 1, 2, FMT_F32, true>();
+  reg_shapes<4, 4, 2, FMT_F32, true>();
+}
+}  // namespace mp
+}  // namespace kf

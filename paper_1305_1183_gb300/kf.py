@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libkf (include/kf.h).
+
+Each function has the name of the C entry point it calls and only marshals
+arguments: torch tensors become device pointers and sizes, the stream is the
+caller's current CUDA stream.  There is no fallback: if libkf is not built
+the first call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+KF_OK = 0
+KF_F32, KF_BF16_ROWSCALE, KF_FP8E4M3_ROWSCALE = 0, 1, 2
+(KF_SEQ_BICGK, KF_SEQ_GEMVER, KF_SEQ_GESUMMV, KF_SEQ_ATAX, KF_SEQ_AXPYDOT, KF_SEQ_WAXPBY,
+ KF_SEQ_GEMV, KF_SEQ_GEMVT, KF_SEQ_DOT) = range(9)
+
+STATUS_NAMES = {
+    -1: "KF_ERR_INVALID_ARG", -2: "KF_ERR_SHAPE", -3: "KF_ERR_DTYPE", -4: "KF_ERR_ALIGN",
+    -5: "KF_ERR_CYCLE", -6: "KF_ERR_UNDEFINED_VAR", -7: "KF_ERR_CUDA", -8: "KF_ERR_NO_MEM",
+    -9: "KF_ERR_DEVICE_TIMEOUT", -10: "KF_ERR_UNSUPPORTED", -11: "KF_ERR_WORKSPACE",
+}
+
+
+class KFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+i64 = ctypes.c_int64
+vp = ctypes.c_void_p
+f32 = ctypes.c_float
+sz = ctypes.c_size_t
+ci = ctypes.c_int
+
+_SIGS = {
+    "kf_version": ([], ctypes.c_char_p),
+    "kf_last_error": ([], ctypes.c_char_p),
+    "kf_device_sm_count": ([ctypes.POINTER(ci)], ci),
+    "kf_workspace_size": ([ci, i64, i64, ci, ctypes.POINTER(sz)], ci),
+    "kf_workspace_init": ([vp, sz, vp], ci),
+    "kf_workspace_status": ([vp, vp], ci),
+    "kf_bicgk": ([i64, i64, vp, i64, ci, vp, vp, vp, vp, vp, vp, sz, vp], ci),
+    "kf_gemver": ([i64, vp, i64, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, sz, vp], ci),
+    "kf_gesummv": ([i64, i64, vp, vp, i64, vp, f32, f32, vp, vp, sz, vp], ci),
+    "kf_atax": ([i64, i64, vp, i64, vp, vp, vp, sz, vp], ci),
+    "kf_axpydot": ([i64, vp, vp, vp, f32, vp, vp, vp, sz, vp], ci),
+    "kf_waxpby": ([i64, f32, vp, f32, vp, vp, vp], ci),
+    "kf_gemv": ([i64, i64, vp, i64, ci, vp, f32, vp, f32, vp, vp, vp, sz, vp], ci),
+    "kf_gemvt": ([i64, i64, vp, i64, ci, vp, f32, vp, f32, vp, vp, vp, sz, vp], ci),
+    "kf_ger": ([i64, i64, vp, i64, f32, vp, vp, vp, i64, vp], ci),
+    "kf_axpby": ([i64, f32, vp, f32, vp, vp, vp], ci),
+    "kf_scal": ([i64, f32, vp, vp, vp], ci),
+    "kf_vadd3": ([i64, vp, vp, vp, vp, vp], ci),
+    "kf_dot": ([i64, vp, vp, vp, vp, sz, vp], ci),
+    "kf_quantize_rows": ([i64, i64, vp, i64, ci, vp, vp, vp], ci),
+    "kf_set_matrix_tuning": ([ci, ci, ci, ci, ci], ci),
+    "kf_get_matrix_tuning": ([ctypes.POINTER(ci)] * 5, ci),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libkf.so (built by ``_build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libkf is not built ({path} missing): run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ck(status: int):
+    if status != KF_OK:
+        raise KFError(status, lib().kf_last_error().decode())
+
+
+def _p(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _st(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _nb(t):
+    return 0 if t is None else t.numel() * t.element_size()
+
+
+# ------------------------------------------------------------------ utilities
+
+def kf_version() -> str:
+    return lib().kf_version().decode()
+
+
+def kf_device_sm_count() -> int:
+    v = ci(0)
+    _ck(lib().kf_device_sm_count(ctypes.byref(v)))
+    return v.value
+
+
+def kf_workspace_size(seq: int, m: int, n: int, fmt: int = KF_F32) -> int:
+    b = sz(0)
+    _ck(lib().kf_workspace_size(seq, m, n, fmt, ctypes.byref(b)))
+    return b.value
+
+
+def workspace(seq: int, m: int, n: int, fmt: int = KF_F32, device="cuda") -> torch.Tensor:
+    """Zero-filled workspace tensor for ``seq`` (torch owns the memory)."""
+    nbytes = max(kf_workspace_size(seq, m, n, fmt), 256)
+    return torch.zeros(nbytes, dtype=torch.uint8, device=device)
+
+
+def kf_workspace_status(ws, stream=None):
+    _ck(lib().kf_workspace_status(_p(ws), _st(stream)))
+
+
+def kf_set_matrix_tuning(warps: int, vec: int, unroll: int, groups: int = 0, stages: int = 4):
+    _ck(lib().kf_set_matrix_tuning(warps, vec, unroll, groups, stages))
+
+
+def kf_get_matrix_tuning():
+    v = [ci(0) for _ in range(5)]
+    _ck(lib().kf_get_matrix_tuning(*[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+# ------------------------------------------------------------------ sequences
+
+def kf_bicgk(A, p, r, q, s, ws, fmt=KF_F32, row_scale=None, lda=None, n=None, stream=None):
+    m = A.shape[0]
+    n = A.shape[1] if n is None else n
+    if fmt == KF_F32:
+        lda = A.stride(0) if lda is None else lda
+    else:
+        lda = n if lda is None else lda
+    _ck(lib().kf_bicgk(m, n, _p(A), lda, fmt, _p(row_scale), _p(p), _p(r), _p(q), _p(s),
+                       _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_gemver(A, u1, v1, u2, v2, y, z, alpha, beta, B, x, w, ws, stream=None):
+    n = A.shape[0]
+    _ck(lib().kf_gemver(n, _p(A), A.stride(0), _p(u1), _p(v1), _p(u2), _p(v2), _p(y), _p(z),
+                        alpha, beta, _p(B), B.stride(0), _p(x), _p(w), _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_gesummv(A, B, x, alpha, beta, y, ws, stream=None):
+    m, n = A.shape
+    assert A.stride(0) == B.stride(0)
+    _ck(lib().kf_gesummv(m, n, _p(A), _p(B), A.stride(0), _p(x), alpha, beta, _p(y),
+                         _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_atax(A, x, y, ws, stream=None):
+    m, n = A.shape
+    _ck(lib().kf_atax(m, n, _p(A), A.stride(0), _p(x), _p(y), _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_axpydot(w, v, u, alpha, z, r, ws, stream=None):
+    _ck(lib().kf_axpydot(w.numel(), _p(w), _p(v), _p(u), alpha, _p(z), _p(r), _p(ws), _nb(ws),
+                         _st(stream)))
+
+
+def kf_waxpby(alpha, x, beta, y, w, stream=None):
+    _ck(lib().kf_waxpby(x.numel(), alpha, _p(x), beta, _p(y), _p(w), _st(stream)))
+
+
+# ------------------------------------------------------------------ elementaries
+
+def kf_gemv(A, x, y, ws, alpha=1.0, beta=0.0, y0=None, fmt=KF_F32, row_scale=None, n=None,
+            stream=None):
+    m = A.shape[0]
+    n = A.shape[1] if n is None else n
+    lda = A.stride(0) if fmt == KF_F32 else n
+    _ck(lib().kf_gemv(m, n, _p(A), lda, fmt, _p(row_scale), alpha, _p(x), beta, _p(y0), _p(y),
+                      _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_gemvt(A, y, x, ws, alpha=1.0, beta=0.0, x0=None, fmt=KF_F32, row_scale=None, n=None,
+             stream=None):
+    m = A.shape[0]
+    n = A.shape[1] if n is None else n
+    lda = A.stride(0) if fmt == KF_F32 else n
+    _ck(lib().kf_gemvt(m, n, _p(A), lda, fmt, _p(row_scale), alpha, _p(y), beta, _p(x0), _p(x),
+                       _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_ger(A, u, v, B, alpha=1.0, stream=None):
+    m, n = A.shape
+    _ck(lib().kf_ger(m, n, _p(A), A.stride(0), alpha, _p(u), _p(v), _p(B), B.stride(0), _st(stream)))
+
+
+def kf_axpby(alpha, x, beta, y, out, stream=None):
+    _ck(lib().kf_axpby(x.numel(), alpha, _p(x), beta, _p(y), _p(out), _st(stream)))
+
+
+def kf_scal(alpha, x, out, stream=None):
+    _ck(lib().kf_scal(x.numel(), alpha, _p(x), _p(out), _st(stream)))
+
+
+def kf_vadd3(w, y, z, out, stream=None):
+    _ck(lib().kf_vadd3(w.numel(), _p(w), _p(y), _p(z), _p(out), _st(stream)))
+
+
+def kf_dot(x, y, out, ws, stream=None):
+    _ck(lib().kf_dot(x.numel(), _p(x), _p(y), _p(out), _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_quantize_rows(A, fmt, Q, row_scale, stream=None):
+    m, n = A.shape
+    _ck(lib().kf_quantize_rows(m, n, _p(A), A.stride(0), fmt, _p(Q), _p(row_scale), _st(stream)))

@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every declared symbol (no GPU).
+
+Only argument validation runs here: those paths return before any CUDA call.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "kf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(kf_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def kf():
+    from paper_1305_1183_gb300 import _build, kf as K
+    _build.build()
+    K.lib()
+    return K
+
+
+def test_every_declared_symbol_is_exported(kf):
+    names = declared_functions()
+    assert len(names) >= 20, names
+    L = kf.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding covers every declared entry point under the same name
+    assert set(names) <= set(kf.exported_symbols()), set(names) - set(kf.exported_symbols())
+
+
+def test_validation_without_gpu(kf):
+    L = kf.lib()
+    assert L.kf_bicgk(-1, 4, None, 4, 0, None, None, None, None, None, None, 0, None) == -1
+    assert L.kf_bicgk(4, 4, None, 4, 0, None, None, None, None, None, None, 0, None) == -1
+    assert b"null matrix" in L.kf_last_error()
+    assert L.kf_bicgk(4, 8, 1024, 4, 0, None, 16, 16, 16, 16, None, 0, None) == -2   # lda < n
+    assert L.kf_bicgk(4, 4, 1024, 4, 9, None, 16, 16, 16, 16, None, 0, None) == -3   # format
+    assert L.kf_bicgk(4, 4, 1024, 4, 2, None, 16, 16, 16, 16, None, 0, None) == -1   # scales
+    assert L.kf_set_matrix_tuning(3, 2, 2, 0, 4) == -1
+    assert L.kf_set_matrix_tuning(8, 2, 2, 0, 9) == -1
+    assert L.kf_set_matrix_tuning(8, 2, 2, 0, 4) == 0
+    b = ctypes.c_size_t(0)
+    assert L.kf_workspace_size(0, 16384, 16384, 0, ctypes.byref(b)) == 0
+    assert 0 < b.value < 64 << 20          # bounded, small next to the 1 GiB matrix
+    assert L.kf_workspace_size(42, 1, 1, 0, ctypes.byref(b)) == -1
+    assert L.kf_axpydot(10, None, None, None, 1.0, None, None, None, 0, None) == -1
+    assert L.kf_ger(4, 4, 1024, 4, 1.0, 16, 16, 1024, 8, None) == -2                   # in place, ldb != lda
