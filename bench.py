@@ -121,36 +121,61 @@ def algorithmic_flops(seq: str, size) -> int:
 class Suite:
     """Device-resident inputs and outputs of every sequence, plus the calls."""
 
-    def __init__(self, kf, sizes, device, seed=0):
+    def __init__(self, kf, sizes, device, seed=0, seqs=None):
         self.kf = kf
         self.sizes = sizes
+        seqs = SEQS if seqs is None else seqs
         d = device
         g = lambda shape, tid: synth.uniform(shape, seed, tid, device=d)  # noqa: E731
+        self.mat_ws = kf.workspace(kf.KF_SEQ_BICGK, 16384, 16384)
+        if "bicgk" in seqs:
+            self._mk_bicgk(kf, sizes, d, g)
+        if "gemver" in seqs:
+            self._mk_gemver(kf, sizes, d, g)
+        if "gesummv" in seqs:
+            self._mk_gesummv(kf, sizes, d, g)
+        if "atax" in seqs:
+            self._mk_atax(kf, sizes, d, g)
+        if "axpydot" in seqs:
+            self._mk_axpydot(kf, sizes, d, g)
+        if "waxpby" in seqs:
+            self._mk_waxpby(kf, sizes, d, g)
+
+    def _mk_bicgk(self, kf, sizes, d, g):
         m, n = sizes["bicgk"]
         self.bicgk = dict(A=g((m, n), synth.TID["A"]), p=g((n,), synth.TID["p"]), r=g((m,), synth.TID["r"]),
                           q=torch.empty(m, device=d), s=torch.empty(n, device=d),
                           ws=kf.workspace(kf.KF_SEQ_BICGK, m, n))
+
+    def _mk_gemver(self, kf, sizes, d, g):
         n = sizes["gemver"]
         self.gemver = dict(A=g((n, n), synth.TID["A"]), **{k: g((n,), synth.TID[k]) for k in
                                                          ("u1", "v1", "u2", "v2", "y", "z")},
                            B=torch.empty(n, n, device=d), x=torch.empty(n, device=d),
                            w=torch.empty(n, device=d), t=torch.empty(n, device=d),
                            ws=kf.workspace(kf.KF_SEQ_GEMVER, n, n))
+
+    def _mk_gesummv(self, kf, sizes, d, g):
         n = sizes["gesummv"]
         self.gesummv = dict(A=g((n, n), synth.TID["A"]), B=g((n, n), synth.TID["B"]), x=g((n,), synth.TID["x"]),
                             y=torch.empty(n, device=d), t1=torch.empty(n, device=d),
                             t2=torch.empty(n, device=d), ws=kf.workspace(kf.KF_SEQ_GESUMMV, n, n))
+
+    def _mk_atax(self, kf, sizes, d, g):
         m, n = sizes["atax"]
         self.atax = dict(A=g((m, n), synth.TID["A"]), x=g((n,), synth.TID["x"]), y=torch.empty(n, device=d),
                          t=torch.empty(m, device=d), ws=kf.workspace(kf.KF_SEQ_ATAX, m, n))
+
+    def _mk_axpydot(self, kf, sizes, d, g):
         n = sizes["axpydot"]
         self.axpydot = dict(w=g((n,), synth.TID["w"]), v=g((n,), synth.TID["v"]), u=g((n,), synth.TID["u"]),
                             z=torch.empty(n, device=d), r=torch.empty(1, device=d),
                             ws=kf.workspace(kf.KF_SEQ_AXPYDOT, 1, n))
+
+    def _mk_waxpby(self, kf, sizes, d, g):
         n = sizes["waxpby"]
         self.waxpby = dict(x=g((n,), synth.TID["x"]), y=g((n,), synth.TID["y"]), w=torch.empty(n, device=d),
                            t=torch.empty(n, device=d))
-        self.mat_ws = kf.workspace(kf.KF_SEQ_BICGK, 16384, 16384)
 
     # fused: the kernels the library emits for each canonical script
     def fused(self, seq, st):
@@ -474,6 +499,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--seqs", default=",".join(SEQS), help="comma-separated subset of the suite")
+    ap.add_argument("--bicgk", type=int, default=0, help="square BiCGK size override (profiling)")
+    ap.add_argument("--mat-tuning", default="", help="warps,vec,unroll,groups,stages for matrix passes")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
 
@@ -486,7 +514,11 @@ def main():
 
     # the CPU baseline runs before any CUDA work (no process forked later)
     cpu = None
-    sizes = SMALL if args.small else FULL
+    sizes = dict(SMALL if args.small else FULL)
+    if args.bicgk > 0:
+        sizes["bicgk"] = (args.bicgk, args.bicgk)
+    seqs = [s for s in args.seqs.split(",") if s]
+    assert all(s in SEQS for s in seqs), seqs
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sizes)
 
@@ -499,7 +531,9 @@ def main():
     _build.build()
     kf.lib()
 
-    suite = Suite(kf, sizes, torch.device("cuda", local))
+    if args.mat_tuning:
+        kf.kf_set_matrix_tuning(*[int(v) for v in args.mat_tuning.split(",")])
+    suite = Suite(kf, sizes, torch.device("cuda", local), seqs=seqs)
     st = torch.cuda.Stream()
     torch.cuda.synchronize()
 
@@ -511,20 +545,20 @@ def main():
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
-    total_ms, per = time_suite(suite, "fused", args.steps, args.warmup, st, SEQS)
+    total_ms, per = time_suite(suite, "fused", args.steps, args.warmup, st, seqs)
     barrier()
     clk = clocks.stop()
 
     unf_total, unf_per = None, {}
     if not args.no_unfused:
-        unf_total, unf_per = time_suite(suite, "unfused", args.steps, args.warmup, st, SEQS)
+        unf_total, unf_per = time_suite(suite, "unfused", args.steps, args.warmup, st, seqs)
 
     e2e = None
     if not args.no_e2e:
-        e2e_ms, h2d, d2h = time_e2e(suite, max(1, min(args.steps, 5)), 1, st, SEQS)
+        e2e_ms, h2d, d2h = time_e2e(suite, max(1, min(args.steps, 5)), 1, st, seqs)
         e2e_steps = max(1, min(args.steps, 5))
 
-    step_bytes = sum(algorithmic_bytes(s, sizes[s]) for s in SEQS)
+    step_bytes = sum(algorithmic_bytes(s, sizes[s]) for s in seqs)
     t_max = total_ms
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")
@@ -535,7 +569,7 @@ def main():
     peak, peak_kind = hbm_peak()
 
     seqinfo = {}
-    for s in SEQS:
+    for s in seqs:
         b = algorithmic_bytes(s, sizes[s])
         g = b / (per[s] * 1e-3) / 1e9
         d = {"ms": per[s], "gbs": g, "frac": g / peak, "frac_nominal": g / NOMINAL_HBM_GBS,
@@ -547,11 +581,11 @@ def main():
             d["speedup_vs_unfused"] = unf_per[s] / per[s]
         seqinfo[s] = d
 
-    dom = "bicgk"
+    dom = "bicgk" if "bicgk" in seqs else seqs[0]
     dom_bytes = algorithmic_bytes(dom, sizes[dom])
     achieved = dom_bytes / (per[dom] * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": committed_traffic() if not args.small else None,
+            "traffic": committed_traffic() if (not args.small and args.bicgk == 0 and dom == "bicgk") else None,
             "kernel": "matprog_kernel (BiCGK q=Ap, s=A^T r, one pass over A)",
             "algorithmic_bytes_per_launch": dom_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else "fallback 6.8 TB/s"}
@@ -560,7 +594,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded splitmix64 uniform[-1,1), seed 0)",
-        "config": {"workload": WORKLOAD if not args.small else "small suite (quick check)",
+        "config": {"workload": WORKLOAD if (not args.small and args.bicgk == 0 and seqs == SEQS)
+                   else f"subset {seqs}, sizes {[sizes[s] for s in seqs]}",
                    "l2": "inputs larger than L2 (every matrix / long vector exceeds 129 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "alpha": ALPHA, "beta": BETA},
@@ -570,7 +605,7 @@ def main():
         "sequences": seqinfo,
         "roofline": roof,
         "clocks": clk,
-        "gpu_launches": args.steps * sum(Suite.FUSED_LAUNCHES[s] for s in SEQS),
+        "gpu_launches": args.steps * sum(Suite.FUSED_LAUNCHES[s] for s in seqs),
     }
     if not args.no_e2e:
         line["e2e"] = {"value": world * step_bytes / (e2e_ms / e2e_steps * 1e-3) / 1e9, "unit": "GB/s",
