@@ -209,6 +209,32 @@ kf_status kf_quantize_rows(int64_t m, int64_t n, const float* A, int64_t lda, kf
 kf_status kf_set_matrix_tuning(int warps, int vec, int unroll, int groups, int stages);
 kf_status kf_get_matrix_tuning(int* warps, int* vec, int* unroll, int* groups, int* stages);
 
+/* ------------------------------------------------------------------------
+ * BiCGK for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a library convenience.
+ *
+ * Some callers cannot call cudaMalloc or any allocating routine where they
+ * need BiCGK (a framework that forbids allocation while it records work, a
+ * host whose device memory belongs to another allocator, a C program with
+ * no device allocator).  kf_bicgk_noalloc computes exactly what kf_bicgk
+ * computes for FP32 A (q = A p, s = A^T r, one read of A) but takes no
+ * workspace: its scratch is a fixed array of KF_BICGK_NOALLOC_SCRATCH_BYTES
+ * in the library's device image, present on every GPU that loads the
+ * library until the process exits.  It allocates nothing.
+ *   - Shapes whose scratch would exceed the array (about m, n <= 8192 when
+ *     m = n) return KF_ERR_SHAPE; use kf_bicgk with a workspace for those.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address and caches it; make that first call before any
+ *     stream capture.
+ *   - Each call clears the array's counters on `stream` before its launch.
+ *   - All calls on a device share the array: calls that overlap on the GPU
+ *     (unordered streams, concurrent threads) race.  Order them on one
+ *     stream.
+ * ---------------------------------------------------------------------- */
+#define KF_BICGK_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+kf_status kf_bicgk_noalloc(int64_t m, int64_t n, const float* A, int64_t lda, const float* p,
+                           const float* r, float* q, float* s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ LIB = os.path.join(BUILD, "libkf.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["abi.cu", "matprog.cu", "matprog_f32s.cu", "matprog_f32p.cu", "matprog_lowp.cu",
-           "vecprog.cu", "atax.cu", "quant.cu"]
+           "vecprog.cu", "atax.cu", "quant.cu", "noalloc.cu"]
 HEADERS = ["kf_internal.h", "kf_device.cuh", "matprog_impl.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

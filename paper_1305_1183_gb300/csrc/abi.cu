@@ -44,6 +44,12 @@ MatTune cur_tune() {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 }  // namespace
 
+// Records the calling thread's error message (used by the other C files).
+const char* set_error_message(const std::string& msg) {
+  g_err = msg;
+  return g_err.c_str();
+}
+
 int device_sm_count() {
   static int cache[64] = {0};
   int dev = 0;

@@ -63,6 +63,7 @@ _SIGS = {
     "kf_dot": ([i64, vp, vp, vp, vp, sz, vp], ci),
     "kf_quantize_rows": ([i64, i64, vp, i64, ci, vp, vp, vp], ci),
     "kf_set_matrix_tuning": ([ci, ci, ci, ci, ci], ci),
+    "kf_bicgk_noalloc": ([i64, i64, vp, i64, vp, vp, vp, vp, vp], ci),
     "kf_get_matrix_tuning": ([ctypes.POINTER(ci)] * 5, ci),
 }
 
@@ -238,3 +239,15 @@ def kf_dot(x, y, out, ws, stream=None):
 def kf_quantize_rows(A, fmt, Q, row_scale, stream=None):
     m, n = A.shape
     _ck(lib().kf_quantize_rows(m, n, _p(A), A.stride(0), fmt, _p(Q), _p(row_scale), _st(stream)))
+
+
+# ------------------------------------------------------------------ no workspace
+
+KF_BICGK_NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def kf_bicgk_noalloc(A, p, r, q, s, stream=None):
+    """BiCGK with the library's fixed device scratch instead of a workspace
+    (for callers that cannot allocate); see include/kf.h."""
+    m, n = A.shape
+    _ck(lib().kf_bicgk_noalloc(m, n, _p(A), A.stride(0), _p(p), _p(r), _p(q), _p(s), _st(stream)))
