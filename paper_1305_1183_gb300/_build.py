@@ -16,7 +16,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkf.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["abi.cu", "matprog.cu", "matprog_f32s.cu", "matprog_f32p.cu", "matprog_lowp.cu",
+SOURCES = ["abi.cu", "matprog.cu", "matprog_f32s.cu", "matprog_f32p.cu", "matprog_f32e.cu", "matprog_f32sig.cu",
+           "matprog_bf16.cu", "matprog_e4m3.cu",
            "vecprog.cu", "atax.cu", "quant.cu", "noalloc.cu"]
 HEADERS = ["kf_internal.h", "kf_device.cuh", "matprog_impl.cuh"]
 

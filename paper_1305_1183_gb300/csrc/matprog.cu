@@ -23,7 +23,10 @@ void ensure_registry() {
   std::call_once(g_reg_once, [] {
     mp::register_f32_staged();
     mp::register_f32_plain();
-    mp::register_lowp();
+    mp::register_f32_elem();
+    mp::register_bf16();
+    mp::register_e4m3();
+    mp::register_f32_sigs();
   });
 }
 
@@ -101,35 +104,64 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   }
   MatTune t = tune;
   if (t.warps == 0) {
-    // automatic: the best measured direct-load forms on GB300 (BiCGK 16384^2,
-    // GEMVER/GESUMMV 8192^2): 4 chunks x 2 rows for one matrix, 2 x 4 for two
-    if (P.fmt != FMT_F32) t = MatTune{8, 1, 2, 0, 4};
-    else if (P.nmat == 2) t = MatTune{8, 2, 4, 0, 0};
-    else t = MatTune{8, 4, 2, 0, 0};
+    // automatic: the best measured forms on GB300 (BiCGK 16384^2, GEMVER and
+    // GESUMMV 8192^2): direct 16-byte loads, one chunk per lane, 4 rows per batch
+    if (P.fmt == FMT_BF16) t = MatTune{8, 2, 2, 0, 0};
+    else if (P.fmt == FMT_E4M3) t = MatTune{8, 1, 2, 0, 0};
+    else t = MatTune{8, 1, 4, 0, 0};
   }
   bool staged = vec && t.stages > 0;
   if (!vec) { t.warps = 8; t.vec = 1; t.unroll = 2; staged = false; }
-  auto it = R.find(mp::Key(t.warps, t.vec, t.unroll, nops_k, P.nmat, P.fmt, vec, staged));
+  // op shape of the instance: ops and GEMV results rounded up to a compiled shape
+  int ngemv = 0;
+  for (int k = 0; k < P.nops; ++k) ngemv += P.ops[k].kind == MOP_GEMV;
+  if (ngemv > 2 || P.nrow_res > 2) { *why = "at most two GEMV results per matrix pass"; return -10; }
+  int shape_nops = nops_k, shape_ng = ngemv;
+  if (P.nmat == 2) { shape_nops = nops_k <= 2 && ngemv == 2 ? 2 : 4; shape_ng = 2; }
+  else if (nops_k == 1) shape_ng = ngemv;
+  else if (nops_k == 2) { shape_ng = 1; if (ngemv == 2) { shape_nops = 4; shape_ng = 2; } }
+  // compile-time signature of this fusion, if it is one of the specialised ones
+  int sig = mp::SIG_SPEC;
+  for (int k = 0; k < P.nops; ++k) sig |= mp::sig_op(P.ops[k].kind, P.ops[k].mat) << (3 * k);
+  const bool gemv_order_ok = [&] {  // GEMV results numbered in op order
+    int c = 0;
+    for (int k = 0; k < P.nops; ++k)
+      if (P.ops[k].kind == MOP_GEMV && P.ops[k].res != c++) return false;
+    return true;
+  }();
+  if (!gemv_order_ok) sig = 0;
+  auto find = [&](int w, int v, int u, bool vv, bool st) {
+    if (sig != 0) {
+      for (const auto& kv : R) {
+        const mp::Entry& x = kv.second;
+        if (x.sig == sig && x.nw == w && x.v == v && x.u == u && x.fmt == P.fmt && x.vec == vv && x.staged == st)
+          return R.find(kv.first);
+      }
+    }
+    return R.find(mp::Key(w, v, u, shape_nops, P.nmat, shape_ng, P.fmt, vv, st, 0));
+  };
+  auto it = find(t.warps, t.vec, t.unroll, vec, staged);
   if (it == R.end()) {
     // fall back to the default instance of the same op shape and format
-    const int dv = (P.fmt == FMT_F32) ? 2 : 1;
-    it = R.find(mp::Key(8, dv, 2, nops_k, P.nmat, P.fmt, vec, staged));
-    if (it == R.end()) it = R.find(mp::Key(8, dv, 2, nops_k, P.nmat, P.fmt, vec, !staged));
-    if (it == R.end()) it = R.find(mp::Key(8, 1, 2, nops_k, P.nmat, P.fmt, vec, false));
+    const int dv = (P.fmt == FMT_E4M3) ? 1 : 2;
+    it = find(8, dv, 2, vec, false);
+    if (it == R.end()) it = find(8, 1, 2, vec, false);
+    if (it == R.end()) it = find(8, 1, 2, false, false);
     if (it == R.end()) { *why = "no kernel instance for this op shape"; return -10; }
   }
   const mp::Entry& e = it->second;
   const int ch = fmt_ch(P.fmt);
-  const int64_t sw = 32LL * e.v * ch;
-  const size_t batch = (size_t)P.nmat * e.u * 32 * e.v * 16;
+  const int64_t sw = (int64_t)e.nw * 32 * e.v * ch;               // strip width (columns)
+  const size_t batch = (size_t)P.nmat * e.u * e.nw * 32 * e.v * 16;  // one ring stage (bytes)
+  const int threads = (e.nw + (e.staged ? 1 : 0)) * 32;
   int stages = e.staged ? std::max(1, std::min(MAT_MAXSTAGES, t.stages > 0 ? t.stages : 4)) : 0;
-  size_t smem = (size_t)e.nw * sw * sizeof(float);
+  size_t smem = 0;
   if (e.staged) {
     // keep the ring within the per-block limit
-    while (stages > 1 && (size_t)e.nw * stages * batch > 200 * 1024) --stages;
-    smem = std::max(smem, (size_t)e.nw * stages * batch);
+    while (stages > 1 && (size_t)stages * batch > 200 * 1024) --stages;
+    smem = (size_t)stages * batch;
   }
-  const int occ = occupancy(e.fn, e.nw * 32, smem);
+  const int occ = occupancy(e.fn, threads, smem);
   if (occ < 1) { *why = "kernel does not fit on an SM with this tuning"; return -10; }
 
   // Geometry: strips by the instance's strip width, groups to fill one wave.
@@ -142,12 +174,6 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   G = std::min<int64_t>(G, std::max<int64_t>(1, nrb));
   G = std::min<int64_t>(G, MAT_MAXGROUPS);
   int64_t bpg = nrb > 0 ? (nrb + G - 1) / G : 0;
-  // keep every warp of a block equally busy when that costs no extra wave
-  if (t.groups <= 0 && bpg > 0 && bpg % e.nw != 0) {
-    const int64_t b2 = ((bpg + e.nw - 1) / e.nw) * e.nw;
-    const int64_t g2 = (nrb + b2 - 1) / b2;
-    if (g2 * strips <= slots) bpg = b2;
-  }
   G = nrb > 0 ? (nrb + bpg - 1) / bpg : 1;
   if (strips > 0x7fffffffLL) { *why = "matrix too wide"; return -2; }
   P.n_strips = (int)strips;
@@ -156,7 +182,7 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   P.stages = stages;
   dim3 grid((unsigned)strips, (unsigned)G);
   void* args[] = {&P};
-  cudaError_t err = cudaLaunchKernel(e.fn, grid, dim3(e.nw * 32), args, smem, (cudaStream_t)stream);
+  cudaError_t err = cudaLaunchKernel(e.fn, grid, dim3(threads), args, smem, (cudaStream_t)stream);
   if (err != cudaSuccess) { *why = cudaGetErrorString(err); return -7; }
   return 0;
 }

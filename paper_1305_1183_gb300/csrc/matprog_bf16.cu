@@ -1,0 +1,14 @@
+// Instances of the matrix pass: row-scaled BF16 storage.
+#include "matprog_impl.cuh"
+
+namespace kf {
+namespace mp {
+void register_bf16() {
+  reg_shapes<8, 2, 2, FMT_BF16, true, false>();
+  reg_shapes<8, 2, 2, FMT_BF16, true, true>();
+  reg_shapes<8, 1, 2, FMT_BF16, false, false>();
+  reg_sigs<8, 2, 2, FMT_BF16, true, false>();
+  reg_sigs<8, 2, 2, FMT_BF16, true, true>();
+}
+}  // namespace mp
+}  // namespace kf

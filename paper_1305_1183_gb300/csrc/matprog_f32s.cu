@@ -4,11 +4,9 @@
 namespace kf {
 namespace mp {
 void register_f32_staged() {
-  reg_shapes<8, 2, 2, FMT_F32, true>();
-  reg_shapes<8, 4, 1, FMT_F32, true>();
-  reg_shapes<8, 2, 1, FMT_F32, true>();
-  reg_shapes<8, 1, 2, FMT_F32, true>();
-  reg_shapes<4, 4, 2, FMT_F32, true>();
+  reg_shapes<8, 1, 4, FMT_F32, true, true>();
+  reg_shapes<8, 2, 2, FMT_F32, true, true>();
+  reg_shapes<4, 1, 4, FMT_F32, true, true>();
 }
 }  // namespace mp
 }  // namespace kf

@@ -3,31 +3,34 @@
 // One read of an m x n matrix (or of two same-shaped matrices) serves every
 // fused GER / GEMV / GEMVT call of a fusion.  Kernel schema (the paper's
 // Algorithm 1, Section 3.3.2, re-derived for a row-major layout on sm_103a):
-//   * a block owns a column strip of 32*V 16-byte chunks and a group of
-//     32-row blocks; warps of the block take row blocks round robin;
-//   * "load invariant data": the column vectors that every row of the strip
-//     multiplies (x of GEMV, v of GER) are loaded once into registers;
-//   * "clear outputs of accumulated reductions": the GEMVT column sums live
-//     in registers across all rows the warp visits and are stored once after
-//     the loop (Algorithm 3: s_l accumulated, stored after the loop);
-//   * per row, the tile values pass through the ops in script order while
-//     they are in registers (GER updates them, GEMV reduces them across the
-//     warp with shuffles, GEMVT accumulates them); the updated matrix is
-//     written once if a later kernel or the caller needs it;
+//   * a block owns a column strip and a group of 32-row blocks; its NW
+//     consumer warps sit side by side across the strip (each owns 32*V
+//     16-byte chunks of every row), so the block reads NW*512*V contiguous
+//     bytes of each row it visits -- long sequential runs for HBM;
+//   * "load invariant data": the column vectors that every row multiplies
+//     (x of GEMV, v of GER) are loaded once into each warp's registers;
+//   * "clear outputs of accumulated reductions": GEMVT column sums live in
+//     registers across all rows of the group and are stored once at the end
+//     (Algorithm 3: s_l accumulated, stored after the loop);
+//   * per row, the values pass through the ops in script order while in
+//     registers (GER updates them, GEMV accumulates per-lane row partials,
+//     GEMVT accumulates column sums); an updated matrix is written once;
+//   * row dots: each lane keeps a partial per row of an 8-row quarter,
+//     reduced across the warp once per quarter (23 shuffles), then across
+//     the warps through shared memory once per 32 rows;
 //   * row results are partial per strip, column results partial per group;
 //     the last block of a group (strip) to finish reduces the partials in a
 //     fixed order and applies the linear epilogue (Section 3.2.2, option
 //     (ii)), so results are deterministic, unlike float atomics.
 //
-// Staged form (STAGED = true): a warp's part of a row of the strip is 512*V
-// contiguous bytes, so each warp streams its rows with one-dimensional bulk
-// asynchronous copies (cp.async.bulk, the TMA engine) into its own ring of
-// shared-memory stages, `stages` batches of U rows ahead, with completion
-// counted in bytes on one mbarrier per stage.  Lanes then read their 16-byte
-// chunks from shared memory (conflict free).  Loads in flight no longer
-// depend on registers, which is what keeps HBM busy.  Every wait is bounded
-// (1 s); a warp whose copy never lands records the error word, stops
-// waiting, and the block still takes part in the completion counters.
+// Staged form (STAGED = true): one extra producer warp streams the block's
+// rows with one-dimensional bulk asynchronous copies (cp.async.bulk, the TMA
+// engine; one copy per row and matrix) into a ring of shared-memory stages,
+// `stages` batches of U rows ahead; a "full" mbarrier per stage counts the
+// bytes, an "empty" mbarrier per stage counts the consumer warps that have
+// read it.  Every wait is bounded (1 s): on a timeout the block records the
+// error word, stops waiting, lets its in-flight copies land (bounded) and
+// still takes part in the completion counters.
 //
 // GEMV is not a dense contraction, so there is nothing for the tensor cores
 // here; the bound is HBM bandwidth.
@@ -195,20 +198,73 @@ __device__ __forceinline__ void epilogue(const EpiOut* outs, int nout, const flo
 }
 
 
-template <int NW, int V, int U, int NOPS, int NMAT, int FMT, bool VEC, bool STAGED>
-__global__ void __launch_bounds__(NW * 32)
+// Row dots of 8 rows, each spread over the 32 lanes as per-lane partials
+// d[0..7]: after the call every lane L holds the total of row (L & 7).
+// Two butterfly steps (xor 16, xor 8) add the four lane quarters, then
+// recursive halving over lane bits 2..0 leaves each lane the row its bits
+// select: 23 shuffles per 8 rows, no per-row chain of dependent shuffles.
+__device__ __forceinline__ float reduce8_rows(float (&d)[8], int lane) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] += __shfl_xor_sync(FULL_MASK, d[i], 16);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] += __shfl_xor_sync(FULL_MASK, d[i], 8);
+#pragma unroll
+  for (int off = 4; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const float send = upper ? d[i] : d[i + off];
+      const float keep = upper ? d[i + off] : d[i];
+      d[i] = keep + __shfl_xor_sync(FULL_MASK, send, off);
+    }
+  }
+  return d[0];
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Compile-time op signatures.  A signature fixes the kind and matrix of
+// every op of a fusion (3 bits per op: kind in bits 0-1, matrix in bit 2;
+// bit 12 marks a specialised signature), so the per-row dispatch over the
+// op list folds away.  SIG = 0 keeps the runtime dispatch for any fusion.
+constexpr int SIG_SPEC = 1 << 12;
+constexpr int sig_op(int kind, int mat) { return kind | (mat << 2); }
+constexpr int sig_kind(int sig, int k) { return (sig >> (3 * k)) & 3; }
+constexpr int sig_mat(int sig, int k) { return (sig >> (3 * k + 2)) & 1; }
+constexpr int SIG_GEMV = SIG_SPEC | sig_op(MOP_GEMV, 0);
+constexpr int SIG_GEMVT = SIG_SPEC | sig_op(MOP_GEMVT, 0);
+constexpr int SIG_GER = SIG_SPEC | sig_op(MOP_GER, 0);
+constexpr int SIG_BICGK = SIG_SPEC | sig_op(MOP_GEMV, 0) | (sig_op(MOP_GEMVT, 0) << 3);
+constexpr int SIG_GEMVER1 = SIG_SPEC | sig_op(MOP_GER, 0) | (sig_op(MOP_GER, 0) << 3) | (sig_op(MOP_GEMVT, 0) << 6);
+constexpr int SIG_GESUMMV = SIG_SPEC | sig_op(MOP_GEMV, 0) | (sig_op(MOP_GEMV, 1) << 3);
+
+template <int NW, int V, int U, int NOPS, int NMAT, int NG, int FMT, bool VEC, bool STAGED, int SIG>
+__global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32)
     matprog_kernel(const __grid_constant__ MatProg P) {
   constexpr int CH = FmtT<FMT>::CH;
   constexpr int BYTES = FmtT<FMT>::BYTES;
-  constexpr int W = V * CH;         // values per lane per row
-  constexpr int SW = 32 * W;        // strip width in columns
-  constexpr int SEG = 32 * V * 16;  // bytes of one warp's part of a row
+  constexpr int W = V * CH;          // values per lane per row
+  constexpr int SWW = 32 * W;        // columns of one warp's slice
+  constexpr int SW = NW * SWW;       // strip width in columns
+  constexpr int SEGW = 32 * V * 16;  // bytes of one warp's slice of a row
+  constexpr int SEG = NW * SEGW;     // bytes of the block's part of a row
   constexpr int BATCH = NMAT * U * SEG;
-  constexpr int NB = 32 / U;        // batches per 32-row block
+  constexpr int NB = 32 / U;         // batches per 32-row block
+  static_assert(U == 1 || U == 2 || U == 4 || U == 8, "U must divide 8");
+  constexpr int NGA = NG > 0 ? NG : 1;
+  constexpr bool SPEC = (SIG & SIG_SPEC) != 0;
   extern __shared__ float4 smem4[];
-  float* smem = reinterpret_cast<float*>(smem4);
-  __shared__ __align__(8) uint64_t bars[STAGED ? NW * MAT_MAXSTAGES : 1];
+  __shared__ __align__(8) uint64_t full[STAGED ? MAT_MAXSTAGES : 1];
+  __shared__ __align__(8) uint64_t empty[STAGED ? MAT_MAXSTAGES : 1];
+  __shared__ float red[2][NGA][NW][32];
   __shared__ int s_last[2];
+  __shared__ int s_abort;
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -216,99 +272,101 @@ __global__ void __launch_bounds__(NW * 32)
   const int group = blockIdx.y;
   const int64_t m = P.m, n = P.n;
   const int64_t col0 = (int64_t)strip * SW;
+  const int64_t wcol0 = col0 + (int64_t)min(warp, NW - 1) * SWW;
   const int nops = P.nops;
 
   const int64_t nrb = (m + 31) >> 5;
   const int64_t rb_begin = (int64_t)group * P.blocks_per_group;
   const int64_t rb_end = min(nrb, rb_begin + P.blocks_per_group);
+  const int64_t nbatch = (rb_end > rb_begin ? rb_end - rb_begin : 0) * NB;
 
-  // ---- bulk-copy ring (staged form, full strips only; block-uniform choice)
   const int S = STAGED ? P.stages : 1;
-  const bool ring = STAGED && (col0 + SW <= n);
-  char* myring = reinterpret_cast<char*>(smem4) + (size_t)warp * S * BATCH;
-  uint64_t* mybar = bars + (STAGED ? warp * MAT_MAXSTAGES : 0);
-  const int64_t my_rbs = (rb_end > rb_begin + warp) ? (rb_end - rb_begin - warp + NW - 1) / NW : 0;
-  const int64_t nbatch = my_rbs * NB;
-  bool dead = false;  // warp-uniform: a copy never completed
-  int64_t jdead = 0;  // first batch whose copy never completed
+  const bool ring = STAGED && (col0 + SW <= n);  // block-uniform
+  char* ringp = reinterpret_cast<char*>(smem4);
 
-  auto issue = [&](int64_t jj) {  // lane 0 only: batch jj into stage jj % S
-    const int s = (int)(jj % S);
-    const int64_t rbx = rb_begin + warp + (jj / NB) * NW;
-    const int64_t rowb = (rbx << 5) + (int64_t)(jj % NB) * U;
-    unsigned bytes = 0;
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (rowb + u < m) bytes += NMAT * SEG;
-    mbar_expect_tx(&mybar[s], bytes);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (rowb + u < m) {
-#pragma unroll
-        for (int t = 0; t < NMAT; ++t) {
-          const char* src = static_cast<const char*>(P.A[t]) + ((rowb + u) * P.lda[t] + col0) * BYTES;
-          bulk_g2s(myring + (size_t)s * BATCH + (size_t)(t * U + u) * SEG, src, SEG, &mybar[s]);
-        }
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    if (ring) {
+      for (int s = 0; s < S; ++s) {
+        mbar_init(&full[s], 1);
+        mbar_init(&empty[s], NW);
       }
-    }
-  };
-
-  if (ring) {
-    if (lane == 0) {
-      for (int s = 0; s < S; ++s) mbar_init(&mybar[s], 1);
       fence_mbar_init();
     }
-    __syncwarp();
-    if (lane == 0)
-      for (int64_t j = 0; j < S && j < nbatch; ++j) issue(j);
   }
+  __syncthreads();
 
-  // Invariant column vectors (GER v, GEMV x) or GEMVT accumulators.
-  float cv[NOPS][W];
+  if (STAGED && warp == NW) {
+    // ------------------------------------------------------------ producer
+    if (ring && lane == 0) {
+      int64_t issued = 0;
+      for (int64_t jj = 0; jj < nbatch; ++jj) {
+        const int s = (int)(jj % S);
+        if (jj >= S) {
+          bool ok = false;
+          if (!*(volatile int*)&s_abort) ok = mbar_wait_bounded(&empty[s], (unsigned)(((jj / S) - 1) & 1));
+          if (!ok) {
+            *(volatile int*)&s_abort = 1;
+            if (P.errword != nullptr) atomicOr(P.errword, KF_DEVERR_TIMEOUT);
+            break;
+          }
+        }
+        const int64_t rowb = ((rb_begin + jj / NB) << 5) + (jj % NB) * U;
+        unsigned bytes = 0;
 #pragma unroll
-  for (int k = 0; k < NOPS; ++k) {
-    const int kind = (k < nops) ? P.ops[k].kind : MOP_NONE;
-    const float* src = (kind == MOP_GER || kind == MOP_GEMV) ? P.ops[k].colvec : nullptr;
+        for (int u = 0; u < U; ++u)
+          if (rowb + u < m) bytes += NMAT * SEG;
+        mbar_expect_tx(&full[s], bytes);
 #pragma unroll
-    for (int v = 0; v < V; ++v)
+        for (int u = 0; u < U; ++u) {
+          if (rowb + u < m) {
 #pragma unroll
-      for (int e = 0; e < CH; ++e) {
-        const int64_t c = col0 + coff<CH, V, VEC>(v, e, lane);
-        cv[k][v * CH + e] = (src != nullptr && c < n) ? __ldg(src + c) : 0.f;
+            for (int t = 0; t < NMAT; ++t) {
+              const char* src = static_cast<const char*>(P.A[t]) + ((rowb + u) * P.lda[t] + col0) * BYTES;
+              bulk_g2s(ringp + (size_t)s * BATCH + (size_t)(t * U + u) * SEG, src, SEG, &full[s]);
+            }
+          }
+        }
+        issued = jj + 1;
       }
-  }
-
-  int64_t j = 0;  // batch counter of this warp
-  for (int64_t rb = rb_begin + warp; rb < rb_end; rb += NW) {
-    const int64_t row0 = rb << 5;
-    const bool lane_row_ok = row0 + lane < m;
-    float rv[NOPS];    // per-lane row scalar (GER u, GEMVT y) for row row0+lane
-    float rres[NOPS];  // per-lane GEMV result for row row0+lane
+      if (*(volatile int*)&s_abort) {
+        // let the copies that may still be in flight land before exiting
+        for (int64_t q = issued - S < 0 ? 0 : issued - S; q < issued; ++q)
+          (void)mbar_wait_bounded(&full[q % S], (unsigned)((q / S) & 1));
+      }
+    }
+    __syncwarp();  // reconverge the producer warp before the block barrier below
+  } else {
+    // ------------------------------------------------------------ consumers
+    float cv[NOPS][W];  // invariant column vectors (GER v, GEMV x) or GEMVT sums
 #pragma unroll
     for (int k = 0; k < NOPS; ++k) {
-      const int kind = (k < nops) ? P.ops[k].kind : MOP_NONE;
-      const float* rs = (kind == MOP_GER || kind == MOP_GEMVT) ? P.ops[k].rowvec : nullptr;
-      rv[k] = (rs != nullptr && lane_row_ok) ? __ldg(rs + row0 + lane) : 0.f;
-      rres[k] = 0.f;
-    }
-    float rsc[NMAT];
+      const int kind = SPEC ? sig_kind(SIG, k) : ((k < nops) ? P.ops[k].kind : MOP_NONE);
+      const float* src = (kind == MOP_GER || kind == MOP_GEMV) ? P.ops[k].colvec : nullptr;
 #pragma unroll
-    for (int t = 0; t < NMAT; ++t)
-      rsc[t] = (FMT != FMT_F32 && lane_row_ok) ? __ldg(P.rscale[t] + row0 + lane) : 1.f;
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int e = 0; e < CH; ++e) {
+          const int64_t c = wcol0 + coff<CH, V, VEC>(v, e, lane);
+          cv[k][v * CH + e] = (src != nullptr && c < n) ? __ldg(src + c) : 0.f;
+        }
+    }
+    bool dead = false;  // block-uniform in effect: set from s_abort
 
-#pragma unroll 1
-    for (int r = 0; r < 32; r += U) {
-      float a[NMAT][U][W];
+    auto load_batch = [&](int64_t row0, int r, int64_t jj, float (&a)[NMAT][U][W]) {
       if (ring) {
-        const int s = (int)(j % S);
-        bool ok = dead ? false : mbar_wait_bounded(&mybar[s], (unsigned)((j / S) & 1));
+        const int s = (int)(jj % S);
+        bool ok = false;
+        if (!dead && !*(volatile int*)&s_abort) ok = mbar_wait_bounded(&full[s], (unsigned)((jj / S) & 1));
         ok = __all_sync(FULL_MASK, ok);
         if (!ok && !dead) {
           dead = true;
-          jdead = j;
-          if (lane == 0 && P.errword != nullptr) atomicOr(P.errword, KF_DEVERR_TIMEOUT);
+          if (lane == 0) {
+            *(volatile int*)&s_abort = 1;
+            if (P.errword != nullptr) atomicOr(P.errword, KF_DEVERR_TIMEOUT);
+          }
         }
-        const char* stage = myring + (size_t)s * BATCH;
+        const char* stage = ringp + (size_t)s * BATCH + (size_t)warp * SEGW;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const bool row_ok = !dead && (row0 + r + u < m);
@@ -327,104 +385,146 @@ __global__ void __launch_bounds__(NW * 32)
             }
         }
         __syncwarp();
-        if (lane == 0 && !dead && j + S < nbatch) {
-          fence_proxy_async_smem();
-          issue(j + S);
-        }
-        ++j;
+        if (lane == 0 && !dead) mbar_arrive(&empty[s]);
       } else {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int64_t row = row0 + r + u;
 #pragma unroll
           for (int t = 0; t < NMAT; ++t)
-            load_row<FMT, V, VEC>(P.A[t], P.lda[t], row, row < m, col0, n, lane, a[t][u]);
+            load_row<FMT, V, VEC>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u]);
         }
       }
-      if constexpr (FMT != FMT_F32) {
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-          for (int t = 0; t < NMAT; ++t) {
-            const float s = __shfl_sync(FULL_MASK, rsc[t], r + u);
-#pragma unroll
-            for (int e = 0; e < W; ++e) a[t][u][e] *= s;
-          }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int rr = r + u;
-#pragma unroll
-        for (int k = 0; k < NOPS; ++k) {
-          if (k < nops) {
-            const MatOp& op = P.ops[k];
-            const int kind = op.kind;
-            auto apply = [&](float (&t)[W]) {
-              if (kind == MOP_GER) {
-                const float s = op.alpha * __shfl_sync(FULL_MASK, rv[k], rr);
-#pragma unroll
-                for (int e = 0; e < W; ++e) t[e] = fmaf(s, cv[k][e], t[e]);
-              } else if (kind == MOP_GEMV) {
-                float d0 = 0.f, d1 = 0.f;
-#pragma unroll
-                for (int e = 0; e < W; e += 2) {
-                  d0 = fmaf(t[e], cv[k][e], d0);
-                  d1 = fmaf(t[e + 1], cv[k][e + 1], d1);
-                }
-                const float d = warp_sum(d0 + d1);
-                if (lane == rr) rres[k] = d;
-              } else if (kind == MOP_GEMVT) {
-                const float y = __shfl_sync(FULL_MASK, rv[k], rr);
-#pragma unroll
-                for (int e = 0; e < W; ++e) cv[k][e] = fmaf(t[e], y, cv[k][e]);
-              }
-            };
-            if (NMAT == 1 || op.mat == 0) apply(a[0][u]);
-            else apply(a[NMAT - 1][u]);
-          }
-        }
-        const int64_t row = row0 + rr;
-        if (row < m) {
-#pragma unroll
-          for (int t = 0; t < NMAT; ++t)
-            if (P.Bout[t] != nullptr)
-              store_row<CH, V, VEC>(P.Bout[t], P.ldb[t], row, col0, n, lane, a[t][u]);
-        }
-      }
-    }
-    // Partial row results of this strip, one coalesced store per GEMV.
-#pragma unroll
-    for (int k = 0; k < NOPS; ++k) {
-      if (k < nops && P.ops[k].kind == MOP_GEMV && lane_row_ok)
-        P.rowpart[((int64_t)P.ops[k].res * P.n_strips + strip) * m + row0 + lane] = rres[k];
-    }
-  }
-  if (ring && dead && lane == 0) {
-    // let copies already in flight land before the block's shared memory is reused
-    for (int64_t q = jdead; q < nbatch && q < jdead + S; ++q)
-      (void)mbar_wait_bounded(&mybar[q % S], (unsigned)((q / S) & 1));
-  }
+    };
 
-  // Column partials of this group: combine the warps in a fixed order.
-  // (The staging area aliases the copy ring, so wait for every warp first.)
-  if (P.ncol_res > 0) {
-    __syncthreads();
+    int64_t j = 0;  // batch counter (every consumer warp visits every batch)
+    for (int64_t rb = rb_begin; rb < rb_end; ++rb) {
+      const int64_t row0 = rb << 5;
+      const bool lane_row_ok = row0 + lane < m;
+      float rv[NOPS];  // per-lane row scalar (GER u, GEMVT y) for row row0+lane
+#pragma unroll
+      for (int k = 0; k < NOPS; ++k) {
+        const int kind = SPEC ? sig_kind(SIG, k) : ((k < nops) ? P.ops[k].kind : MOP_NONE);
+        const float* rs = (kind == MOP_GER || kind == MOP_GEMVT) ? P.ops[k].rowvec : nullptr;
+        rv[k] = (rs != nullptr && lane_row_ok) ? __ldg(rs + row0 + lane) : 0.f;
+      }
+      float rsc[NMAT];
+#pragma unroll
+      for (int t = 0; t < NMAT; ++t)
+        rsc[t] = (FMT != FMT_F32 && lane_row_ok) ? __ldg(P.rscale[t] + row0 + lane) : 1.f;
+      float rowdot[NGA];  // this warp's partial of row row0+lane
+
+#pragma unroll 1
+      for (int h = 0; h < 4; ++h) {  // four quarters of 8 rows
+        float dacc[NGA][8];          // per-lane partial dot of each row of the quarter
+#pragma unroll
+        for (int g = 0; g < NGA; ++g)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) dacc[g][i] = 0.f;
+#pragma unroll
+        for (int r16 = 0; r16 < 8; r16 += U) {
+          const int r = h * 8 + r16;
+          float a[NMAT][U][W];
+          load_batch(row0, r, j, a);
+          ++j;
+          if constexpr (FMT != FMT_F32) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+              for (int t = 0; t < NMAT; ++t) {
+                const float sc = __shfl_sync(FULL_MASK, rsc[t], r + u);
+#pragma unroll
+                for (int e = 0; e < W; ++e) a[t][u][e] *= sc;
+              }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int rr = r + u;
+#pragma unroll
+            for (int k = 0; k < NOPS; ++k) {
+              if (SPEC || k < nops) {
+                const MatOp& op = P.ops[k];
+                const int kind = SPEC ? sig_kind(SIG, k) : op.kind;
+                const int opmat = SPEC ? sig_mat(SIG, k) : op.mat;
+                auto apply = [&](float (&t)[W]) {
+                  if (kind == MOP_GER) {
+                    const float sc = op.alpha * __shfl_sync(FULL_MASK, rv[k], rr);
+#pragma unroll
+                    for (int e = 0; e < W; ++e) t[e] = fmaf(sc, cv[k][e], t[e]);
+                  } else if (kind == MOP_GEMV) {
+                    if constexpr (NG > 0) {
+                      float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+                      for (int e = 0; e < W; e += 2) {
+                        d0 = fmaf(t[e], cv[k][e], d0);
+                        d1 = fmaf(t[e + 1], cv[k][e + 1], d1);
+                      }
+                      int slot0;
+                      if constexpr (SPEC) {
+                        int c = 0;
+#pragma unroll
+                        for (int q = 0; q < k; ++q) c += sig_kind(SIG, q) == MOP_GEMV;
+                        slot0 = (c == 0);
+                      } else {
+                        slot0 = (op.res == 0);
+                      }
+                      if (NG == 1 || slot0) dacc[0][r16 + u] += d0 + d1;
+                      else dacc[NGA - 1][r16 + u] += d0 + d1;
+                    }
+                  } else if (kind == MOP_GEMVT) {
+                    const float y = __shfl_sync(FULL_MASK, rv[k], rr);
+#pragma unroll
+                    for (int e = 0; e < W; ++e) cv[k][e] = fmaf(t[e], y, cv[k][e]);
+                  }
+                };
+                if (NMAT == 1 || opmat == 0) apply(a[0][u]);
+                else apply(a[NMAT - 1][u]);
+              }
+            }
+            const int64_t row = row0 + rr;
+            if (row < m) {
+#pragma unroll
+              for (int t = 0; t < NMAT; ++t)
+                if (P.Bout[t] != nullptr)
+                  store_row<CH, V, VEC>(P.Bout[t], P.ldb[t], row, wcol0, n, lane, a[t][u]);
+            }
+          }
+        }
+        if constexpr (NG > 0) {
+#pragma unroll
+          for (int g = 0; g < NGA; ++g) {
+            const float v = reduce8_rows(dacc[g], lane);
+            if ((lane >> 3) == h) rowdot[g] = v;
+          }
+        }
+      }
+      // Row dots across the warps of the strip (fixed warp order), one
+      // coalesced store of the strip's partial per GEMV result.
+      if constexpr (NG > 0) {
+        const int buf = (int)(rb & 1);
+#pragma unroll
+        for (int g = 0; g < NGA; ++g) red[buf][g][warp][lane] = rowdot[g];
+        consumer_sync(NW * 32);
+        if (warp < NGA && warp < P.nrow_res && lane_row_ok) {
+          float sum = 0.f;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) sum += red[buf][warp][w][lane];
+          P.rowpart[((int64_t)warp * P.n_strips + strip) * m + row0 + lane] = sum;
+        }
+      }
+    }
+    // GEMVT: each warp owns its columns; one store of the group's partial.
 #pragma unroll
     for (int k = 0; k < NOPS; ++k) {
-      if (k < nops && P.ops[k].kind == MOP_GEMVT) {
+      if ((SPEC ? sig_kind(SIG, k) : (k < nops ? P.ops[k].kind : 0)) == MOP_GEMVT) {
+        float* part = P.colpart + ((int64_t)P.ops[k].res * P.n_groups + group) * n;
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
-          for (int e = 0; e < CH; ++e) smem[warp * SW + coff<CH, V, VEC>(v, e, lane)] = cv[k][v * CH + e];
-        __syncthreads();
-        for (int c = threadIdx.x; c < SW; c += NW * 32) {
-          float s = 0.f;
-#pragma unroll
-          for (int w = 0; w < NW; ++w) s += smem[w * SW + c];
-          const int64_t col = col0 + c;
-          if (col < n) P.colpart[((int64_t)P.ops[k].res * P.n_groups + group) * n + col] = s;
-        }
-        __syncthreads();
+          for (int e = 0; e < CH; ++e) {
+            const int64_t c = wcol0 + coff<CH, V, VEC>(v, e, lane);
+            if (c < n) part[c] = cv[k][v * CH + e];
+          }
       }
     }
   }
@@ -443,47 +543,92 @@ __global__ void __launch_bounds__(NW * 32)
   __syncthreads();
   if (s_last[0]) {
     __threadfence();
-    for (int c = threadIdx.x; c < SW; c += NW * 32) {
+    // Column results of this strip: sum the groups' partials in group order.
+    // Four adjacent columns per thread and eight loads in flight.
+    const bool v4 = (n & 3) == 0;
+    const int step = v4 ? 4 : 1;
+    for (int c = threadIdx.x * step; c < SW; c += blockDim.x * step) {
       const int64_t col = col0 + c;
       if (col >= n) continue;
-      float raw[NOPS];
+      float raw[4][NOPS];
 #pragma unroll
       for (int q = 0; q < NOPS; ++q) {
-        float s = 0.f;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         if (q < P.ncol_res) {
           const float* part = P.colpart + (int64_t)q * P.n_groups * n + col;
-          for (int g = 0; g < P.n_groups; ++g) s += __ldcg(part + (int64_t)g * n);
+          int g = 0;
+          if (v4) {
+            for (; g + 8 <= P.n_groups; g += 8) {
+              float4 t[8];
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) t[jj] = __ldcg(reinterpret_cast<const float4*>(part + (int64_t)(g + jj) * n));
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) { acc.x += t[jj].x; acc.y += t[jj].y; acc.z += t[jj].z; acc.w += t[jj].w; }
+            }
+            for (; g < P.n_groups; ++g) {
+              const float4 t = __ldcg(reinterpret_cast<const float4*>(part + (int64_t)g * n));
+              acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
+            }
+          } else {
+            for (; g + 8 <= P.n_groups; g += 8) {
+              float t[8];
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) t[jj] = __ldcg(part + (int64_t)(g + jj) * n);
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) acc.x += t[jj];
+            }
+            for (; g < P.n_groups; ++g) acc.x += __ldcg(part + (int64_t)g * n);
+          }
         }
-        raw[q] = s;
+        raw[0][q] = acc.x; raw[1][q] = acc.y; raw[2][q] = acc.z; raw[3][q] = acc.w;
       }
-      epilogue<NOPS>(P.col_out, P.ncol_out, raw, col);
+      for (int e = 0; e < step; ++e)
+        if (col + e < n) epilogue<NOPS>(P.col_out, P.ncol_out, raw[e], col + e);
     }
     if (threadIdx.x == 0) P.counters[strip] = 0u;
   }
   if (s_last[1]) {
     __threadfence();
+    // Row results of this group: sum the strips' partials in strip order.
     const int64_t r0 = rb_begin << 5;
     const int64_t r1 = min(m, rb_end << 5);
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += NW * 32) {
-      float raw[NOPS];
+    const bool v4 = (m & 3) == 0;
+    const int step = v4 ? 4 : 1;
+    for (int64_t i = r0 + threadIdx.x * step; i < r1; i += (int64_t)blockDim.x * step) {
+      float raw[4][NOPS];
 #pragma unroll
       for (int q = 0; q < NOPS; ++q) {
-        float s = 0.f;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         if (q < P.nrow_res) {
           const float* part = P.rowpart + (int64_t)q * P.n_strips * m + i;
           int st = 0;
-          for (; st + 8 <= P.n_strips; st += 8) {
-            float t[8];
+          if (v4) {
+            for (; st + 8 <= P.n_strips; st += 8) {
+              float4 t[8];
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) t[jj] = __ldcg(part + (int64_t)(st + jj) * m);
+              for (int jj = 0; jj < 8; ++jj) t[jj] = __ldcg(reinterpret_cast<const float4*>(part + (int64_t)(st + jj) * m));
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) s += t[jj];
+              for (int jj = 0; jj < 8; ++jj) { acc.x += t[jj].x; acc.y += t[jj].y; acc.z += t[jj].z; acc.w += t[jj].w; }
+            }
+            for (; st < P.n_strips; ++st) {
+              const float4 t = __ldcg(reinterpret_cast<const float4*>(part + (int64_t)st * m));
+              acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
+            }
+          } else {
+            for (; st + 8 <= P.n_strips; st += 8) {
+              float t[8];
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) t[jj] = __ldcg(part + (int64_t)(st + jj) * m);
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) acc.x += t[jj];
+            }
+            for (; st < P.n_strips; ++st) acc.x += __ldcg(part + (int64_t)st * m);
           }
-          for (; st < P.n_strips; ++st) s += __ldcg(part + (int64_t)st * m);
         }
-        raw[q] = s;
+        raw[0][q] = acc.x; raw[1][q] = acc.y; raw[2][q] = acc.z; raw[3][q] = acc.w;
       }
-      epilogue<NOPS>(P.row_out, P.nrow_out, raw, i);
+      for (int e = 0; e < step; ++e)
+        if (i + e < r1) epilogue<NOPS>(P.row_out, P.nrow_out, raw[e], i + e);
     }
     if (threadIdx.x == 0) P.counters[P.n_strips + group] = 0u;
   }
@@ -493,35 +638,55 @@ __global__ void __launch_bounds__(NW * 32)
 
 struct Entry {
   const void* fn;
-  int nw, v, u, nops, nmat, fmt;
+  int nw, v, u, nops, nmat, ng, fmt;
   bool vec, staged;
+  int sig;
 };
 
-// (warps, vec, unroll, nops, nmat, fmt, vec-path, staged)
-using Key = std::tuple<int, int, int, int, int, int, bool, bool>;
+// (warps, vec, unroll, nops, nmat, ngemv, fmt, vec-path, staged, signature)
+using Key = std::tuple<int, int, int, int, int, int, int, bool, bool, int>;
 
 std::map<Key, Entry>& registry();
 
-template <int NW, int V, int U, int NOPS, int NMAT, int FMT, bool VEC, bool STAGED>
+template <int NW, int V, int U, int NOPS, int NMAT, int NG, int FMT, bool VEC, bool STAGED, int SIG = 0>
 void reg() {
-  registry()[Key(NW, V, U, NOPS, NMAT, FMT, VEC, STAGED)] =
-      Entry{(const void*)&matprog_kernel<NW, V, U, NOPS, NMAT, FMT, VEC, STAGED>, NW, V, U, NOPS,
-            NMAT, FMT, VEC, STAGED};
+  registry()[Key(NW, V, U, NOPS, NMAT, NG, FMT, VEC, STAGED, SIG)] =
+      Entry{(const void*)&matprog_kernel<NW, V, U, NOPS, NMAT, NG, FMT, VEC, STAGED, SIG>, NW, V, U,
+            NOPS, NMAT, NG, FMT, VEC, STAGED, SIG};
 }
 
-// the five op shapes: (nops, nmat) = (1,1) (2,1) (4,1) (2,2) (4,2)
-template <int NW, int V, int U, int FMT, bool STAGED>
+// Runtime-dispatch op shapes (ops, matrices, GEMV results):
+//   (1,1,0) GER or GEMVT alone   (1,1,1) GEMV alone       (2,1,1) BiCGK-like
+//   (2,2,2) GESUMMV-like          (4,1,0) GEMVER pass 1    (4,1,1) (4,1,2) (4,2,2) general
+template <int NW, int V, int U, int FMT, bool VEC, bool STAGED>
 void reg_shapes() {
-  reg<NW, V, U, 1, 1, FMT, true, STAGED>();
-  reg<NW, V, U, 2, 1, FMT, true, STAGED>();
-  reg<NW, V, U, 4, 1, FMT, true, STAGED>();
-  reg<NW, V, U, 2, 2, FMT, true, STAGED>();
-  reg<NW, V, U, 4, 2, FMT, true, STAGED>();
+  reg<NW, V, U, 1, 1, 0, FMT, VEC, STAGED>();
+  reg<NW, V, U, 1, 1, 1, FMT, VEC, STAGED>();
+  reg<NW, V, U, 2, 1, 1, FMT, VEC, STAGED>();
+  reg<NW, V, U, 2, 2, 2, FMT, VEC, STAGED>();
+  reg<NW, V, U, 4, 1, 0, FMT, VEC, STAGED>();
+  reg<NW, V, U, 4, 1, 1, FMT, VEC, STAGED>();
+  reg<NW, V, U, 4, 1, 2, FMT, VEC, STAGED>();
+  reg<NW, V, U, 4, 2, 2, FMT, VEC, STAGED>();
+}
+
+// Specialised signatures of the sequences' fusions.
+template <int NW, int V, int U, int FMT, bool VEC, bool STAGED>
+void reg_sigs() {
+  reg<NW, V, U, 1, 1, 1, FMT, VEC, STAGED, SIG_GEMV>();
+  reg<NW, V, U, 1, 1, 0, FMT, VEC, STAGED, SIG_GEMVT>();
+  reg<NW, V, U, 1, 1, 0, FMT, VEC, STAGED, SIG_GER>();
+  reg<NW, V, U, 2, 1, 1, FMT, VEC, STAGED, SIG_BICGK>();
+  reg<NW, V, U, 3, 1, 0, FMT, VEC, STAGED, SIG_GEMVER1>();
+  reg<NW, V, U, 2, 2, 2, FMT, VEC, STAGED, SIG_GESUMMV>();
 }
 
 void register_f32_staged();
 void register_f32_plain();
-void register_lowp();
+void register_f32_elem();
+void register_bf16();
+void register_e4m3();
+void register_f32_sigs();
 
 }  // namespace mp
 }  // namespace kf
