@@ -26,7 +26,7 @@ constexpr int ATAX_MAXSTAGES = 8;
 namespace {
 
 template <int NT, int VA>
-__global__ void __launch_bounds__(NT) atax_rows_kernel(const float* __restrict__ A, int64_t lda, int64_t m,
+__global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const float* __restrict__ A, int64_t lda, int64_t m,
                                                         int64_t n, const float* __restrict__ x,
                                                         float* __restrict__ ypart, int stages,
                                                         int64_t rowcap, unsigned* err) {
@@ -131,7 +131,16 @@ __global__ void __launch_bounds__(256) atax_finish_kernel(const float* __restric
   float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
   if (c4 < n4) {
     const float4* p = reinterpret_cast<const float4*>(ypart) + c4;
-    for (int b = slice; b < nparts; b += 8) {
+    int b = slice;
+    // eight independent loads in flight per step, added in block order
+    for (; b + 7 * 8 < nparts; b += 8 * 8) {
+      float4 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = __ldcg(p + (int64_t)(b + 8 * q) * n4);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { s.x += v[q].x; s.y += v[q].y; s.z += v[q].z; s.w += v[q].w; }
+    }
+    for (; b < nparts; b += 8) {
       const float4 v = __ldcg(p + (int64_t)b * n4);
       s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
     }

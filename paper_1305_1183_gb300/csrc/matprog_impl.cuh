@@ -244,8 +244,13 @@ constexpr int SIG_BICGK = SIG_SPEC | sig_op(MOP_GEMV, 0) | (sig_op(MOP_GEMVT, 0)
 constexpr int SIG_GEMVER1 = SIG_SPEC | sig_op(MOP_GER, 0) | (sig_op(MOP_GER, 0) << 3) | (sig_op(MOP_GEMVT, 0) << 6);
 constexpr int SIG_GESUMMV = SIG_SPEC | sig_op(MOP_GEMV, 0) | (sig_op(MOP_GEMV, 1) << 3);
 
+// Resident blocks per SM asked of the register allocator: the one-chunk
+// FP32 forms are latency bound and need four blocks of eight warps.
+template <int NW, int V, int NMAT, int FMT>
+constexpr int min_blocks() { return (NW == 8 && V == 1 && NMAT == 1 && FMT == FMT_F32) ? 4 : 1; }
+
 template <int NW, int V, int U, int NOPS, int NMAT, int NG, int FMT, bool VEC, bool STAGED, int SIG>
-__global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32)
+__global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, V, NMAT, FMT>()))
     matprog_kernel(const __grid_constant__ MatProg P) {
   constexpr int CH = FmtT<FMT>::CH;
   constexpr int BYTES = FmtT<FMT>::BYTES;
