@@ -210,6 +210,96 @@ kf_status kf_set_matrix_tuning(int warps, int vec, int unroll, int groups, int s
 kf_status kf_get_matrix_tuning(int* warps, int* vec, int* unroll, int* groups, int* stages);
 
 /* ------------------------------------------------------------------------
+ * Scripts and plans (Sections 3.1-3.2: the script of elementary calls, the
+ * data-dependency graph, fusions, their combination and its prediction).
+ *
+ * A script declares variables (vectors of length n, row-major m x n
+ * matrices with leading dimension n, device float scalars), marks inputs
+ * and outputs, and lists calls in order.  Every variable, inputs, outputs
+ * and temporaries alike, is bound to caller-owned device memory at
+ * execution (bindings[var_id]); a fused plan may leave temporaries that
+ * stay on chip unwritten.  Call semantics (BLAS conventions):
+ *   AXPBY  out = a x + b y          ins (x, y)        scalars (a, b)   [AXPY: out = y, b = 1]
+ *   SCAL   out = a x                ins (x)           scalars (a)
+ *   DOT    out = x . y  (scalar)    ins (x, y)
+ *   VADD   out = w + y + z          ins (w, y, z)
+ *   GEMV   out = a A x + b y0       ins (A, x[, y0])  scalars (a, b)   out may not be x
+ *   GEMVT  out = a A^T y + b x0     ins (A, y[, x0])  scalars (a, b)   out may not be y
+ *   GER    out = A + a u v^T        ins (A, u, v)     scalars (a)      out may be A (in place)
+ * Missing scalars default to a = 1 and b = 1 (AXPBY) / b = 1 when y0 or x0
+ * is given, else 0.
+ *
+ * Fusion rules (Section 3.2): calls of one fusion have the same nesting
+ * depth and iteration space (vectors of one length, or matrices of one
+ * shape); no call consumes a reduction result (DOT, GEMV, GEMVT) of the
+ * same fusion, except linear maps (AXPBY, SCAL, VADD) of row or column
+ * results, which run after the last-block barrier; a fusion is convex in
+ * the dependency graph; at most 4 matrix ops over at most 2 matrices and 2
+ * GEMV results per matrix pass; at most 6 input vectors, 4 outputs and 4
+ * dots per vector pass.  Plans are enumerated call by call in script order
+ * (at most max_plans).
+ * ---------------------------------------------------------------------- */
+typedef struct kf_script kf_script;
+typedef struct kf_plan kf_plan;
+
+typedef enum {
+  KF_OP_AXPBY = 0,
+  KF_OP_SCAL = 1,
+  KF_OP_DOT = 2,
+  KF_OP_VADD = 3,
+  KF_OP_GEMV = 4,
+  KF_OP_GEMVT = 5,
+  KF_OP_GER = 6
+} kf_op;
+
+typedef enum {
+  KF_PLAN_UNFUSED = 0,   /* one kernel per call                                   */
+  KF_PLAN_GREEDY = 1,    /* fewest kernels                                        */
+  KF_PLAN_ANALYTIC = 2,  /* least predicted time: bytes / bandwidth + launch cost */
+  KF_PLAN_INDEX = 3      /* the index-th plan of the enumeration                  */
+} kf_plan_mode;
+
+typedef struct {
+  int mode;       /* kf_plan_mode                         */
+  int max_plans;  /* enumeration cap (<= 0: 20000)        */
+  int index;      /* KF_PLAN_INDEX                        */
+} kf_plan_options;
+
+kf_status kf_script_create(kf_script** out);
+void kf_script_destroy(kf_script* s);
+kf_status kf_script_vector(kf_script* s, const char* name, int64_t n, int* var_id);
+kf_status kf_script_matrix(kf_script* s, const char* name, int64_t m, int64_t n, int* var_id);
+kf_status kf_script_scalar(kf_script* s, const char* name, int* var_id);
+kf_status kf_script_input(kf_script* s, int var_id);
+kf_status kf_script_output(kf_script* s, int var_id);
+kf_status kf_script_call(kf_script* s, kf_op op, const int* outs, int n_out, const int* ins, int n_in,
+                         const double* scalars, int n_scalars);
+/* Check shapes and that every read variable is an input or written earlier
+ * (KF_ERR_SHAPE / KF_ERR_UNDEFINED_VAR). */
+kf_status kf_script_validate(const kf_script* s);
+/* Number of legal plans (at most cap); *truncated = 1 when the cap was hit. */
+kf_status kf_plan_count(const kf_script* s, int cap, int* count, int* truncated);
+kf_status kf_plan_build(const kf_script* s, const kf_plan_options* opt, kf_plan** out);
+void kf_plan_destroy(kf_plan* p);
+kf_status kf_plan_workspace_size(const kf_plan* p, size_t* bytes);
+kf_status kf_plan_kernel_count(const kf_plan* p, int* n);
+/* Analytic prediction (microseconds): sum over kernels of bytes moved /
+ * model bandwidth + a fixed launch cost (kf_planner_set_model). */
+kf_status kf_plan_predicted_us(const kf_plan* p, double* us);
+kf_status kf_planner_set_model(double bw_gbs, double launch_us);
+/* Features of a plan for the learned cost model (16 floats). */
+kf_status kf_plan_features(const kf_script* s, const kf_plan* p, float* out, int cap, int* n);
+/* JSON: kernels, their calls and bytes, prediction. */
+kf_status kf_plan_describe(const kf_plan* p, char* buf, size_t cap, size_t* needed);
+/* Enqueue the plan's kernels on `stream`. */
+kf_status kf_plan_execute(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
+                          void* stream);
+/* Synchronous: run once, then time `reps` executions with CUDA events on
+ * `stream`; the median in milliseconds (empirical search, Section 3.2). */
+kf_status kf_plan_time(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
+                       void* stream, int reps, float* median_ms);
+
+/* ------------------------------------------------------------------------
  * BiCGK for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a library convenience.
  *

@@ -50,6 +50,8 @@ const char* set_error_message(const std::string& msg) {
   return g_err.c_str();
 }
 
+MatTune current_matrix_tuning();
+
 int device_sm_count() {
   static int cache[64] = {0};
   int dev = 0;
@@ -61,6 +63,8 @@ int device_sm_count() {
   }
   return cache[dev];
 }
+
+MatTune current_matrix_tuning() { return cur_tune(); }
 
 }  // namespace kf
 

@@ -76,7 +76,8 @@ size_t matprog_workspace_bytes(int64_t m, int64_t n, int nrow_res, int ncol_res,
 // [header (error word) | counters | row partials | column partials].
 int matprog_bind_workspace(MatProg& P, void* ws, size_t bytes) {
   P.errword = ws ? static_cast<unsigned*>(ws) : nullptr;
-  const bool needs_ws = P.nrow_out > 0 || P.ncol_out > 0;
+  // partial sums are written for every reduction, stored or not
+  const bool needs_ws = P.nrow_out > 0 || P.ncol_out > 0 || P.nrow_res > 0 || P.ncol_res > 0;
   if (!needs_ws) return 0;
   const size_t need = matprog_workspace_bytes(P.m, P.n, P.nrow_res, P.ncol_res, P.fmt);
   if (ws == nullptr || bytes < need) return -11;

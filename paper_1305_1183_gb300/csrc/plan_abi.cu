@@ -1,0 +1,373 @@
+// C ABI of scripts and plans (include/kf.h, "Scripts and plans").
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/kf.h"
+#include "kf_internal.h"
+#include "planner.h"
+
+namespace kf {
+const char* set_error_message(const std::string& msg);
+namespace plan {
+void set_model(double bw_bytes_per_s, double launch_us);
+void get_model(double* bw, double* launch_us);
+}  // namespace plan
+}  // namespace kf
+
+struct kf_script {
+  kf::plan::Script s;
+};
+struct kf_plan {
+  kf::plan::Plan p;
+  int nvars = 0;
+};
+
+using namespace kf;
+using namespace kf::plan;
+
+namespace {
+
+kf_status err(kf_status st, const std::string& m) {
+  set_error_message(m);
+  return st;
+}
+
+kf_status add_var(kf_script* sc, const char* name, int kind, int64_t m, int64_t n, int* id) {
+  if (sc == nullptr || id == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  if (m < 0 || n < 0) return err(KF_ERR_INVALID_ARG, "negative size");
+  Var v;
+  v.name = name ? name : ("v" + std::to_string(sc->s.vars.size()));
+  v.kind = kind;
+  v.m = m;
+  v.n = n;
+  sc->s.vars.push_back(v);
+  sc->s.analysed = false;
+  *id = (int)sc->s.vars.size() - 1;
+  return KF_OK;
+}
+
+kf_status ensure_analysed(const kf_script* sc) {
+  auto* s = const_cast<Script*>(&sc->s);
+  if (s->analysed) return KF_OK;
+  std::string e = analyse(*s);
+  if (!e.empty()) {
+    const bool undef = e.find("read before") != std::string::npos;
+    return err(undef ? KF_ERR_UNDEFINED_VAR : KF_ERR_SHAPE, e);
+  }
+  return KF_OK;
+}
+
+std::vector<std::vector<int>> unfused_groups(const Script& s) {
+  std::vector<std::vector<int>> g;
+  for (int c = 0; c < (int)s.calls.size(); ++c) g.push_back({c});
+  return g;
+}
+
+// A plan's workspace: [vector-pass region (header, counter, dot partials) |
+// matrix-pass region (its own header, counters, partials)], so that the
+// partial sums of one kind never land on the counters of the other.
+size_t plan_vec_region() { return (vecprog_workspace_bytes(VP_MAXDOT) + 255) & ~(size_t)255; }
+
+// Bind variable pointers into a copy of a kernel's program and launch it.
+kf_status launch_kernel(const Kernel& K, void* const* bindings, int nb, void* ws, size_t ws_bytes, void* stream,
+                        const MatTune& tune) {
+  if (K.is_mat) {
+    MatProg P = K.mp;
+    for (auto& b : K.bind) {
+      if (b.second < 0 || b.second >= nb || bindings[b.second] == nullptr)
+        return err(KF_ERR_INVALID_ARG, "variable " + std::to_string(b.second) + " is not bound");
+      *reinterpret_cast<void**>(reinterpret_cast<char*>(&P) + (size_t)(uintptr_t)b.first) = bindings[b.second];
+    }
+    // matrix passes use the workspace after the vector passes' region
+    char* wsm = ws ? static_cast<char*>(ws) + plan_vec_region() : nullptr;
+    const size_t wsm_bytes = ws_bytes > plan_vec_region() ? ws_bytes - plan_vec_region() : 0;
+    if (P.nrow_res == 0 && P.ncol_res == 0 && P.nrow_out == 0 && P.ncol_out == 0) {
+      P.errword = nullptr;
+    } else if (matprog_bind_workspace(P, wsm, wsm_bytes) != 0) {
+      return err(KF_ERR_WORKSPACE, "workspace missing or smaller than kf_plan_workspace_size()");
+    }
+    const char* why = nullptr;
+    const int rc = launch_matprog(P, tune, stream, &why);
+    return rc == 0 ? KF_OK : err(rc, why ? why : "launch failed");
+  }
+  VecProg P = K.vp;
+  for (auto& b : K.bind) {
+    if (b.second < 0 || b.second >= nb || bindings[b.second] == nullptr)
+      return err(KF_ERR_INVALID_ARG, "variable " + std::to_string(b.second) + " is not bound");
+    *reinterpret_cast<void**>(reinterpret_cast<char*>(&P) + (size_t)(uintptr_t)b.first) = bindings[b.second];
+  }
+  if (P.ndot > 0) {
+    if (ws == nullptr || ws_bytes < plan_vec_region())
+      return err(KF_ERR_WORKSPACE, "workspace missing or smaller than kf_plan_workspace_size()");
+    P.counter = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + WS_HEADER);
+    P.dotpart = reinterpret_cast<float*>(static_cast<char*>(ws) + WS_HEADER + 256);
+  }
+  P.fp64_final = P.n >= (int64_t(1) << 26);
+  const char* why = nullptr;
+  VecTune t{256, 4, 0};
+  const int rc = launch_vecprog(P, t, stream, &why);
+  return rc == 0 ? KF_OK : err(rc, why ? why : "launch failed");
+}
+
+
+// Name of the program field at byte offset `o` (for plan descriptions).
+std::string field_name(const Kernel& K, size_t o) {
+  auto at = [&](const void* base, const void* f) { return (size_t)((const char*)f - (const char*)base); };
+  if (K.is_mat) {
+    const MatProg& P = K.mp;
+    for (int t = 0; t < 2; ++t) {
+      if (o == at(&P, &P.A[t])) return "A" + std::to_string(t);
+      if (o == at(&P, &P.Bout[t])) return "Bout" + std::to_string(t);
+    }
+    for (int k = 0; k < MAT_MAXOPS; ++k) {
+      if (o == at(&P, &P.ops[k].colvec)) return "op" + std::to_string(k) + ".col";
+      if (o == at(&P, &P.ops[k].rowvec)) return "op" + std::to_string(k) + ".row";
+    }
+    for (int j = 0; j < EPI_MAXOUT; ++j) {
+      if (o == at(&P, &P.row_out[j].dst)) return "rowout" + std::to_string(j) + ".dst";
+      if (o == at(&P, &P.col_out[j].dst)) return "colout" + std::to_string(j) + ".dst";
+      for (int t = 0; t < EPI_MAXTERM; ++t) {
+        if (o == at(&P, &P.row_out[j].ext[t])) return "rowout" + std::to_string(j) + ".ext";
+        if (o == at(&P, &P.col_out[j].ext[t])) return "colout" + std::to_string(j) + ".ext";
+      }
+    }
+    return "?";
+  }
+  const VecProg& P = K.vp;
+  for (int k = 0; k < VP_MAXIN; ++k)
+    if (o == at(&P, &P.in[k])) return "in" + std::to_string(k);
+  for (int k = 0; k < VP_MAXOUT; ++k)
+    if (o == at(&P, &P.out[k])) return "out" + std::to_string(k);
+  for (int k = 0; k < VP_MAXDOT; ++k)
+    if (o == at(&P, &P.dot_out[k])) return "dot" + std::to_string(k);
+  return "?";
+}
+
+}  // namespace
+
+namespace kf {
+MatTune current_matrix_tuning();
+}
+
+extern "C" {
+
+kf_status kf_script_create(kf_script** out) {
+  if (out == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  *out = new (std::nothrow) kf_script();
+  return *out ? KF_OK : err(KF_ERR_NO_MEM, "out of host memory");
+}
+
+void kf_script_destroy(kf_script* s) { delete s; }
+
+kf_status kf_script_vector(kf_script* s, const char* name, int64_t n, int* id) {
+  return add_var(s, name, VK_VECTOR, 1, n, id);
+}
+
+kf_status kf_script_matrix(kf_script* s, const char* name, int64_t m, int64_t n, int* id) {
+  return add_var(s, name, VK_MATRIX, m, n, id);
+}
+
+kf_status kf_script_scalar(kf_script* s, const char* name, int* id) { return add_var(s, name, VK_SCALAR, 1, 1, id); }
+
+kf_status kf_script_input(kf_script* s, int id) {
+  if (s == nullptr || id < 0 || id >= (int)s->s.vars.size()) return err(KF_ERR_INVALID_ARG, "bad variable id");
+  s->s.vars[id].input = true;
+  s->s.analysed = false;
+  return KF_OK;
+}
+
+kf_status kf_script_output(kf_script* s, int id) {
+  if (s == nullptr || id < 0 || id >= (int)s->s.vars.size()) return err(KF_ERR_INVALID_ARG, "bad variable id");
+  s->s.vars[id].output = true;
+  s->s.analysed = false;
+  return KF_OK;
+}
+
+kf_status kf_script_call(kf_script* s, kf_op op, const int* outs, int n_out, const int* ins, int n_in,
+                         const double* scalars, int n_scalars) {
+  if (s == nullptr || (n_out > 0 && outs == nullptr) || (n_in > 0 && ins == nullptr) ||
+      (n_scalars > 0 && scalars == nullptr) || n_scalars > 2 || n_out < 0 || n_in < 0)
+    return err(KF_ERR_INVALID_ARG, "bad call arguments");
+  if ((int)op < 0 || (int)op > OP_GER) return err(KF_ERR_INVALID_ARG, "unknown op");
+  Call c;
+  c.op = (int)op;
+  c.outs.assign(outs, outs + n_out);
+  c.ins.assign(ins, ins + n_in);
+  // defaults: AXPBY (a, b) = (1, 1); SCAL a = 1; GEMV/GEMVT (a, b) = (1, 0 or 1 with y0); GER a = 1
+  c.sc[0] = 1.0;
+  c.sc[1] = (op == KF_OP_AXPBY) ? 1.0 : ((op == KF_OP_GEMV || op == KF_OP_GEMVT) && n_in == 3 ? 1.0 : 0.0);
+  for (int i = 0; i < n_scalars; ++i) c.sc[i] = scalars[i];
+  s->s.calls.push_back(c);
+  s->s.analysed = false;
+  return KF_OK;
+}
+
+kf_status kf_script_validate(const kf_script* s) {
+  if (s == nullptr) return err(KF_ERR_INVALID_ARG, "null script");
+  return ensure_analysed(s);
+}
+
+kf_status kf_plan_count(const kf_script* s, int cap, int* count, int* truncated) {
+  if (s == nullptr || count == nullptr || cap <= 0) return err(KF_ERR_INVALID_ARG, "bad arguments");
+  kf_status st = ensure_analysed(s);
+  if (st != KF_OK) return st;
+  std::vector<std::vector<std::vector<int>>> all;
+  bool tr = false;
+  enumerate(s->s, (size_t)cap, &all, &tr);
+  *count = (int)all.size();
+  if (truncated) *truncated = tr ? 1 : 0;
+  return KF_OK;
+}
+
+kf_status kf_plan_build(const kf_script* s, const kf_plan_options* opt, kf_plan** out) {
+  if (s == nullptr || out == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  kf_status st = ensure_analysed(s);
+  if (st != KF_OK) return st;
+  const int mode = opt ? opt->mode : KF_PLAN_ANALYTIC;
+  const int cap = (opt && opt->max_plans > 0) ? opt->max_plans : 20000;
+  std::vector<std::vector<int>> chosen;
+  if (mode == KF_PLAN_UNFUSED) {
+    chosen = unfused_groups(s->s);
+  } else {
+    std::vector<std::vector<std::vector<int>>> all;
+    bool tr = false;
+    enumerate(s->s, (size_t)cap, &all, &tr);
+    if (all.empty()) return err(KF_ERR_UNSUPPORTED, "no legal plan");
+    if (mode == KF_PLAN_INDEX) {
+      const int idx = opt ? opt->index : 0;
+      if (idx < 0 || idx >= (int)all.size()) return err(KF_ERR_INVALID_ARG, "plan index out of range");
+      chosen = all[idx];
+    } else if (mode == KF_PLAN_GREEDY) {
+      // fewest kernels (fuse as much as legal); first such plan in enumeration order
+      size_t best = all[0].size();
+      chosen = all[0];
+      for (auto& g : all)
+        if (g.size() < best) { best = g.size(); chosen = g; }
+    } else if (mode == KF_PLAN_ANALYTIC) {
+      double best = 1e300;
+      for (auto& g : all) {
+        Plan p;
+        if (!make_plan(s->s, g, &p).empty()) continue;
+        if (p.predicted_us < best * (1.0 - 1e-9)) { best = p.predicted_us; chosen = g; }
+      }
+      if (chosen.empty()) return err(KF_ERR_UNSUPPORTED, "no buildable plan");
+    } else {
+      return err(KF_ERR_INVALID_ARG, "unknown plan mode");
+    }
+  }
+  auto* pl = new (std::nothrow) kf_plan();
+  if (pl == nullptr) return err(KF_ERR_NO_MEM, "out of host memory");
+  std::string e = make_plan(s->s, chosen, &pl->p);
+  if (!e.empty()) {
+    delete pl;
+    return err(KF_ERR_UNSUPPORTED, e);
+  }
+  pl->nvars = (int)s->s.vars.size();
+  *out = pl;
+  return KF_OK;
+}
+
+void kf_plan_destroy(kf_plan* p) { delete p; }
+
+kf_status kf_plan_workspace_size(const kf_plan* p, size_t* bytes) {
+  if (p == nullptr || bytes == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  *bytes = p->p.ws_bytes;
+  return KF_OK;
+}
+
+kf_status kf_plan_kernel_count(const kf_plan* p, int* n) {
+  if (p == nullptr || n == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  *n = (int)p->p.kernels.size();
+  return KF_OK;
+}
+
+kf_status kf_plan_predicted_us(const kf_plan* p, double* us) {
+  if (p == nullptr || us == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  *us = p->p.predicted_us;
+  return KF_OK;
+}
+
+kf_status kf_plan_features(const kf_script* s, const kf_plan* p, float* out, int cap, int* n) {
+  if (s == nullptr || p == nullptr || out == nullptr || n == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  std::vector<float> f;
+  features(s->s, p->p, &f);
+  *n = (int)f.size();
+  if (cap < (int)f.size()) return err(KF_ERR_INVALID_ARG, "feature buffer too small");
+  std::copy(f.begin(), f.end(), out);
+  return KF_OK;
+}
+
+kf_status kf_plan_describe(const kf_plan* p, char* buf, size_t cap, size_t* needed) {
+  if (p == nullptr) return err(KF_ERR_INVALID_ARG, "null plan");
+  std::ostringstream o;
+  o << "{\"predicted_us\":" << p->p.predicted_us << ",\"bytes\":" << p->p.bytes << ",\"kernels\":[";
+  for (size_t i = 0; i < p->p.kernels.size(); ++i) {
+    const Kernel& K = p->p.kernels[i];
+    o << (i ? "," : "") << "{\"kind\":\"" << (K.is_mat ? "matrix" : "vector") << "\",\"calls\":[";
+    for (size_t j = 0; j < K.calls.size(); ++j) o << (j ? "," : "") << K.calls[j];
+    o << "],\"bytes\":" << K.bytes << ",\"m\":" << K.m << ",\"n\":" << K.n << ",\"bind\":[";
+    for (size_t j = 0; j < K.bind.size(); ++j)
+      o << (j ? "," : "") << "[\"" << field_name(K, (size_t)(uintptr_t)K.bind[j].first) << "\"," << K.bind[j].second << "]";
+    o << "]}";
+  }
+  o << "]}";
+  const std::string str = o.str();
+  if (needed) *needed = str.size() + 1;
+  if (buf != nullptr && cap > 0) {
+    const size_t k = std::min(cap - 1, str.size());
+    std::memcpy(buf, str.data(), k);
+    buf[k] = 0;
+  }
+  return KF_OK;
+}
+
+kf_status kf_plan_execute(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
+                          void* stream) {
+  if (p == nullptr || (n_bindings > 0 && bindings == nullptr)) return err(KF_ERR_INVALID_ARG, "null argument");
+  if (n_bindings < p->nvars) return err(KF_ERR_INVALID_ARG, "every script variable needs a binding");
+  const MatTune tune = current_matrix_tuning();
+  for (const Kernel& K : p->p.kernels) {
+    kf_status st = launch_kernel(K, bindings, n_bindings, ws, ws_bytes, stream, tune);
+    if (st != KF_OK) return st;
+  }
+  return KF_OK;
+}
+
+kf_status kf_plan_time(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
+                       void* stream, int reps, float* median_ms) {
+  if (p == nullptr || median_ms == nullptr || reps <= 0) return err(KF_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+    return err(KF_ERR_CUDA, "cudaEventCreate failed");
+  kf_status rc = kf_plan_execute(p, bindings, n_bindings, ws, ws_bytes, stream);  // warm up
+  std::vector<float> t;
+  for (int r = 0; r < reps && rc == KF_OK; ++r) {
+    cudaEventRecord(a, st);
+    rc = kf_plan_execute(p, bindings, n_bindings, ws, ws_bytes, stream);
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess) rc = err(KF_ERR_CUDA, "timing failed");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    t.push_back(ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != KF_OK) return rc;
+  std::sort(t.begin(), t.end());
+  *median_ms = t[t.size() / 2];
+  return KF_OK;
+}
+
+kf_status kf_planner_set_model(double bw_gbs, double launch_us) {
+  if (bw_gbs <= 0 || launch_us < 0) return err(KF_ERR_INVALID_ARG, "bandwidth must be positive");
+  set_model(bw_gbs * 1e9, launch_us);
+  return KF_OK;
+}
+
+}  // extern "C"

@@ -111,7 +111,9 @@ __global__ void __launch_bounds__(256) vecprog_kernel(const __grid_constant__ Ve
       if (d < ndot) acc[d] += lin1<NIN>(P.P[d], xs, nin) * lin1<NIN>(P.Q[d], xs, nin);
   }
 
-  if constexpr (NDOT > 0) {
+  // the finishing step only when this launch has dot products (the
+  // instance may have room for more than it was given)
+  if (NDOT > 0 && ndot > 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 0; d < NDOT; ++d) {
@@ -179,7 +181,9 @@ __global__ void __launch_bounds__(256) vecprog_scalar_kernel(const __grid_consta
     for (int d = 0; d < NDOT; ++d)
       if (d < ndot) acc[d] += lin1<NIN>(P.P[d], xs, nin) * lin1<NIN>(P.Q[d], xs, nin);
   }
-  if constexpr (NDOT > 0) {
+  // the finishing step only when this launch has dot products (the
+  // instance may have room for more than it was given)
+  if (NDOT > 0 && ndot > 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 0; d < NDOT; ++d) {

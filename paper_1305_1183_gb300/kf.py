@@ -64,6 +64,26 @@ _SIGS = {
     "kf_quantize_rows": ([i64, i64, vp, i64, ci, vp, vp, vp], ci),
     "kf_set_matrix_tuning": ([ci, ci, ci, ci, ci], ci),
     "kf_bicgk_noalloc": ([i64, i64, vp, i64, vp, vp, vp, vp, vp], ci),
+    "kf_script_create": ([ctypes.POINTER(vp)], ci),
+    "kf_script_destroy": ([vp], None),
+    "kf_script_vector": ([vp, ctypes.c_char_p, i64, ctypes.POINTER(ci)], ci),
+    "kf_script_matrix": ([vp, ctypes.c_char_p, i64, i64, ctypes.POINTER(ci)], ci),
+    "kf_script_scalar": ([vp, ctypes.c_char_p, ctypes.POINTER(ci)], ci),
+    "kf_script_input": ([vp, ci], ci),
+    "kf_script_output": ([vp, ci], ci),
+    "kf_script_call": ([vp, ci, ctypes.POINTER(ci), ci, ctypes.POINTER(ci), ci, ctypes.POINTER(ctypes.c_double), ci], ci),
+    "kf_script_validate": ([vp], ci),
+    "kf_plan_count": ([vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
+    "kf_plan_build": ([vp, ctypes.POINTER(ci * 3), ctypes.POINTER(vp)], ci),
+    "kf_plan_destroy": ([vp], None),
+    "kf_plan_workspace_size": ([vp, ctypes.POINTER(sz)], ci),
+    "kf_plan_kernel_count": ([vp, ctypes.POINTER(ci)], ci),
+    "kf_plan_predicted_us": ([vp, ctypes.POINTER(ctypes.c_double)], ci),
+    "kf_planner_set_model": ([ctypes.c_double, ctypes.c_double], ci),
+    "kf_plan_features": ([vp, vp, ctypes.POINTER(ctypes.c_float), ci, ctypes.POINTER(ci)], ci),
+    "kf_plan_describe": ([vp, ctypes.c_char_p, sz, ctypes.POINTER(sz)], ci),
+    "kf_plan_execute": ([vp, ctypes.POINTER(vp), ci, vp, sz, vp], ci),
+    "kf_plan_time": ([vp, ctypes.POINTER(vp), ci, vp, sz, vp, ci, ctypes.POINTER(ctypes.c_float)], ci),
     "kf_get_matrix_tuning": ([ctypes.POINTER(ci)] * 5, ci),
 }
 
@@ -251,3 +271,134 @@ def kf_bicgk_noalloc(A, p, r, q, s, stream=None):
     (for callers that cannot allocate); see include/kf.h."""
     m, n = A.shape
     _ck(lib().kf_bicgk_noalloc(m, n, _p(A), A.stride(0), _p(p), _p(r), _p(q), _p(s), _st(stream)))
+
+
+# ------------------------------------------------------------------ scripts and plans
+
+KF_OP_AXPBY, KF_OP_SCAL, KF_OP_DOT, KF_OP_VADD, KF_OP_GEMV, KF_OP_GEMVT, KF_OP_GER = range(7)
+OPS = {"AXPBY": 0, "SCAL": 1, "DOT": 2, "VADD": 3, "GEMV": 4, "GEMVT": 5, "GER": 6}
+KF_PLAN_UNFUSED, KF_PLAN_GREEDY, KF_PLAN_ANALYTIC, KF_PLAN_INDEX = range(4)
+
+
+class Script:
+    """A script of elementary calls (kf_script_* entry points)."""
+
+    def __init__(self):
+        h = vp()
+        _ck(lib().kf_script_create(ctypes.byref(h)))
+        self.h = h
+        self.ids = {}
+        self.kinds = {}
+        self.shapes = {}
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.kf_script_destroy(self.h)
+            self.h = None
+
+    def vector(self, name, n):
+        i = ci(0)
+        _ck(lib().kf_script_vector(self.h, name.encode(), n, ctypes.byref(i)))
+        self.ids[name] = i.value; self.kinds[name] = "v"; self.shapes[name] = (n,)
+        return i.value
+
+    def matrix(self, name, m, n):
+        i = ci(0)
+        _ck(lib().kf_script_matrix(self.h, name.encode(), m, n, ctypes.byref(i)))
+        self.ids[name] = i.value; self.kinds[name] = "m"; self.shapes[name] = (m, n)
+        return i.value
+
+    def scalar(self, name):
+        i = ci(0)
+        _ck(lib().kf_script_scalar(self.h, name.encode(), ctypes.byref(i)))
+        self.ids[name] = i.value; self.kinds[name] = "s"; self.shapes[name] = (1,)
+        return i.value
+
+    def input(self, *names):
+        for nm in names:
+            _ck(lib().kf_script_input(self.h, self.ids[nm]))
+
+    def output(self, *names):
+        for nm in names:
+            _ck(lib().kf_script_output(self.h, self.ids[nm]))
+
+    def call(self, op, outs, ins, scalars=()):
+        o = (ci * len(outs))(*[self.ids[x] for x in outs])
+        i = (ci * len(ins))(*[self.ids[x] for x in ins])
+        s = (ctypes.c_double * max(1, len(scalars)))(*scalars)
+        _ck(lib().kf_script_call(self.h, OPS[op], o, len(outs), i, len(ins), s, len(scalars)))
+
+    def validate(self):
+        _ck(lib().kf_script_validate(self.h))
+
+    def count_plans(self, cap=20000):
+        c, t = ci(0), ci(0)
+        _ck(lib().kf_plan_count(self.h, cap, ctypes.byref(c), ctypes.byref(t)))
+        return c.value, bool(t.value)
+
+    def plan(self, mode=KF_PLAN_ANALYTIC, index=0, max_plans=0):
+        opt = (ci * 3)(mode, max_plans, index)
+        h = vp()
+        _ck(lib().kf_plan_build(self.h, ctypes.byref(opt), ctypes.byref(h)))
+        return Plan(h, self)
+
+
+class Plan:
+    def __init__(self, h, script):
+        self.h = h
+        self.script = script
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.kf_plan_destroy(self.h)
+            self.h = None
+
+    def workspace_size(self):
+        b = sz(0)
+        _ck(lib().kf_plan_workspace_size(self.h, ctypes.byref(b)))
+        return b.value
+
+    def kernel_count(self):
+        n = ci(0)
+        _ck(lib().kf_plan_kernel_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def predicted_us(self):
+        d = ctypes.c_double(0)
+        _ck(lib().kf_plan_predicted_us(self.h, ctypes.byref(d)))
+        return d.value
+
+    def features(self):
+        buf = (ctypes.c_float * 64)()
+        n = ci(0)
+        _ck(lib().kf_plan_features(self.script.h, self.h, buf, 64, ctypes.byref(n)))
+        return list(buf[:n.value])
+
+    def describe(self):
+        need = sz(0)
+        _ck(lib().kf_plan_describe(self.h, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _ck(lib().kf_plan_describe(self.h, buf, need.value, ctypes.byref(need)))
+        import json
+        return json.loads(buf.value.decode())
+
+    def _bind(self, bindings):
+        nv = len(self.script.ids)
+        arr = (vp * nv)()
+        for name, t in bindings.items():
+            arr[self.script.ids[name]] = _p(t)
+        return arr, nv
+
+    def execute(self, bindings, ws, stream=None):
+        arr, nv = self._bind(bindings)
+        _ck(lib().kf_plan_execute(self.h, arr, nv, _p(ws), _nb(ws), _st(stream)))
+
+    def time(self, bindings, ws, reps=5, stream=None):
+        arr, nv = self._bind(bindings)
+        ms = ctypes.c_float(0)
+        _ck(lib().kf_plan_time(self.h, arr, nv, _p(ws), _nb(ws), _st(stream), reps, ctypes.byref(ms)))
+        return ms.value
+
+
+def kf_planner_set_model(bw_gbs, launch_us):
+    _ck(lib().kf_planner_set_model(bw_gbs, launch_us))

@@ -1,0 +1,196 @@
+"""Planner host logic (no GPU): dependency analysis, fusion legality, plan
+enumeration and the analytic choice, on the canonical scripts of Table 1.
+
+The expected fusions follow from the rules of Section 3.2: calls that share
+data and have the same nesting depth fuse; a reduction result (DOT, GEMV,
+GEMVT) is never consumed in the kernel that computes it, except by a linear
+epilogue map after the last-block barrier.
+"""
+
+import pytest
+
+ALPHA, BETA = 1.5, 1.2
+
+
+@pytest.fixture(scope="module")
+def kf():
+    from paper_1305_1183_gb300 import _build, kf as K
+    _build.build()
+    K.lib()
+    return K
+
+
+def bicgk(kf, m=64, n=48):
+    s = kf.Script()
+    s.matrix("A", m, n); s.vector("p", n); s.vector("r", m); s.vector("q", m); s.vector("s", n)
+    s.input("A", "p", "r"); s.output("q", "s")
+    s.call("GEMV", ["q"], ["A", "p"], [1.0, 0.0])
+    s.call("GEMVT", ["s"], ["A", "r"], [1.0, 0.0])
+    return s
+
+
+def gemver(kf, n=40):
+    s = kf.Script()
+    s.matrix("A", n, n); s.matrix("B", n, n)
+    for v in ("u1", "v1", "u2", "v2", "y", "z", "x", "w", "t"):
+        s.vector(v, n)
+    s.input("A", "u1", "v1", "u2", "v2", "y", "z"); s.output("B", "x", "w")
+    s.call("GER", ["B"], ["A", "u1", "v1"], [1.0])
+    s.call("GER", ["B"], ["B", "u2", "v2"], [1.0])
+    s.call("GEMVT", ["t"], ["B", "y"], [1.0, 0.0])
+    s.call("AXPBY", ["x"], ["t", "z"], [BETA, 1.0])
+    s.call("GEMV", ["w"], ["B", "x"], [ALPHA, 0.0])
+    return s
+
+
+def gesummv(kf, n=40):
+    s = kf.Script()
+    s.matrix("A", n, n); s.matrix("B", n, n)
+    for v in ("x", "y", "t1", "t2"):
+        s.vector(v, n)
+    s.input("A", "B", "x"); s.output("y")
+    s.call("GEMV", ["t1"], ["A", "x"], [ALPHA, 0.0])
+    s.call("GEMV", ["t2"], ["B", "x"], [BETA, 0.0])
+    s.call("AXPBY", ["y"], ["t1", "t2"], [1.0, 1.0])
+    return s
+
+
+def atax(kf, n=40):
+    s = kf.Script()
+    s.matrix("A", n, n); s.vector("x", n); s.vector("t", n); s.vector("y", n)
+    s.input("A", "x"); s.output("y")
+    s.call("GEMV", ["t"], ["A", "x"], [1.0, 0.0])
+    s.call("GEMVT", ["y"], ["A", "t"], [1.0, 0.0])
+    return s
+
+
+def axpydot(kf, n=1000):
+    s = kf.Script()
+    for v in ("w", "v", "u", "z"):
+        s.vector(v, n)
+    s.scalar("r")
+    s.input("w", "v", "u"); s.output("z", "r")
+    s.call("AXPBY", ["z"], ["w", "v"], [1.0, -ALPHA])
+    s.call("DOT", ["r"], ["z", "u"])
+    return s
+
+
+def waxpby(kf, n=1000):
+    s = kf.Script()
+    for v in ("x", "y", "t", "w"):
+        s.vector(v, n)
+    s.input("x", "y"); s.output("w")
+    s.call("SCAL", ["t"], ["x"], [ALPHA])
+    s.call("AXPBY", ["w"], ["y", "t"], [BETA, 1.0])
+    return s
+
+
+@pytest.mark.parametrize("name,nplans,fused_kernels", [
+    ("bicgk", 2, 1), ("gemver", None, 2), ("gesummv", None, 1), ("atax", 1, 2),
+    ("axpydot", 2, 1), ("waxpby", 2, 1)])
+def test_canonical_scripts(kf, name, nplans, fused_kernels):
+    s = globals()[name](kf)
+    s.validate()
+    count, trunc = s.count_plans()
+    assert not trunc
+    if nplans is not None:
+        assert count == nplans
+    ncalls = len(s.shapes) and None
+    unf = s.plan(kf.KF_PLAN_UNFUSED)
+    p = s.plan(kf.KF_PLAN_ANALYTIC)
+    assert p.kernel_count() == fused_kernels
+    assert p.predicted_us() <= unf.predicted_us() + 1e-9
+    g = s.plan(kf.KF_PLAN_GREEDY)
+    assert g.kernel_count() <= p.kernel_count()
+    d = p.describe()
+    assert len(d["kernels"]) == fused_kernels
+    assert sum(len(k["calls"]) for k in d["kernels"]) == unf.kernel_count()
+    assert len(p.features()) == 16
+    assert ncalls is None
+
+
+def test_gemver_fusion_shape(kf):
+    """GEMVER: {GER, GER, GEMVT, AXPBY epilogue} then {GEMV} (w needs all of x)."""
+    d = gemver(kf).plan(kf.KF_PLAN_ANALYTIC).describe()
+    assert [k["calls"] for k in d["kernels"]] == [[0, 1, 2, 3], [4]]
+    assert [k["kind"] for k in d["kernels"]] == ["matrix", "matrix"]
+    # bytes: A read, B written; then B read (vectors small)
+    n = 40
+    assert abs(d["bytes"] - (3 * 4 * n * n + 4 * n * 9)) < 4 * n * 2
+
+
+def test_gesummv_epilogue_and_bytes(kf):
+    d = gesummv(kf).plan(kf.KF_PLAN_ANALYTIC).describe()
+    assert [k["calls"] for k in d["kernels"]] == [[0, 1, 2]]
+    n = 40
+    assert d["bytes"] == 4 * (2 * n * n + 2 * n)
+
+
+def test_errors(kf):
+    s = kf.Script()
+    s.vector("x", 10); s.vector("y", 10); s.vector("z", 11)
+    s.input("x")
+    s.call("AXPBY", ["z"], ["x", "y"])
+    with pytest.raises(kf.KFError) as e:
+        s.validate()
+    assert e.value.status == -2                 # shape
+    s = kf.Script()
+    s.vector("x", 10); s.vector("y", 10); s.vector("z", 10)
+    s.input("x")
+    s.call("AXPBY", ["z"], ["x", "y"])
+    with pytest.raises(kf.KFError) as e:
+        s.validate()
+    assert e.value.status == -6                 # y read before written
+    s = kf.Script()
+    s.matrix("A", 8, 8); s.vector("x", 8)
+    s.input("A", "x")
+    s.call("GEMV", ["x"], ["A", "x"])
+    with pytest.raises(kf.KFError):
+        s.validate()                            # GEMV may not overwrite its x
+
+
+def test_dependencies_respected(kf):
+    """AXPY in place then DOT of the old value: the DOT must run first
+    (write-after-read edge); in one vector pass both see per-element order."""
+    s = kf.Script()
+    for v in ("x", "y"):
+        s.vector(v, 100)
+    s.scalar("d1"); s.scalar("d2")
+    s.input("x", "y"); s.output("y", "d1", "d2")
+    s.call("DOT", ["d1"], ["x", "y"])
+    s.call("AXPBY", ["y"], ["x", "y"], [2.0, 1.0])
+    s.call("DOT", ["d2"], ["x", "y"])
+    count, _ = s.count_plans()
+    assert count >= 2
+    p = s.plan(kf.KF_PLAN_ANALYTIC)
+    assert p.kernel_count() == 1
+
+
+def test_reduction_results_not_consumed_in_kernel(kf):
+    """A GEMV result feeding a GEMVT (ATAX) or a DOT of a map of it never
+    shares a kernel with its producer."""
+    s = kf.Script()
+    s.matrix("A", 16, 16)
+    for v in ("x", "t", "u"):
+        s.vector(v, 16)
+    s.scalar("d")
+    s.input("A", "x"); s.output("d")
+    s.call("GEMV", ["t"], ["A", "x"])
+    s.call("SCAL", ["u"], ["t"], [3.0])
+    s.call("DOT", ["d"], ["u", "x"])
+    for i in range(s.count_plans()[0]):
+        d = s.plan(kf.KF_PLAN_INDEX, index=i).describe()
+        for k in d["kernels"]:
+            assert not (0 in k["calls"] and 2 in k["calls"])
+
+
+def test_enumeration_cap(kf):
+    s = kf.Script()
+    for v in range(8):
+        s.vector(f"v{v}", 64)
+    s.input("v0", "v1")
+    for i in range(2, 8):
+        s.call("AXPBY", [f"v{i}"], [f"v{i - 1}", f"v{i - 2}"], [0.5, 0.25])
+    s.output("v7")
+    c, t = s.count_plans(cap=10)
+    assert c == 10 and t
