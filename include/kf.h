@@ -300,6 +300,46 @@ kf_status kf_plan_time(const kf_plan* p, void* const* bindings, int n_bindings, 
                        void* stream, int reps, float* median_ms);
 
 /* ------------------------------------------------------------------------
+ * Batched BiCGK / GESUMMV: many independent instances of uneven sizes in one
+ * persistent launch (not in the paper; its persistent-thread remark is in
+ * Section 4.2).  Each instance is described by device pointers:
+ *   BiCGK   : y = A x (q = A p), s = A^T r        (B unused, alpha/beta unused)
+ *   GESUMMV : y = alpha A x + beta B x             (r, s unused)
+ * with A (and B) m x n, leading dimension lda >= n (any alignment).  The
+ * host tables (descriptors, tiles sorted largest first) live in the batch
+ * object; kf_batched_upload copies them into the caller's workspace
+ * (synchronous), after which kf_batched_launch may be enqueued or captured
+ * any number of times: its work queue and per-instance counters reset
+ * themselves.  band_rows (a multiple of 32; 0 = 128) is the tile height.
+ * Each instance's result equals the same instance batched alone (fixed
+ * reduction order per instance).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int64_t m, n, lda;
+  const float* A;
+  const float* B;
+  const float* x;
+  const float* r;
+  float* y;
+  float* s;
+  float alpha, beta;
+} kf_batch_desc;
+
+typedef struct kf_batched kf_batched;
+
+kf_status kf_batched_create(kf_seq seq, const kf_batch_desc* descs, int count, int band_rows, kf_batched** out);
+void kf_batched_destroy(kf_batched* b);
+kf_status kf_batched_workspace_size(const kf_batched* b, size_t* bytes);
+/* Tiles of one launch and its algorithmic bytes (matrices once, vectors once). */
+kf_status kf_batched_info(const kf_batched* b, int* ntiles, double* bytes);
+kf_status kf_batched_upload(const kf_batched* b, void* ws, size_t ws_bytes, void* stream);
+kf_status kf_batched_launch(const kf_batched* b, void* ws, size_t ws_bytes, void* stream);
+/* Capture one launch into a CUDA graph (cudaGraphExec_t returned as void*). */
+kf_status kf_batched_graph_create(const kf_batched* b, void* ws, size_t ws_bytes, void** graph_exec);
+kf_status kf_batched_graph_launch(void* graph_exec, void* stream);
+void kf_batched_graph_destroy(void* graph_exec);
+
+/* ------------------------------------------------------------------------
  * BiCGK for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a library convenience.
  *

@@ -64,6 +64,15 @@ _SIGS = {
     "kf_quantize_rows": ([i64, i64, vp, i64, ci, vp, vp, vp], ci),
     "kf_set_matrix_tuning": ([ci, ci, ci, ci, ci], ci),
     "kf_bicgk_noalloc": ([i64, i64, vp, i64, vp, vp, vp, vp, vp], ci),
+    "kf_batched_create": ([ci, vp, ci, ci, ctypes.POINTER(vp)], ci),
+    "kf_batched_destroy": ([vp], None),
+    "kf_batched_workspace_size": ([vp, ctypes.POINTER(sz)], ci),
+    "kf_batched_info": ([vp, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_double)], ci),
+    "kf_batched_upload": ([vp, vp, sz, vp], ci),
+    "kf_batched_launch": ([vp, vp, sz, vp], ci),
+    "kf_batched_graph_create": ([vp, vp, sz, ctypes.POINTER(vp)], ci),
+    "kf_batched_graph_launch": ([vp, vp], ci),
+    "kf_batched_graph_destroy": ([vp], None),
     "kf_script_create": ([ctypes.POINTER(vp)], ci),
     "kf_script_destroy": ([vp], None),
     "kf_script_vector": ([vp, ctypes.c_char_p, i64, ctypes.POINTER(ci)], ci),
@@ -402,3 +411,58 @@ class Plan:
 
 def kf_planner_set_model(bw_gbs, launch_us):
     _ck(lib().kf_planner_set_model(bw_gbs, launch_us))
+
+
+# ------------------------------------------------------------------ batched
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("m", i64), ("n", i64), ("lda", i64), ("A", vp), ("B", vp), ("x", vp), ("r", vp),
+                ("y", vp), ("s", vp), ("alpha", f32), ("beta", f32)]
+
+
+class Batched:
+    """kf_batched_* handle: `descs` is a list of dicts with m, n, lda and
+    device pointers A, B, x, r, y, s (ints or tensors), alpha, beta."""
+
+    def __init__(self, seq, descs, band_rows=0):
+        arr = (BatchDesc * max(1, len(descs)))()
+        for i, d in enumerate(descs):
+            arr[i] = BatchDesc(d["m"], d["n"], d.get("lda", d["n"]), _p(d.get("A")), _p(d.get("B")),
+                               _p(d.get("x")), _p(d.get("r")), _p(d.get("y")), _p(d.get("s")),
+                               d.get("alpha", 1.0), d.get("beta", 0.0))
+        h = vp()
+        _ck(lib().kf_batched_create(seq, ctypes.cast(arr, vp), len(descs), band_rows, ctypes.byref(h)))
+        self.h = h
+        self.graph = None
+
+    def __del__(self):
+        if getattr(self, "graph", None) and _lib is not None:
+            _lib.kf_batched_graph_destroy(self.graph)
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.kf_batched_destroy(self.h)
+
+    def workspace_size(self):
+        b = sz(0)
+        _ck(lib().kf_batched_workspace_size(self.h, ctypes.byref(b)))
+        return b.value
+
+    def info(self):
+        t, b = ci(0), ctypes.c_double(0)
+        _ck(lib().kf_batched_info(self.h, ctypes.byref(t), ctypes.byref(b)))
+        return t.value, b.value
+
+    def upload(self, ws, stream=None):
+        _ck(lib().kf_batched_upload(self.h, _p(ws), _nb(ws), _st(stream)))
+
+    def launch(self, ws, stream=None):
+        _ck(lib().kf_batched_launch(self.h, _p(ws), _nb(ws), _st(stream)))
+
+    def capture(self, ws):
+        g = vp()
+        _ck(lib().kf_batched_graph_create(self.h, _p(ws), _nb(ws), ctypes.byref(g)))
+        self.graph = g
+        return g
+
+    def replay(self, stream=None):
+        _ck(lib().kf_batched_graph_launch(self.graph, _st(stream)))
