@@ -289,6 +289,11 @@ kf_status kf_plan_predicted_us(const kf_plan* p, double* us);
 kf_status kf_planner_set_model(double bw_gbs, double launch_us);
 /* Features of a plan for the learned cost model (16 floats). */
 kf_status kf_plan_features(const kf_script* s, const kf_plan* p, float* out, int cap, int* n);
+/* For every enumerated plan (at most cap, in KF_PLAN_INDEX order): its 16
+ * features (feats: cap x 16), analytic prediction and kernel count (any
+ * output may be NULL). */
+kf_status kf_plan_enumerate_info(const kf_script* s, int cap, float* feats, double* pred_us, int* kernels,
+                                 int* count);
 /* JSON: kernels, their calls and bytes, prediction. */
 kf_status kf_plan_describe(const kf_plan* p, char* buf, size_t cap, size_t* needed);
 /* Enqueue the plan's kernels on `stream`. */
@@ -298,6 +303,29 @@ kf_status kf_plan_execute(const kf_plan* p, void* const* bindings, int n_binding
  * `stream`; the median in milliseconds (empirical search, Section 3.2). */
 kf_status kf_plan_time(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
                        void* stream, int reps, float* median_ms);
+
+/* ------------------------------------------------------------------------
+ * Autotuning (Section 3.2: block size and serial iterations are part of a
+ * fusion implementation; routines are benchmarked once per architecture).
+ * kf_autotune_plan runs, for every kernel of the plan on the bound data,
+ * each compiled implementation that fits its op shape (warps, 16-byte chunks
+ * per lane, rows per batch, direct loads or a bulk-copy ring of depth 2..4;
+ * for vector passes rows in flight and grid size) `reps` times and stores
+ * the fastest in a process-wide tuning cache keyed by op signature, storage
+ * format and size class (powers of two of m and n).  Automatic launches
+ * (every entry point, unless kf_set_matrix_tuning fixed a tuning) consult
+ * the cache.  Synchronous; it writes the plan's outputs and in-place
+ * operands.  *tuned_ms / *auto_ms: sum over kernels of the best median and
+ * of the median with the tuning the cache had before.  The cache can be
+ * saved and loaded (text, keyed by device name and SM count; entries for
+ * another device are ignored).
+ * ---------------------------------------------------------------------- */
+kf_status kf_autotune_plan(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
+                           void* stream, int reps, float* tuned_ms, float* auto_ms);
+kf_status kf_tune_cache_clear(void);
+kf_status kf_tune_cache_entries(int* n);
+kf_status kf_tune_cache_save(const char* path);
+kf_status kf_tune_cache_load(const char* path, int* loaded);
 
 /* ------------------------------------------------------------------------
  * Batched BiCGK / GESUMMV: many independent instances of uneven sizes in one
@@ -334,10 +362,37 @@ kf_status kf_batched_workspace_size(const kf_batched* b, size_t* bytes);
 kf_status kf_batched_info(const kf_batched* b, int* ntiles, double* bytes);
 kf_status kf_batched_upload(const kf_batched* b, void* ws, size_t ws_bytes, void* stream);
 kf_status kf_batched_launch(const kf_batched* b, void* ws, size_t ws_bytes, void* stream);
+/* Autotuned tile height: each candidate band height (32..512 rows) is
+ * uploaded into `ws` and timed `reps` times (synchronous); the workspace
+ * must hold the largest candidate (kf_batched_workspace_bound). */
+kf_status kf_batched_workspace_bound(kf_seq seq, const kf_batch_desc* descs, int count, size_t* bytes);
+kf_status kf_batched_autotune(kf_seq seq, const kf_batch_desc* descs, int count, void* ws, size_t ws_bytes,
+                              void* stream, int reps, int* best_band_rows, float* best_ms);
 /* Capture one launch into a CUDA graph (cudaGraphExec_t returned as void*). */
 kf_status kf_batched_graph_create(const kf_batched* b, void* ws, size_t ws_bytes, void** graph_exec);
 kf_status kf_batched_graph_launch(void* graph_exec, void* stream);
 void kf_batched_graph_destroy(void* graph_exec);
+
+/* ------------------------------------------------------------------------
+ * Learned cost model (not in the paper, whose predictor is the additive
+ * one of Section 3.2): a 3-layer perceptron with ReLU activations
+ *   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), f = W3 h2 + b3,
+ * 64 hidden units, d_in <= 32 inputs, trained with the mean squared error
+ * on log plan time and Adam (Kingma and Ba 2015, Algorithm 1).  Parameters
+ * are one caller-owned device FP32 array: W1 (64 x d_in, row major), b1
+ * (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1).  X is batch x d_in row
+ * major.  Gradients are summed over blocks in a fixed order.
+ * ---------------------------------------------------------------------- */
+kf_status kf_mlp_param_count(int d_in, int hidden, int* count);
+kf_status kf_mlp_workspace_size(int d_in, int hidden, int batch, size_t* bytes);
+kf_status kf_mlp_forward(const float* params, int d_in, int hidden, const float* X, int batch, float* out,
+                         void* stream);
+/* *loss (device float, may be NULL) = mean (f - y)^2; grad = dL/dparams. */
+kf_status kf_mlp_loss_grad(const float* params, int d_in, int hidden, const float* X, const float* y, int batch,
+                           float* grad, float* loss, void* ws, size_t ws_bytes, void* stream);
+/* One Adam step (step counts from 1) on params with moments m, v. */
+kf_status kf_mlp_adam(float* params, const float* grad, float* m, float* v, int count, int step, float lr, float b1,
+                      float b2, float eps, void* stream);
 
 /* ------------------------------------------------------------------------
  * BiCGK for callers that cannot allocate device memory.  The paper has no

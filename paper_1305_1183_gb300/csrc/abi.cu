@@ -138,7 +138,7 @@ kf_status run_vec(VecProg& P, void* ws, size_t ws_bytes, void* stream) {
   }
   P.fp64_final = P.n >= (int64_t(1) << 26);
   const char* why = nullptr;
-  VecTune t{256, 4, 0};
+  VecTune t{0, 0, 0};  // automatic (tuning cache or defaults)
   return from_launch(launch_vecprog(P, t, stream, &why), why);
 }
 

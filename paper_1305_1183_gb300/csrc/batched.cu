@@ -396,4 +396,63 @@ void kf_batched_graph_destroy(void* graph_exec) {
   if (graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)graph_exec);
 }
 
+
+// Tile height for a batch: every candidate band height is uploaded into the
+// workspace and launched `reps` times; the fastest median wins.  The
+// workspace must hold the largest candidate (kf_batched_workspace_bound).
+static const int kBandCandidates[] = {32, 64, 128, 256, 512};
+
+kf_status kf_batched_workspace_bound(kf_seq seq, const kf_batch_desc* descs, int count, size_t* bytes) {
+  if (bytes == nullptr) { set_error_message("null argument"); return KF_ERR_INVALID_ARG; }
+  size_t mx = 0;
+  for (int br : kBandCandidates) {
+    kf_batched* b = nullptr;
+    kf_status st = kf_batched_create(seq, descs, count, br, &b);
+    if (st != KF_OK) return st;
+    mx = std::max(mx, b->total);
+    kf_batched_destroy(b);
+  }
+  *bytes = mx;
+  return KF_OK;
+}
+
+kf_status kf_batched_autotune(kf_seq seq, const kf_batch_desc* descs, int count, void* ws, size_t ws_bytes,
+                              void* stream, int reps, int* best_band_rows, float* best_ms) {
+  if (best_band_rows == nullptr || reps <= 0) { set_error_message("bad arguments"); return KF_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t a, e;
+  cudaEventCreate(&a);
+  cudaEventCreate(&e);
+  float bm = 1e30f;
+  int bb = 128;
+  kf_status rc = KF_OK;
+  for (int br : kBandCandidates) {
+    kf_batched* b = nullptr;
+    rc = kf_batched_create(seq, descs, count, br, &b);
+    if (rc != KF_OK) break;
+    rc = kf_batched_upload(b, ws, ws_bytes, stream);
+    std::vector<float> v;
+    if (rc == KF_OK) rc = kf_batched_launch(b, ws, ws_bytes, stream);
+    for (int r = 0; r < reps && rc == KF_OK; ++r) {
+      cudaEventRecord(a, st);
+      rc = kf_batched_launch(b, ws, ws_bytes, stream);
+      cudaEventRecord(e, st);
+      cudaEventSynchronize(e);
+      float x = 0.f;
+      cudaEventElapsedTime(&x, a, e);
+      v.push_back(x);
+    }
+    kf_batched_destroy(b);
+    if (rc != KF_OK) break;
+    std::sort(v.begin(), v.end());
+    if (!v.empty() && v[v.size() / 2] < bm * 0.999f) { bm = v[v.size() / 2]; bb = br; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(e);
+  if (rc != KF_OK) return rc;
+  *best_band_rows = bb;
+  if (best_ms) *best_ms = bm;
+  return KF_OK;
+}
+
 }  // extern "C"

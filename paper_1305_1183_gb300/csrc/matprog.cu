@@ -3,6 +3,8 @@
 // sizes the grid to one wave of resident blocks, and binds the workspace.
 #include <algorithm>
 #include <map>
+#include <string>
+#include <vector>
 #include <mutex>
 #include <tuple>
 
@@ -60,6 +62,75 @@ int occupancy(const void* fn, int threads, size_t smem) {
   return occ;
 }
 
+// ---------------------------------------------------------------- tuning cache
+// Best tuning per (op signature or op shape, storage format, size class),
+// filled by the autotuner, read by automatic launches.
+std::mutex g_cache_mu;
+std::map<std::string, MatTune> g_mat_cache;
+std::map<std::string, VecTune> g_vec_cache;
+
+int log2_class(int64_t v) {
+  int b = 0;
+  while (b < 62 && (int64_t(1) << (b + 1)) <= v) ++b;
+  return b;
+}
+
+}  // namespace
+
+std::string mat_cache_key(const MatProg& P, int sig, int shape_nops, int shape_ng) {
+  return "mat " + std::to_string(sig) + " " + std::to_string(shape_nops) + " " + std::to_string(P.nmat) + " " +
+         std::to_string(shape_ng) + " " + std::to_string(P.fmt) + " " + std::to_string(log2_class(P.m)) + " " +
+         std::to_string(log2_class(P.n));
+}
+
+std::string vec_cache_key(const VecProg& P) {
+  return "vec " + std::to_string(P.nin) + " " + std::to_string(P.nout) + " " + std::to_string(P.ndot) + " " +
+         std::to_string(log2_class(P.n));
+}
+
+bool tune_cache_get_mat(const std::string& k, MatTune* t) {
+  std::lock_guard<std::mutex> g(g_cache_mu);
+  auto it = g_mat_cache.find(k);
+  if (it == g_mat_cache.end()) return false;
+  *t = it->second;
+  return true;
+}
+void tune_cache_put_mat(const std::string& k, const MatTune& t) {
+  std::lock_guard<std::mutex> g(g_cache_mu);
+  g_mat_cache[k] = t;
+}
+bool tune_cache_get_vec(const std::string& k, VecTune* t) {
+  std::lock_guard<std::mutex> g(g_cache_mu);
+  auto it = g_vec_cache.find(k);
+  if (it == g_vec_cache.end()) return false;
+  *t = it->second;
+  return true;
+}
+void tune_cache_put_vec(const std::string& k, const VecTune& t) {
+  std::lock_guard<std::mutex> g(g_cache_mu);
+  g_vec_cache[k] = t;
+}
+void tune_cache_clear() {
+  std::lock_guard<std::mutex> g(g_cache_mu);
+  g_mat_cache.clear();
+  g_vec_cache.clear();
+}
+void tune_cache_dump(std::vector<std::string>* lines) {
+  std::lock_guard<std::mutex> g(g_cache_mu);
+  for (auto& kv : g_mat_cache)
+    lines->push_back(kv.first + " : " + std::to_string(kv.second.warps) + " " + std::to_string(kv.second.vec) + " " +
+                     std::to_string(kv.second.unroll) + " " + std::to_string(kv.second.groups) + " " +
+                     std::to_string(kv.second.stages));
+  for (auto& kv : g_vec_cache)
+    lines->push_back(kv.first + " : " + std::to_string(kv.second.threads) + " " + std::to_string(kv.second.unroll) +
+                     " " + std::to_string(kv.second.blocks));
+}
+size_t tune_cache_size() {
+  std::lock_guard<std::mutex> g(g_cache_mu);
+  return g_mat_cache.size() + g_vec_cache.size();
+}
+
+namespace {
 }  // namespace
 
 size_t matprog_workspace_bytes(int64_t m, int64_t n, int nrow_res, int ncol_res, int fmt) {
@@ -93,6 +164,27 @@ int matprog_bind_workspace(MatProg& P, void* ws, size_t bytes) {
   return 0;
 }
 
+// Op signature (0 when the GEMV results are not numbered in op order) and
+// the compiled op shape a fusion maps to.
+void op_shape(const MatProg& P, int* sig, int* shape_nops, int* shape_ng, int* ngemv_out) {
+  int ngemv = 0;
+  for (int k = 0; k < P.nops; ++k) ngemv += P.ops[k].kind == MOP_GEMV;
+  const int nops_k = pick_nops(P.nops);
+  int sn = nops_k, sg = ngemv;
+  if (P.nmat == 2) { sn = nops_k <= 2 && ngemv == 2 ? 2 : 4; sg = 2; }
+  else if (nops_k == 1) sg = ngemv;
+  else if (nops_k == 2) { sg = 1; if (ngemv == 2) { sn = 4; sg = 2; } }
+  int sg2 = mp::SIG_SPEC;
+  for (int k = 0; k < P.nops; ++k) sg2 |= mp::sig_op(P.ops[k].kind, P.ops[k].mat) << (3 * k);
+  int c = 0;
+  for (int k = 0; k < P.nops; ++k)
+    if (P.ops[k].kind == MOP_GEMV && P.ops[k].res != c++) sg2 = 0;
+  *sig = sg2;
+  *shape_nops = sn;
+  *shape_ng = sg;
+  *ngemv_out = ngemv;
+}
+
 int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** why) {
   ensure_registry();
   auto& R = mp::registry();
@@ -104,33 +196,22 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
     if (P.Bout[t] != nullptr && (!aligned16(P.Bout[t]) || ((P.ldb[t] * 4) & 15) != 0)) vec = false;
   }
   MatTune t = tune;
+  // op shape of the instance and its compile-time signature
+  int sig = 0, shape_nops = 0, shape_ng = 0, ngemv = 0;
+  op_shape(P, &sig, &shape_nops, &shape_ng, &ngemv);
+  if (ngemv > 2 || P.nrow_res > 2) { *why = "at most two GEMV results per matrix pass"; return -10; }
   if (t.warps == 0) {
-    // automatic: the best measured forms on GB300 (BiCGK 16384^2, GEMVER and
-    // GESUMMV 8192^2): direct 16-byte loads, one chunk per lane, 4 rows per batch
-    if (P.fmt == FMT_BF16) t = MatTune{8, 2, 2, 0, 0};
-    else if (P.fmt == FMT_E4M3) t = MatTune{8, 1, 2, 0, 0};
-    else t = MatTune{8, 1, 4, 0, 0};
+    // automatic: the tuning cache, else the best measured forms on GB300
+    // (BiCGK 16384^2, GEMVER and GESUMMV 8192^2): direct 16-byte loads,
+    // one chunk per lane, 4 rows per batch
+    if (!tune_cache_get_mat(mat_cache_key(P, sig, shape_nops, shape_ng), &t)) {
+      if (P.fmt == FMT_BF16) t = MatTune{8, 2, 2, 0, 0};
+      else if (P.fmt == FMT_E4M3) t = MatTune{8, 1, 2, 0, 0};
+      else t = MatTune{8, 1, 4, 0, 0};
+    }
   }
   bool staged = vec && t.stages > 0;
   if (!vec) { t.warps = 8; t.vec = 1; t.unroll = 2; staged = false; }
-  // op shape of the instance: ops and GEMV results rounded up to a compiled shape
-  int ngemv = 0;
-  for (int k = 0; k < P.nops; ++k) ngemv += P.ops[k].kind == MOP_GEMV;
-  if (ngemv > 2 || P.nrow_res > 2) { *why = "at most two GEMV results per matrix pass"; return -10; }
-  int shape_nops = nops_k, shape_ng = ngemv;
-  if (P.nmat == 2) { shape_nops = nops_k <= 2 && ngemv == 2 ? 2 : 4; shape_ng = 2; }
-  else if (nops_k == 1) shape_ng = ngemv;
-  else if (nops_k == 2) { shape_ng = 1; if (ngemv == 2) { shape_nops = 4; shape_ng = 2; } }
-  // compile-time signature of this fusion, if it is one of the specialised ones
-  int sig = mp::SIG_SPEC;
-  for (int k = 0; k < P.nops; ++k) sig |= mp::sig_op(P.ops[k].kind, P.ops[k].mat) << (3 * k);
-  const bool gemv_order_ok = [&] {  // GEMV results numbered in op order
-    int c = 0;
-    for (int k = 0; k < P.nops; ++k)
-      if (P.ops[k].kind == MOP_GEMV && P.ops[k].res != c++) return false;
-    return true;
-  }();
-  if (!gemv_order_ok) sig = 0;
   auto find = [&](int w, int v, int u, bool vv, bool st) {
     if (sig != 0) {
       for (const auto& kv : R) {
@@ -185,6 +266,73 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   void* args[] = {&P};
   cudaError_t err = cudaLaunchKernel(e.fn, grid, dim3(threads), args, smem, (cudaStream_t)stream);
   if (err != cudaSuccess) { *why = cudaGetErrorString(err); return -7; }
+  return 0;
+}
+
+
+// Empirical search over the compiled instances that fit P's op shape:
+// every (warps, chunks, rows per batch, direct or staged with ring depth
+// 2/3/4) is launched `reps` times after one warm-up and the median event
+// time kept; the best goes to the tuning cache.  Synchronous; P must be
+// bound (pointers and workspace).  In-place operands are overwritten.
+int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* best_ms, float* auto_ms) {
+  ensure_registry();
+  auto& R = mp::registry();
+  int sig = 0, shape_nops = 0, shape_ng = 0, ngemv = 0;
+  op_shape(P, &sig, &shape_nops, &shape_ng, &ngemv);
+  std::vector<MatTune> cands;
+  for (auto& kv : R) {
+    const mp::Entry& e = kv.second;
+    if (e.fmt != P.fmt || !e.vec) continue;
+    const bool sig_match = e.sig == sig;
+    const bool shape_match = e.sig == 0 && e.nops == shape_nops && e.nmat == P.nmat && e.ng == shape_ng;
+    if (!sig_match && !shape_match) continue;
+    if (e.staged) {
+      for (int st : {2, 3, 4}) cands.push_back(MatTune{e.nw, e.v, e.u, 0, st});
+    } else {
+      cands.push_back(MatTune{e.nw, e.v, e.u, 0, 0});
+    }
+  }
+  if (cands.empty()) return -10;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  auto time_one = [&](const MatTune& t, float* ms) -> int {
+    const char* why = nullptr;
+    int rc = launch_matprog(P, t, stream, &why);
+    if (rc != 0) return rc;
+    std::vector<float> v;
+    for (int r = 0; r < reps; ++r) {
+      cudaEventRecord(a, st);
+      rc = launch_matprog(P, t, stream, &why);
+      cudaEventRecord(b, st);
+      cudaEventSynchronize(b);
+      float x = 0.f;
+      cudaEventElapsedTime(&x, a, b);
+      v.push_back(x);
+      if (rc != 0) return rc;
+    }
+    std::sort(v.begin(), v.end());
+    *ms = v[v.size() / 2];
+    return 0;
+  };
+  float bm = 1e30f;
+  MatTune bt = cands[0];
+  for (const MatTune& t : cands) {
+    float ms = 0.f;
+    if (time_one(t, &ms) != 0) continue;
+    if (ms < bm * 0.999f) { bm = ms; bt = t; }
+  }
+  float am = 0.f;
+  time_one(MatTune{0, 0, 0, 0, 0}, &am);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (bm >= 1e29f) return -7;
+  tune_cache_put_mat(mat_cache_key(P, sig, shape_nops, shape_ng), bt);
+  *best = bt;
+  *best_ms = bm;
+  if (auto_ms) *auto_ms = am;
   return 0;
 }
 

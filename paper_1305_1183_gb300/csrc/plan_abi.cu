@@ -2,7 +2,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -13,6 +15,13 @@
 
 namespace kf {
 const char* set_error_message(const std::string& msg);
+int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* best_ms, float* auto_ms);
+int autotune_vecprog(VecProg& P, void* stream, int reps, VecTune* best, float* best_ms, float* auto_ms);
+void tune_cache_clear();
+void tune_cache_dump(std::vector<std::string>* lines);
+size_t tune_cache_size();
+void tune_cache_put_mat(const std::string& k, const MatTune& t);
+void tune_cache_put_vec(const std::string& k, const VecTune& t);
 namespace plan {
 void set_model(double bw_bytes_per_s, double launch_us);
 void get_model(double* bw, double* launch_us);
@@ -109,7 +118,7 @@ kf_status launch_kernel(const Kernel& K, void* const* bindings, int nb, void* ws
   }
   P.fp64_final = P.n >= (int64_t(1) << 26);
   const char* why = nullptr;
-  VecTune t{256, 4, 0};
+  VecTune t{0, 0, 0};  // automatic (tuning cache or defaults)
   const int rc = launch_vecprog(P, t, stream, &why);
   return rc == 0 ? KF_OK : err(rc, why ? why : "launch failed");
 }
@@ -367,6 +376,145 @@ kf_status kf_plan_time(const kf_plan* p, void* const* bindings, int n_bindings, 
 kf_status kf_planner_set_model(double bw_gbs, double launch_us) {
   if (bw_gbs <= 0 || launch_us < 0) return err(KF_ERR_INVALID_ARG, "bandwidth must be positive");
   set_model(bw_gbs * 1e9, launch_us);
+  return KF_OK;
+}
+
+
+kf_status kf_autotune_plan(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
+                           void* stream, int reps, float* tuned_ms, float* auto_ms) {
+  if (p == nullptr || reps <= 0 || (n_bindings > 0 && bindings == nullptr)) return err(KF_ERR_INVALID_ARG, "bad arguments");
+  if (n_bindings < p->nvars) return err(KF_ERR_INVALID_ARG, "every script variable needs a binding");
+  float tsum = 0.f, asum = 0.f;
+  for (const Kernel& K : p->p.kernels) {
+    float bm = 0.f, am = 0.f;
+    if (K.is_mat) {
+      MatProg P = K.mp;
+      for (auto& b : K.bind) {
+        if (b.second < 0 || b.second >= n_bindings || bindings[b.second] == nullptr)
+          return err(KF_ERR_INVALID_ARG, "variable " + std::to_string(b.second) + " is not bound");
+        *reinterpret_cast<void**>(reinterpret_cast<char*>(&P) + (size_t)(uintptr_t)b.first) = bindings[b.second];
+      }
+      char* wsm = ws ? static_cast<char*>(ws) + plan_vec_region() : nullptr;
+      const size_t wsm_bytes = ws_bytes > plan_vec_region() ? ws_bytes - plan_vec_region() : 0;
+      if ((P.nrow_res || P.ncol_res || P.nrow_out || P.ncol_out) && matprog_bind_workspace(P, wsm, wsm_bytes) != 0)
+        return err(KF_ERR_WORKSPACE, "workspace missing or smaller than kf_plan_workspace_size()");
+      MatTune best{};
+      const int rc = autotune_matprog(P, stream, reps, &best, &bm, &am);
+      if (rc != 0) return err(rc, "autotune failed");
+    } else {
+      VecProg P = K.vp;
+      for (auto& b : K.bind) {
+        if (b.second < 0 || b.second >= n_bindings || bindings[b.second] == nullptr)
+          return err(KF_ERR_INVALID_ARG, "variable " + std::to_string(b.second) + " is not bound");
+        *reinterpret_cast<void**>(reinterpret_cast<char*>(&P) + (size_t)(uintptr_t)b.first) = bindings[b.second];
+      }
+      if (P.ndot > 0) {
+        if (ws == nullptr || ws_bytes < plan_vec_region()) return err(KF_ERR_WORKSPACE, "workspace too small");
+        P.counter = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + WS_HEADER);
+        P.dotpart = reinterpret_cast<float*>(static_cast<char*>(ws) + WS_HEADER + 256);
+      }
+      P.fp64_final = P.n >= (int64_t(1) << 26);
+      VecTune best{};
+      const int rc = autotune_vecprog(P, stream, reps, &best, &bm, &am);
+      if (rc != 0) return err(rc, "autotune failed");
+    }
+    tsum += bm;
+    asum += am;
+  }
+  if (tuned_ms) *tuned_ms = tsum;
+  if (auto_ms) *auto_ms = asum;
+  return KF_OK;
+}
+
+kf_status kf_tune_cache_clear(void) {
+  tune_cache_clear();
+  return KF_OK;
+}
+
+kf_status kf_tune_cache_entries(int* n) {
+  if (n == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  *n = (int)tune_cache_size();
+  return KF_OK;
+}
+
+static std::string device_tag() {
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+  std::string name = prop.name;
+  for (char& c : name)
+    if (c == ' ') c = '_';
+  return name + "_sm" + std::to_string(prop.multiProcessorCount);
+}
+
+kf_status kf_tune_cache_save(const char* path) {
+  if (path == nullptr) return err(KF_ERR_INVALID_ARG, "null path");
+  std::vector<std::string> lines;
+  tune_cache_dump(&lines);
+  std::ofstream f(path);
+  if (!f) return err(KF_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  f << "# kf tuning cache v1\ndevice " << device_tag() << "\n";
+  for (auto& l : lines) f << l << "\n";
+  return f ? KF_OK : err(KF_ERR_INVALID_ARG, "write failed");
+}
+
+kf_status kf_tune_cache_load(const char* path, int* loaded) {
+  if (path == nullptr) return err(KF_ERR_INVALID_ARG, "null path");
+  std::ifstream f(path);
+  if (!f) return err(KF_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  std::string line;
+  int n = 0;
+  bool dev_ok = false;
+  while (std::getline(f, line)) {
+    if (line.empty() || line[0] == '#') continue;
+    if (line.rfind("device ", 0) == 0) {
+      dev_ok = line.substr(7) == device_tag();
+      continue;
+    }
+    if (!dev_ok) continue;  // tunings of another device are not used
+    const size_t colon = line.find(" : ");
+    if (colon == std::string::npos) return err(KF_ERR_INVALID_ARG, "malformed tuning cache line: " + line);
+    const std::string key = line.substr(0, colon);
+    int v[5] = {0, 0, 0, 0, 0};
+    const int got = std::sscanf(line.c_str() + colon + 3, "%d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4]);
+    if (key.rfind("mat ", 0) == 0 && got == 5) {
+      tune_cache_put_mat(key, MatTune{v[0], v[1], v[2], v[3], v[4]});
+      ++n;
+    } else if (key.rfind("vec ", 0) == 0 && got == 3) {
+      tune_cache_put_vec(key, VecTune{v[0], v[1], v[2]});
+      ++n;
+    } else {
+      return err(KF_ERR_INVALID_ARG, "malformed tuning cache line: " + line);
+    }
+  }
+  if (loaded) *loaded = n;
+  return KF_OK;
+}
+
+
+// Features, analytic prediction and kernel count of every enumerated plan
+// (index order of KF_PLAN_INDEX), in one call.
+kf_status kf_plan_enumerate_info(const kf_script* s, int cap, float* feats, double* pred_us, int* kernels,
+                                 int* count) {
+  if (s == nullptr || count == nullptr || cap <= 0) return err(KF_ERR_INVALID_ARG, "bad arguments");
+  kf_status st = ensure_analysed(s);
+  if (st != KF_OK) return st;
+  std::vector<std::vector<std::vector<int>>> all;
+  bool tr = false;
+  enumerate(s->s, (size_t)cap, &all, &tr);
+  std::vector<float> f;
+  for (size_t i = 0; i < all.size(); ++i) {
+    Plan p;
+    std::string e = make_plan(s->s, all[i], &p);
+    if (!e.empty()) return err(KF_ERR_UNSUPPORTED, e);
+    if (feats) {
+      features(s->s, p, &f);
+      std::copy(f.begin(), f.end(), feats + i * NFEATURES);
+    }
+    if (pred_us) pred_us[i] = p.predicted_us;
+    if (kernels) kernels[i] = (int)p.kernels.size();
+  }
+  *count = (int)all.size();
   return KF_OK;
 }
 

@@ -10,6 +10,8 @@
 // the last block to finish adds the per-block partials in block order
 // (Section 3.2.2, option (ii)), in double when the vectors are long.
 #include <map>
+#include <string>
+#include <vector>
 #include <mutex>
 #include <tuple>
 
@@ -270,8 +272,14 @@ size_t vecprog_workspace_bytes(int ndot) {
   return WS_HEADER + 256 + (size_t)(ndot > 0 ? ndot : 1) * VP_MAXBLOCKS * sizeof(float);
 }
 
-int launch_vecprog(VecProg& P, const VecTune& tune, void* stream, const char** why) {
+std::string vec_cache_key(const VecProg& P);
+bool tune_cache_get_vec(const std::string& k, VecTune* t);
+void tune_cache_put_vec(const std::string& k, const VecTune& t);
+
+int launch_vecprog(VecProg& P, const VecTune& tune_in, void* stream, const char** why) {
   ensure_vregistry();
+  VecTune tune = tune_in;
+  if (tune.unroll == 0 && !tune_cache_get_vec(vec_cache_key(P), &tune)) tune = VecTune{256, 4, 0};
   bool vec = true;
   for (int k = 0; k < P.nin; ++k) vec = vec && al16(P.in[k]);
   for (int j = 0; j < P.nout; ++j) vec = vec && al16(P.out[j]);
@@ -299,6 +307,52 @@ int launch_vecprog(VecProg& P, const VecTune& tune, void* stream, const char** w
   cudaError_t err = cudaLaunchKernel(e->fn, dim3((unsigned)blocks), dim3(threads), args, 0,
                                      (cudaStream_t)stream);
   if (err != cudaSuccess) { *why = cudaGetErrorString(err); return -7; }
+  return 0;
+}
+
+
+// Empirical search over rows in flight (2 or 4 chunks per input) and grid
+// size (2, 4 or 8 blocks per SM); best to the tuning cache.  Synchronous.
+int autotune_vecprog(VecProg& P, void* stream, int reps, VecTune* best, float* best_ms, float* auto_ms) {
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  auto time_one = [&](const VecTune& t, float* ms) -> int {
+    const char* why = nullptr;
+    int rc = launch_vecprog(P, t, stream, &why);
+    std::vector<float> v;
+    for (int r = 0; r < reps && rc == 0; ++r) {
+      cudaEventRecord(a, st);
+      rc = launch_vecprog(P, t, stream, &why);
+      cudaEventRecord(b, st);
+      cudaEventSynchronize(b);
+      float x = 0.f;
+      cudaEventElapsedTime(&x, a, b);
+      v.push_back(x);
+    }
+    if (rc != 0) return rc;
+    std::sort(v.begin(), v.end());
+    *ms = v[v.size() / 2];
+    return 0;
+  };
+  float bm = 1e30f;
+  VecTune bt{256, 4, 0};
+  for (int u : {2, 4})
+    for (int k : {2, 4, 8}) {
+      VecTune t{256, u, device_sm_count() * k};
+      float ms = 0.f;
+      if (time_one(t, &ms) == 0 && ms < bm * 0.999f) { bm = ms; bt = t; }
+    }
+  float am = 0.f;
+  time_one(VecTune{0, 0, 0}, &am);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (bm >= 1e29f) return -7;
+  tune_cache_put_vec(vec_cache_key(P), bt);
+  *best = bt;
+  *best_ms = bm;
+  if (auto_ms) *auto_ms = am;
   return 0;
 }
 

@@ -73,6 +73,18 @@ _SIGS = {
     "kf_batched_graph_create": ([vp, vp, sz, ctypes.POINTER(vp)], ci),
     "kf_batched_graph_launch": ([vp, vp], ci),
     "kf_batched_graph_destroy": ([vp], None),
+    "kf_batched_workspace_bound": ([ci, vp, ci, ctypes.POINTER(sz)], ci),
+    "kf_batched_autotune": ([ci, vp, ci, vp, sz, vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_float)], ci),
+    "kf_autotune_plan": ([vp, ctypes.POINTER(vp), ci, vp, sz, vp, ci, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)], ci),
+    "kf_tune_cache_clear": ([], ci),
+    "kf_tune_cache_entries": ([ctypes.POINTER(ci)], ci),
+    "kf_tune_cache_save": ([ctypes.c_char_p], ci),
+    "kf_tune_cache_load": ([ctypes.c_char_p, ctypes.POINTER(ci)], ci),
+    "kf_mlp_param_count": ([ci, ci, ctypes.POINTER(ci)], ci),
+    "kf_mlp_workspace_size": ([ci, ci, ci, ctypes.POINTER(sz)], ci),
+    "kf_mlp_forward": ([vp, ci, ci, vp, ci, vp, vp], ci),
+    "kf_mlp_loss_grad": ([vp, ci, ci, vp, vp, ci, vp, vp, vp, sz, vp], ci),
+    "kf_mlp_adam": ([vp, vp, vp, vp, ci, ci, f32, f32, f32, f32, vp], ci),
     "kf_script_create": ([ctypes.POINTER(vp)], ci),
     "kf_script_destroy": ([vp], None),
     "kf_script_vector": ([vp, ctypes.c_char_p, i64, ctypes.POINTER(ci)], ci),
@@ -91,6 +103,7 @@ _SIGS = {
     "kf_planner_set_model": ([ctypes.c_double, ctypes.c_double], ci),
     "kf_plan_features": ([vp, vp, ctypes.POINTER(ctypes.c_float), ci, ctypes.POINTER(ci)], ci),
     "kf_plan_describe": ([vp, ctypes.c_char_p, sz, ctypes.POINTER(sz)], ci),
+    "kf_plan_enumerate_info": ([vp, ci, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
     "kf_plan_execute": ([vp, ctypes.POINTER(vp), ci, vp, sz, vp], ci),
     "kf_plan_time": ([vp, ctypes.POINTER(vp), ci, vp, sz, vp, ci, ctypes.POINTER(ctypes.c_float)], ci),
     "kf_get_matrix_tuning": ([ctypes.POINTER(ci)] * 5, ci),
@@ -345,6 +358,18 @@ class Script:
         _ck(lib().kf_plan_count(self.h, cap, ctypes.byref(c), ctypes.byref(t)))
         return c.value, bool(t.value)
 
+    def enumerate_info(self, cap=2000):
+        """(features [count x 16], analytic predictions [count], kernel counts [count])."""
+        import numpy as np
+        f = (ctypes.c_float * (cap * 16))()
+        p = (ctypes.c_double * cap)()
+        kk = (ci * cap)()
+        c = ci(0)
+        _ck(lib().kf_plan_enumerate_info(self.h, cap, f, p, kk, ctypes.byref(c)))
+        n = c.value
+        return (np.frombuffer(f, dtype=np.float32)[:n * 16].reshape(n, 16).copy(),
+                np.frombuffer(p, dtype=np.float64)[:n].copy(), np.frombuffer(kk, dtype=np.int32)[:n].copy())
+
     def plan(self, mode=KF_PLAN_ANALYTIC, index=0, max_plans=0):
         opt = (ci * 3)(mode, max_plans, index)
         h = vp()
@@ -402,6 +427,14 @@ class Plan:
         arr, nv = self._bind(bindings)
         _ck(lib().kf_plan_execute(self.h, arr, nv, _p(ws), _nb(ws), _st(stream)))
 
+    def autotune(self, bindings, ws, reps=5, stream=None):
+        """Tune every kernel of the plan on the bound data; returns
+        (tuned_ms, previous_ms), sums over the kernels of median times."""
+        arr, nv = self._bind(bindings)
+        a, b = ctypes.c_float(0), ctypes.c_float(0)
+        _ck(lib().kf_autotune_plan(self.h, arr, nv, _p(ws), _nb(ws), _st(stream), reps, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def time(self, bindings, ws, reps=5, stream=None):
         arr, nv = self._bind(bindings)
         ms = ctypes.c_float(0)
@@ -421,16 +454,33 @@ class BatchDesc(ctypes.Structure):
                 ("y", vp), ("s", vp), ("alpha", f32), ("beta", f32)]
 
 
+def _desc_array(descs):
+    arr = (BatchDesc * max(1, len(descs)))()
+    for i, d in enumerate(descs):
+        arr[i] = BatchDesc(d["m"], d["n"], d.get("lda", d["n"]), _p(d.get("A")), _p(d.get("B")),
+                           _p(d.get("x")), _p(d.get("r")), _p(d.get("y")), _p(d.get("s")),
+                           d.get("alpha", 1.0), d.get("beta", 0.0))
+    return arr
+
+
+def kf_batched_autotune(seq, descs, reps=5, stream=None):
+    """Best tile height for the batch (library-side empirical search)."""
+    arr = _desc_array(descs)
+    b = sz(0)
+    _ck(lib().kf_batched_workspace_bound(seq, ctypes.cast(arr, vp), len(descs), ctypes.byref(b)))
+    ws = torch.zeros(max(b.value, 256), dtype=torch.uint8, device="cuda")
+    best, ms = ci(0), ctypes.c_float(0)
+    _ck(lib().kf_batched_autotune(seq, ctypes.cast(arr, vp), len(descs), _p(ws), _nb(ws), _st(stream), reps,
+                                  ctypes.byref(best), ctypes.byref(ms)))
+    return best.value, ms.value
+
+
 class Batched:
     """kf_batched_* handle: `descs` is a list of dicts with m, n, lda and
     device pointers A, B, x, r, y, s (ints or tensors), alpha, beta."""
 
     def __init__(self, seq, descs, band_rows=0):
-        arr = (BatchDesc * max(1, len(descs)))()
-        for i, d in enumerate(descs):
-            arr[i] = BatchDesc(d["m"], d["n"], d.get("lda", d["n"]), _p(d.get("A")), _p(d.get("B")),
-                               _p(d.get("x")), _p(d.get("r")), _p(d.get("y")), _p(d.get("s")),
-                               d.get("alpha", 1.0), d.get("beta", 0.0))
+        arr = _desc_array(descs)
         h = vp()
         _ck(lib().kf_batched_create(seq, ctypes.cast(arr, vp), len(descs), band_rows, ctypes.byref(h)))
         self.h = h
@@ -466,3 +516,53 @@ class Batched:
 
     def replay(self, stream=None):
         _ck(lib().kf_batched_graph_launch(self.graph, _st(stream)))
+
+
+def kf_tune_cache_clear():
+    _ck(lib().kf_tune_cache_clear())
+
+
+def kf_tune_cache_entries():
+    n = ci(0)
+    _ck(lib().kf_tune_cache_entries(ctypes.byref(n)))
+    return n.value
+
+
+def kf_tune_cache_save(path):
+    _ck(lib().kf_tune_cache_save(str(path).encode()))
+
+
+def kf_tune_cache_load(path):
+    n = ci(0)
+    _ck(lib().kf_tune_cache_load(str(path).encode(), ctypes.byref(n)))
+    return n.value
+
+
+# ------------------------------------------------------------------ cost model
+
+MLP_HIDDEN = 64
+
+
+def kf_mlp_param_count(d_in, hidden=MLP_HIDDEN):
+    c = ci(0)
+    _ck(lib().kf_mlp_param_count(d_in, hidden, ctypes.byref(c)))
+    return c.value
+
+
+def kf_mlp_workspace_size(d_in, batch, hidden=MLP_HIDDEN):
+    b = sz(0)
+    _ck(lib().kf_mlp_workspace_size(d_in, hidden, batch, ctypes.byref(b)))
+    return b.value
+
+
+def kf_mlp_forward(params, X, out, hidden=MLP_HIDDEN, stream=None):
+    _ck(lib().kf_mlp_forward(_p(params), X.shape[1], hidden, _p(X), X.shape[0], _p(out), _st(stream)))
+
+
+def kf_mlp_loss_grad(params, X, y, grad, loss, ws, hidden=MLP_HIDDEN, stream=None):
+    _ck(lib().kf_mlp_loss_grad(_p(params), X.shape[1], hidden, _p(X), _p(y), X.shape[0], _p(grad), _p(loss),
+                               _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_mlp_adam(params, grad, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    _ck(lib().kf_mlp_adam(_p(params), _p(grad), _p(m), _p(v), params.numel(), step, lr, b1, b2, eps, _st(stream)))

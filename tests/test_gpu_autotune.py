@@ -1,0 +1,86 @@
+"""Autotuner: empirical search over compiled implementations, tuning cache,
+its persistence, and tuned launches keeping parity with the oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import built, dev, host  # noqa: F401
+from tolerance import check_reduce
+from test_planner_cpu import bicgk, gemver
+
+pytestmark = pytest.mark.gpu
+
+
+def bind_bicgk(m, n):
+    A = synth.uniform((m, n), 0, 1, device=dev())
+    p = synth.uniform((n,), 0, 3, device=dev())
+    r = synth.uniform((m,), 0, 4, device=dev())
+    return {"A": A, "p": p, "r": r, "q": torch.empty(m, device=dev()), "s": torch.empty(n, device=dev())}
+
+
+def test_autotune_plan_and_cache(built, tmp_path):
+    kf = built
+    kf.kf_tune_cache_clear()
+    m = n = 4096
+    s = bicgk(kf, m, n)
+    p = s.plan(kf.KF_PLAN_ANALYTIC)
+    b = bind_bicgk(m, n)
+    ws = torch.zeros(p.workspace_size(), dtype=torch.uint8, device=dev())
+    tuned, before = p.autotune(b, ws, reps=3)
+    assert 0 < tuned <= before * 1.02        # the default is among the candidates
+    assert kf.kf_tune_cache_entries() >= 1
+    # the fixed entry point of the same size class now runs the tuned kernel
+    q = torch.empty(m, device=dev()); sv = torch.empty(n, device=dev())
+    kf.kf_bicgk(b["A"], b["p"], b["r"], q, sv, kf.workspace(kf.KF_SEQ_BICGK, m, n))
+    Ah, ph, rh = host(b["A"]), host(b["p"]), host(b["r"])
+    qo, so = oracle.bicgk(Ah, ph, rh)
+    check_reduce(host(q), qo, oracle.abs_gemv(Ah, ph), n, "q tuned")
+    check_reduce(host(sv), so, oracle.abs_gemvt(Ah, rh), m, "s tuned")
+    # persistence
+    path = tmp_path / "tune.txt"
+    kf.kf_tune_cache_save(path)
+    entries = kf.kf_tune_cache_entries()
+    kf.kf_tune_cache_clear()
+    assert kf.kf_tune_cache_entries() == 0
+    assert kf.kf_tune_cache_load(path) == entries
+    # a cache written on another device is ignored; a malformed one is an error
+    other = tmp_path / "other.txt"
+    other.write_text(open(path).read().replace("device ", "device SomeOtherGPU_", 1))
+    kf.kf_tune_cache_clear()
+    assert kf.kf_tune_cache_load(other) == 0
+    bad = tmp_path / "bad.txt"
+    bad.write_text(open(path).read() + "mat 1 2 3 : nonsense\n")
+    with pytest.raises(kf.KFError):
+        kf.kf_tune_cache_load(bad)
+    kf.kf_tune_cache_clear()
+
+
+def test_autotune_gemver_plan(built):
+    kf = built
+    n = 2048
+    s = gemver(kf, n)
+    p = s.plan(kf.KF_PLAN_ANALYTIC)
+    names = ["A", "B", "u1", "v1", "u2", "v2", "y", "z", "x", "w", "t"]
+    b = {k: (synth.uniform((n, n) if k in ("A", "B") else (n,), 0, 20 + i, device=dev())) for i, k in enumerate(names)}
+    ws = torch.zeros(p.workspace_size(), dtype=torch.uint8, device=dev())
+    tuned, before = p.autotune(b, ws, reps=3)
+    assert 0 < tuned <= before * 1.02
+    kf.kf_tune_cache_clear()
+
+
+def test_batched_autotune(built):
+    kf = built
+    ms = synth.log_uniform_int(32, 1024, 5, synth.TID["sizes"], 128).tolist()
+    ns = synth.log_uniform_int(32, 1024, 6, synth.TID["sizes"], 128).tolist()
+    descs, keep = [], []
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        A = synth.uniform((m, n), i, 1, device=dev())
+        x = synth.uniform((n,), i, 3, device=dev()); r = synth.uniform((m,), i, 4, device=dev())
+        y = torch.empty(m, device=dev()); s = torch.empty(n, device=dev())
+        keep += [A, x, r, y, s]
+        descs.append({"m": m, "n": n, "lda": n, "A": A, "x": x, "r": r, "y": y, "s": s})
+    br, t = kf.kf_batched_autotune(kf.KF_SEQ_BICGK, descs, reps=3)
+    assert br in (32, 64, 128, 256, 512) and t > 0
