@@ -305,6 +305,67 @@ kf_status kf_plan_time(const kf_plan* p, void* const* bindings, int n_bindings, 
                        void* stream, int reps, float* median_ms);
 
 /* ------------------------------------------------------------------------
+ * Plan selection.  The paper ranks the implementations of a script with an
+ * additive predictor and can search them empirically (Section 3.2).
+ * kf_plan_select picks one of the enumerated plans (at most max_plans;
+ * <= 0: 2000):
+ *   KF_SELECT_ANALYTIC    least analytic prediction; no GPU work, ws and
+ *                         bindings unused;
+ *   KF_SELECT_MLP         the learned cost model (kf_mlp_*, 16 inputs, 64
+ *                         hidden units) scores every plan on the GPU from its
+ *                         features standardised as (f - mean) * inv_std (the
+ *                         score estimates ln(ms), see kf_cost_model); the
+ *                         lowest score ranks first; with top_k <= 1 the first-ranked
+ *                         plan is kept untimed, else the top_k best-ranked
+ *                         plans are timed on the bound data and the fastest
+ *                         kept (top_k >= the plan count: every plan is timed,
+ *                         the exhaustive fallback);
+ *   KF_SELECT_EXHAUSTIVE  every plan is timed; the fastest is kept.
+ * Timing is kf_plan_time's (one warm-up run, median of `reps` >= 1; <= 0:
+ * 3) and writes the plans' outputs and in-place operands.  ws: at least
+ * kf_plan_select_workspace_size bytes, zero-filled before its first use
+ * (the plans' region, then the model's inputs and outputs).  Synchronous on
+ * `stream`.  *out is a new plan (kf_plan_destroy); info may be NULL.
+ * Errors: KF_ERR_INVALID_ARG (no model for KF_SELECT_MLP, missing bindings
+ * when timing), KF_ERR_WORKSPACE, KF_ERR_UNSUPPORTED (no legal plan).
+ * ---------------------------------------------------------------------- */
+typedef enum { KF_SELECT_ANALYTIC = 0, KF_SELECT_MLP = 1, KF_SELECT_EXHAUSTIVE = 2 } kf_select_mode;
+
+typedef struct {
+  int mode;       /* kf_select_mode                          */
+  int max_plans;  /* enumeration cap (<= 0: 2000)            */
+  int top_k;      /* KF_SELECT_MLP: best-ranked plans timed  */
+  int reps;       /* timed runs per plan (<= 0: 3)           */
+} kf_select_options;
+
+typedef struct {
+  const float* params;   /* device: kf_mlp_param_count(16, 64) floats   */
+  float mean[16];        /* host: feature standardisation               */
+  float inv_std[16];
+  float analytic_weight; /* score = MLP output + analytic_weight *
+                            ln(analytic prediction in ms); 1: the network
+                            learned the residual of the analytic model   */
+} kf_cost_model;
+
+typedef struct {
+  int index;        /* chosen plan, in KF_PLAN_INDEX order                 */
+  int count;        /* plans enumerated                                    */
+  int timed;        /* plans timed                                         */
+  float best_ms;    /* median of the chosen plan (0 when nothing was timed) */
+  double predicted; /* MLP: the chosen plan's score; otherwise analytic us */
+} kf_select_info;
+
+kf_status kf_plan_select_workspace_size(const kf_script* s, int max_plans, size_t* bytes);
+kf_status kf_plan_select(const kf_script* s, const kf_select_options* opt, const kf_cost_model* model,
+                         void* const* bindings, int n_bindings, void* ws, size_t ws_bytes, void* stream, kf_plan** out,
+                         kf_select_info* info);
+/* Median time (ms) of every enumerated plan, in KF_PLAN_INDEX order (ms:
+ * room for max_plans floats): the data of the exhaustive search, which
+ * judges the cost models.  Workspace and timing as kf_plan_select. */
+kf_status kf_plan_time_all(const kf_script* s, int max_plans, void* const* bindings, int n_bindings, void* ws,
+                           size_t ws_bytes, void* stream, int reps, float* ms, int* count);
+
+/* ------------------------------------------------------------------------
  * Autotuning (Section 3.2: block size and serial iterations are part of a
  * fusion implementation; routines are benchmarked once per architecture).
  * kf_autotune_plan runs, for every kernel of the plan on the bound data,

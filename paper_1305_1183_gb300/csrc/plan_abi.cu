@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -15,6 +16,7 @@
 
 namespace kf {
 const char* set_error_message(const std::string& msg);
+MatTune current_matrix_tuning();
 int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* best_ms, float* auto_ms);
 int autotune_vecprog(VecProg& P, void* stream, int reps, VecTune* best, float* best_ms, float* auto_ms);
 void tune_cache_clear();
@@ -124,6 +126,45 @@ kf_status launch_kernel(const Kernel& K, void* const* bindings, int nb, void* ws
 }
 
 
+// Run once, then time `reps` executions with CUDA events; the median (ms).
+kf_status time_plan(const Plan& P, int nvars, void* const* bindings, int nb, void* ws, size_t ws_bytes, void* stream,
+                    int reps, float* median_ms) {
+  if (nb > 0 && bindings == nullptr) return err(KF_ERR_INVALID_ARG, "null bindings");
+  if (nb < nvars) return err(KF_ERR_INVALID_ARG, "every script variable needs a binding");
+  cudaStream_t st = (cudaStream_t)stream;
+  const MatTune tune = current_matrix_tuning();
+  auto run = [&]() -> kf_status {
+    for (const Kernel& K : P.kernels) {
+      kf_status rc = launch_kernel(K, bindings, nb, ws, ws_bytes, stream, tune);
+      if (rc != KF_OK) return rc;
+    }
+    return KF_OK;
+  };
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return err(KF_ERR_CUDA, "cudaEventCreate failed");
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return err(KF_ERR_CUDA, "cudaEventCreate failed");
+  }
+  kf_status rc = run();  // warm up
+  std::vector<float> t;
+  for (int r = 0; r < reps && rc == KF_OK; ++r) {
+    cudaEventRecord(a, st);
+    rc = run();
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess) rc = err(KF_ERR_CUDA, "timing failed");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    t.push_back(ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != KF_OK) return rc;
+  std::sort(t.begin(), t.end());
+  *median_ms = t[t.size() / 2];
+  return KF_OK;
+}
+
 // Name of the program field at byte offset `o` (for plan descriptions).
 std::string field_name(const Kernel& K, size_t o) {
   auto at = [&](const void* base, const void* f) { return (size_t)((const char*)f - (const char*)base); };
@@ -158,10 +199,6 @@ std::string field_name(const Kernel& K, size_t o) {
 }
 
 }  // namespace
-
-namespace kf {
-MatTune current_matrix_tuning();
-}
 
 extern "C" {
 
@@ -350,27 +387,7 @@ kf_status kf_plan_execute(const kf_plan* p, void* const* bindings, int n_binding
 kf_status kf_plan_time(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
                        void* stream, int reps, float* median_ms) {
   if (p == nullptr || median_ms == nullptr || reps <= 0) return err(KF_ERR_INVALID_ARG, "bad arguments");
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaEvent_t a, b;
-  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
-    return err(KF_ERR_CUDA, "cudaEventCreate failed");
-  kf_status rc = kf_plan_execute(p, bindings, n_bindings, ws, ws_bytes, stream);  // warm up
-  std::vector<float> t;
-  for (int r = 0; r < reps && rc == KF_OK; ++r) {
-    cudaEventRecord(a, st);
-    rc = kf_plan_execute(p, bindings, n_bindings, ws, ws_bytes, stream);
-    cudaEventRecord(b, st);
-    if (cudaEventSynchronize(b) != cudaSuccess) rc = err(KF_ERR_CUDA, "timing failed");
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    t.push_back(ms);
-  }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  if (rc != KF_OK) return rc;
-  std::sort(t.begin(), t.end());
-  *median_ms = t[t.size() / 2];
-  return KF_OK;
+  return time_plan(p->p, p->nvars, bindings, n_bindings, ws, ws_bytes, stream, reps, median_ms);
 }
 
 kf_status kf_planner_set_model(double bw_gbs, double launch_us) {
@@ -515,6 +532,167 @@ kf_status kf_plan_enumerate_info(const kf_script* s, int cap, float* feats, doub
     if (kernels) kernels[i] = (int)p.kernels.size();
   }
   *count = (int)all.size();
+  return KF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Plan selection: analytic ranking, learned ranking pruning the empirical
+// search, exhaustive empirical search (Section 3.2).
+namespace {
+
+constexpr int SELECT_DEFAULT_CAP = 2000;
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct Enumerated {
+  std::vector<Plan> plans;
+  size_t ws_max = 0;  // largest plan workspace
+};
+
+kf_status enumerate_built(const kf_script* s, int cap, Enumerated* E) {
+  kf_status st = ensure_analysed(s);
+  if (st != KF_OK) return st;
+  std::vector<std::vector<std::vector<int>>> all;
+  bool tr = false;
+  enumerate(s->s, (size_t)cap, &all, &tr);
+  if (all.empty()) return err(KF_ERR_UNSUPPORTED, "no legal plan");
+  E->plans.resize(all.size());
+  for (size_t i = 0; i < all.size(); ++i) {
+    std::string e = make_plan(s->s, all[i], &E->plans[i]);
+    if (!e.empty()) return err(KF_ERR_UNSUPPORTED, e);
+    E->ws_max = std::max(E->ws_max, E->plans[i].ws_bytes);
+  }
+  return KF_OK;
+}
+
+// [plans' region | standardised features (count x 16) | predictions (count)]
+size_t select_ws_bytes(const Enumerated& E) {
+  const size_t n = E.plans.size();
+  return align256(E.ws_max) + align256(n * NFEATURES * sizeof(float)) + align256(n * sizeof(float));
+}
+
+kf_status check_bindings(const kf_script* s, void* const* bindings, int nb) {
+  if (bindings == nullptr) return err(KF_ERR_INVALID_ARG, "timing needs bindings");
+  if (nb < (int)s->s.vars.size()) return err(KF_ERR_INVALID_ARG, "every script variable needs a binding");
+  return KF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kf_status kf_plan_select_workspace_size(const kf_script* s, int max_plans, size_t* bytes) {
+  if (s == nullptr || bytes == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  Enumerated E;
+  kf_status st = enumerate_built(s, max_plans > 0 ? max_plans : SELECT_DEFAULT_CAP, &E);
+  if (st != KF_OK) return st;
+  *bytes = select_ws_bytes(E);
+  return KF_OK;
+}
+
+kf_status kf_plan_time_all(const kf_script* s, int max_plans, void* const* bindings, int n_bindings, void* ws,
+                           size_t ws_bytes, void* stream, int reps, float* ms, int* count) {
+  if (s == nullptr || ms == nullptr || count == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  Enumerated E;
+  kf_status st = enumerate_built(s, max_plans > 0 ? max_plans : SELECT_DEFAULT_CAP, &E);
+  if (st != KF_OK) return st;
+  if ((st = check_bindings(s, bindings, n_bindings)) != KF_OK) return st;
+  if (ws_bytes < select_ws_bytes(E) || (ws == nullptr && E.ws_max > 0))
+    return err(KF_ERR_WORKSPACE, "workspace smaller than kf_plan_select_workspace_size()");
+  const int nvars = (int)s->s.vars.size();
+  for (size_t i = 0; i < E.plans.size(); ++i) {
+    st = time_plan(E.plans[i], nvars, bindings, n_bindings, ws, ws_bytes, stream, reps > 0 ? reps : 3, &ms[i]);
+    if (st != KF_OK) return st;
+  }
+  *count = (int)E.plans.size();
+  return KF_OK;
+}
+
+kf_status kf_plan_select(const kf_script* s, const kf_select_options* opt, const kf_cost_model* model,
+                         void* const* bindings, int n_bindings, void* ws, size_t ws_bytes, void* stream, kf_plan** out,
+                         kf_select_info* info) {
+  if (s == nullptr || opt == nullptr || out == nullptr) return err(KF_ERR_INVALID_ARG, "null argument");
+  const int cap = opt->max_plans > 0 ? opt->max_plans : SELECT_DEFAULT_CAP;
+  const int reps = opt->reps > 0 ? opt->reps : 3;
+  Enumerated E;
+  kf_status st = enumerate_built(s, cap, &E);
+  if (st != KF_OK) return st;
+  const int count = (int)E.plans.size();
+  const int nvars = (int)s->s.vars.size();
+  cudaStream_t cs = (cudaStream_t)stream;
+  int chosen = 0;
+  double predicted = 0.0;
+  std::vector<int> cand;  // plans to time
+  if (opt->mode == KF_SELECT_ANALYTIC) {
+    for (int i = 1; i < count; ++i)
+      if (E.plans[i].predicted_us < E.plans[chosen].predicted_us * (1.0 - 1e-9)) chosen = i;
+    predicted = E.plans[chosen].predicted_us;
+  } else if (opt->mode == KF_SELECT_MLP) {
+    if (model == nullptr || model->params == nullptr) return err(KF_ERR_INVALID_ARG, "KF_SELECT_MLP needs a model");
+    if (ws == nullptr || ws_bytes < select_ws_bytes(E))
+      return err(KF_ERR_WORKSPACE, "workspace smaller than kf_plan_select_workspace_size()");
+    std::vector<float> X((size_t)count * NFEATURES), f;
+    for (int i = 0; i < count; ++i) {
+      features(s->s, E.plans[i], &f);
+      for (int c = 0; c < NFEATURES; ++c)
+        X[(size_t)i * NFEATURES + c] = (f[c] - model->mean[c]) * model->inv_std[c];
+    }
+    float* dX = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(E.ws_max));
+    float* dY = reinterpret_cast<float*>(reinterpret_cast<char*>(dX) + align256(X.size() * sizeof(float)));
+    std::vector<float> y(count);
+    if (cudaMemcpyAsync(dX, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, cs) != cudaSuccess)
+      return err(KF_ERR_CUDA, "copy of plan features failed");
+    st = kf_mlp_forward(model->params, NFEATURES, 64, dX, count, dY, stream);
+    if (st != KF_OK) return st;
+    if (cudaMemcpyAsync(y.data(), dY, count * sizeof(float), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess)
+      return err(KF_ERR_CUDA, "cost model evaluation failed");
+    if (model->analytic_weight != 0.f)
+      for (int i = 0; i < count; ++i)
+        y[i] += model->analytic_weight * (float)std::log(std::max(E.plans[i].predicted_us, 1e-3) * 1e-3);
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return y[a] < y[b]; });
+    chosen = order[0];
+    predicted = y[chosen];
+    if (opt->top_k > 1) cand.assign(order.begin(), order.begin() + std::min(opt->top_k, count));
+  } else if (opt->mode == KF_SELECT_EXHAUSTIVE) {
+    cand.resize(count);
+    for (int i = 0; i < count; ++i) cand[i] = i;
+  } else {
+    return err(KF_ERR_INVALID_ARG, "unknown selection mode");
+  }
+  float best_ms = 0.f;
+  if (!cand.empty()) {
+    if ((st = check_bindings(s, bindings, n_bindings)) != KF_OK) return st;
+    if (ws_bytes < select_ws_bytes(E) || (ws == nullptr && E.ws_max > 0))
+      return err(KF_ERR_WORKSPACE, "workspace smaller than kf_plan_select_workspace_size()");
+    best_ms = 3.4e38f;
+    for (int i : cand) {
+      float ms = 0.f;
+      st = time_plan(E.plans[i], nvars, bindings, n_bindings, ws, ws_bytes, stream, reps, &ms);
+      if (st != KF_OK) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        chosen = i;
+      }
+    }
+    if (opt->mode == KF_SELECT_EXHAUSTIVE) predicted = E.plans[chosen].predicted_us;
+  }
+  auto* pl = new (std::nothrow) kf_plan();
+  if (pl == nullptr) return err(KF_ERR_NO_MEM, "out of host memory");
+  pl->p = std::move(E.plans[chosen]);
+  pl->nvars = nvars;
+  *out = pl;
+  if (info) {
+    info->index = chosen;
+    info->count = count;
+    info->timed = (int)cand.size();
+    info->best_ms = best_ms;
+    info->predicted = predicted;
+  }
   return KF_OK;
 }
 

@@ -647,7 +647,6 @@ void features(const Script& s, const Plan& p, std::vector<float>* f) {
         nger += K.mp.ops[k].kind == MOP_GER;
       }
       nepi += (float)(K.mp.nrow_out + K.mp.ncol_out);
-      for (int t = 0; t < K.mp.nmat; ++t) nstore += 0;  // stored matrices counted below
       nmax = std::max<int64_t>(nmax, std::max(K.m, K.n));
     } else {
       nvec += 1;
@@ -663,9 +662,10 @@ void features(const Script& s, const Plan& p, std::vector<float>* f) {
   (*f)[0] = nk;
   (*f)[1] = nmat;
   (*f)[2] = nvec;
-  (*f)[3] = (float)(p.bytes / 1e9);
-  (*f)[4] = matb / 1e9f;
-  (*f)[5] = vecb / 1e9f;
+  // byte counts span orders of magnitude across sizes: log scale
+  (*f)[3] = (float)std::log2(1.0 + p.bytes);
+  (*f)[4] = (float)std::log2(1.0 + (double)matb);
+  (*f)[5] = (float)std::log2(1.0 + (double)vecb);
   (*f)[6] = (float)std::log2((double)nmax);
   (*f)[7] = nk > 0 ? (float)s.calls.size() / nk : 0.f;
   (*f)[8] = maxops;
@@ -673,7 +673,7 @@ void features(const Script& s, const Plan& p, std::vector<float>* f) {
   (*f)[10] = ngemvt;
   (*f)[11] = nger;
   (*f)[12] = ndot;
-  (*f)[13] = (float)(p.predicted_us / 100.0);
+  (*f)[13] = (float)std::log2(1.0 + p.predicted_us);
   (*f)[14] = nepi;
   (*f)[15] = nstore;
 }

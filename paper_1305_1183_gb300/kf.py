@@ -107,6 +107,10 @@ _SIGS = {
     "kf_plan_execute": ([vp, ctypes.POINTER(vp), ci, vp, sz, vp], ci),
     "kf_plan_time": ([vp, ctypes.POINTER(vp), ci, vp, sz, vp, ci, ctypes.POINTER(ctypes.c_float)], ci),
     "kf_get_matrix_tuning": ([ctypes.POINTER(ci)] * 5, ci),
+    "kf_plan_select_workspace_size": ([vp, ci, ctypes.POINTER(sz)], ci),
+    "kf_plan_select": ([vp, vp, vp, ctypes.POINTER(vp), ci, vp, sz, vp, ctypes.POINTER(vp), vp], ci),
+    "kf_plan_time_all": ([vp, ci, ctypes.POINTER(vp), ci, vp, sz, vp, ci, ctypes.POINTER(ctypes.c_float),
+                          ctypes.POINTER(ci)], ci),
 }
 
 
@@ -300,6 +304,56 @@ def kf_bicgk_noalloc(A, p, r, q, s, stream=None):
 KF_OP_AXPBY, KF_OP_SCAL, KF_OP_DOT, KF_OP_VADD, KF_OP_GEMV, KF_OP_GEMVT, KF_OP_GER = range(7)
 OPS = {"AXPBY": 0, "SCAL": 1, "DOT": 2, "VADD": 3, "GEMV": 4, "GEMVT": 5, "GER": 6}
 KF_PLAN_UNFUSED, KF_PLAN_GREEDY, KF_PLAN_ANALYTIC, KF_PLAN_INDEX = range(4)
+KF_SELECT_ANALYTIC, KF_SELECT_MLP, KF_SELECT_EXHAUSTIVE = range(3)
+NFEATURES = 16
+
+
+class _SelectOptions(ctypes.Structure):
+    _fields_ = [("mode", ci), ("max_plans", ci), ("top_k", ci), ("reps", ci)]
+
+
+class _CostModel(ctypes.Structure):
+    _fields_ = [("params", vp), ("mean", ctypes.c_float * 16), ("inv_std", ctypes.c_float * 16),
+                ("analytic_weight", ctypes.c_float)]
+
+
+class _SelectInfo(ctypes.Structure):
+    _fields_ = [("index", ci), ("count", ci), ("timed", ci), ("best_ms", ctypes.c_float),
+                ("predicted", ctypes.c_double)]
+
+
+class CostModel:
+    """Learned plan cost model: device parameters of the kf_mlp network
+    (16 inputs, 64 hidden units), the host feature standardisation and the
+    weight of ln(analytic ms) added to the network's output."""
+
+    def __init__(self, params, mean, inv_std, analytic_weight=0.0):
+        self.params = params
+        self.mean = [float(x) for x in mean]
+        self.inv_std = [float(x) for x in inv_std]
+        self.analytic_weight = float(analytic_weight)
+        assert len(self.mean) == NFEATURES and len(self.inv_std) == NFEATURES
+
+    def _c(self):
+        c = _CostModel()
+        c.params = _p(self.params)
+        for i in range(NFEATURES):
+            c.mean[i] = self.mean[i]
+            c.inv_std[i] = self.inv_std[i]
+        c.analytic_weight = self.analytic_weight
+        return c
+
+    def save(self, path):
+        import numpy as np
+        np.savez(path, params=self.params.detach().float().cpu().numpy(), mean=np.array(self.mean),
+                 inv_std=np.array(self.inv_std), analytic_weight=np.array(self.analytic_weight))
+
+    @staticmethod
+    def load(path, device="cuda"):
+        import numpy as np
+        z = np.load(path)
+        return CostModel(torch.tensor(z["params"], dtype=torch.float32, device=device), z["mean"], z["inv_std"],
+                         float(z["analytic_weight"]))
 
 
 class Script:
@@ -369,6 +423,40 @@ class Script:
         n = c.value
         return (np.frombuffer(f, dtype=np.float32)[:n * 16].reshape(n, 16).copy(),
                 np.frombuffer(p, dtype=np.float64)[:n].copy(), np.frombuffer(kk, dtype=np.int32)[:n].copy())
+
+    def _bind(self, bindings):
+        arr = (vp * len(self.ids))()
+        for name, t in bindings.items():
+            arr[self.ids[name]] = _p(t)
+        return arr, len(self.ids)
+
+    def select_workspace_size(self, max_plans=0):
+        b = sz(0)
+        _ck(lib().kf_plan_select_workspace_size(self.h, max_plans, ctypes.byref(b)))
+        return b.value
+
+    def select(self, mode, bindings=None, ws=None, model=None, top_k=1, reps=3, max_plans=0, stream=None):
+        """kf_plan_select: (Plan, info dict with index, count, timed, best_ms, predicted)."""
+        opt = _SelectOptions(mode, max_plans, top_k, reps)
+        cm = model._c() if model is not None else None
+        arr, nv = self._bind(bindings) if bindings else (None, 0)
+        h = vp()
+        info = _SelectInfo()
+        _ck(lib().kf_plan_select(self.h, ctypes.byref(opt), ctypes.byref(cm) if cm is not None else None, arr, nv,
+                                 _p(ws) if ws is not None else None, _nb(ws) if ws is not None else 0,
+                                 _st(stream) if mode != KF_SELECT_ANALYTIC else None,
+                                 ctypes.byref(h), ctypes.byref(info)))
+        return Plan(h, self), {k: getattr(info, k) for k, _ in _SelectInfo._fields_}
+
+    def time_all(self, bindings, ws, reps=3, max_plans=0, stream=None):
+        """kf_plan_time_all: median ms of every enumerated plan (numpy array)."""
+        import numpy as np
+        cap = max_plans if max_plans > 0 else 2000
+        ms = (ctypes.c_float * cap)()
+        c = ci(0)
+        arr, nv = self._bind(bindings)
+        _ck(lib().kf_plan_time_all(self.h, max_plans, arr, nv, _p(ws), _nb(ws), _st(stream), reps, ms, ctypes.byref(c)))
+        return np.frombuffer(ms, dtype=np.float32)[:c.value].astype(np.float64)
 
     def plan(self, mode=KF_PLAN_ANALYTIC, index=0, max_plans=0):
         opt = (ci * 3)(mode, max_plans, index)

@@ -1,19 +1,28 @@
-"""Learned planner: measure plan timings on random scripts, train the MLP cost
-model with the library's own kernels, and compare its choices.
+"""Learned planner: train the plan cost model on timings the planner
+measures, and judge its choices against exhaustive empirical search.
 
 The paper ranks fusion implementations with an additive predictor of
-pre-benchmarked routine times and falls back on empirical search
-(Section 3.2; its accuracy in the table of Section 4.3).  Here a 3-layer
-perceptron (16 plan features -> 64 -> 64 -> 1, ReLU) learns log plan time
-from timings the planner itself measures; forward, backward and Adam run in
-libkf (kf_mlp_*).  Per script, up to `per_script` plans are timed: every plan
-when there are that few, else the best predicted half by the analytic model,
-the fewest-kernel plan, the one-kernel-per-call plan and a seeded uniform
-sample of the rest.  The best measured plan of that set is the judge; the
-MLP's first choice, the analytic choice and the fewest-kernel choice are
-scored by t(choice) / t(best).
+benchmarked routine times and can search them empirically (Section 3.2; the
+predictor's accuracy is tabulated in Section 4.3).  Here a 3-layer
+perceptron (16 plan features -> 64 -> 64 -> 1, ReLU) predicts log plan time;
+its forward, backward and Adam steps are libkf kernels (kf_mlp_*), and
+kf_plan_select uses it to rank every enumerated plan and re-time only the
+best-ranked few.
 
-    python -m paper_1305_1183_gb300.learn --scripts 500 --train 400 --out results.json
+Data.  Random scripts (synth.scripts) of 6-10 calls over shared vectors and
+matrices, n = 2^k with k drawn per script in [kmin, kmax].  For a training
+script up to `per_script` plans are timed (kf_plan_time on the bound data):
+all of them when there are that few, else the best-predicted half by the
+analytic model, the fewest-kernel plan, the one-kernel-per-call plan and a
+seeded uniform sample of the rest.
+
+Judge.  For a held-out script every enumerated plan is timed
+(kf_plan_time_all); each method's choice is scored by t(choice) / t(best)
+on that table: the MLP's first choice (no timing), the MLP's top-k re-timed
+(kf_plan_select, KF_SELECT_MLP), the analytic model, the fewest-kernel plan
+and the unfused chain.
+
+    python -m paper_1305_1183_gb300.learn --scripts 500 --train 400 --out learned.json
 """
 
 from __future__ import annotations
@@ -66,53 +75,55 @@ def script_size(seed, index, kmin, kmax):
     return 1 << (kmin + min(int(u * (kmax - kmin + 1)), kmax - kmin))
 
 
-def collect(seed, indices, kmin, kmax, per_script, reps, cap=2000, device="cuda", log=None):
-    records = []
+def make(seed, i, kmin, kmax):
+    n = script_size(seed, i, kmin, kmax)
+    sd = sscripts.random_script(seed, i, n)
+    return n, sd, to_script(sd)
+
+
+def training_subset(seed, i, pred, nk, ncalls, per_script):
+    count = len(pred)
+    if count <= per_script:
+        return list(range(count))
+    chosen = [int(j) for j in np.argsort(pred, kind="stable")[: per_script // 2]]
+    greedy = int(np.argmin(nk))
+    unfused = [j for j in range(count) if nk[j] == ncalls]
+    for j in [greedy] + unfused[:1]:
+        if j not in chosen:
+            chosen.append(j)
+    rest = [j for j in range(count) if j not in chosen]
+    k = 0
+    while len(chosen) < per_script and rest:
+        u = synth.uniform_scalar(seed + 1, synth.TID["script"], i * 1000 + k) * 0.5 + 0.5
+        chosen.append(rest.pop(min(int(u * len(rest)), len(rest) - 1)))
+        k += 1
+    return sorted(chosen)
+
+
+def collect(seed, indices, kmin, kmax, per_script, reps, cap=2000, device="cuda"):
+    """Training data: features and measured ms of a subset of each script's plans."""
+    X, y, pu, meta = [], [], [], []
     for i in indices:
-        n = script_size(seed, i, kmin, kmax)
-        sd = sscripts.random_script(seed, i, n)
-        s = to_script(sd)
+        n, sd, s = make(seed, i, kmin, kmax)
         feats, pred, nk = s.enumerate_info(cap)
-        count = len(pred)
-        ncalls = len(sd["calls"])
-        order = np.argsort(pred, kind="stable")
-        chosen = []
-        if count <= per_script:
-            chosen = list(range(count))
-        else:
-            chosen = list(order[: per_script // 2])
-            greedy = int(np.lexsort((pred, nk))[0])
-            unfused = [j for j in range(count) if nk[j] == ncalls]
-            for j in [greedy] + unfused[:1]:
-                if j not in chosen:
-                    chosen.append(j)
-            rest = [j for j in range(count) if j not in chosen]
-            k = 0
-            while len(chosen) < per_script and rest:
-                u = synth.uniform_scalar(seed + 1, synth.TID["script"], i * 1000 + k) * 0.5 + 0.5
-                chosen.append(rest.pop(min(int(u * len(rest)), len(rest) - 1)))
-                k += 1
+        chosen = training_subset(seed, i, pred, nk, len(sd["calls"]), per_script)
         bind = bindings(sd, i, device)
-        timed = []
         ws = None
-        for j in sorted(int(x) for x in chosen):
+        for j in chosen:
             p = s.plan(kf.KF_PLAN_INDEX, index=j, max_plans=cap)
             need = max(p.workspace_size(), 256)
             if ws is None or ws.numel() < need:
                 ws = torch.zeros(need, dtype=torch.uint8, device=device)
-            ms = p.time(bind, ws, reps=reps)
-            timed.append({"plan": j, "ms": ms, "pred_us": float(pred[j]), "kernels": int(nk[j]),
-                          "feats": [float(x) for x in feats[j]]})
+            X.append(feats[j])
+            pu.append(pred[j])
+            y.append(p.time(bind, ws, reps=reps))
+        meta.append({"index": int(i), "n": n, "calls": len(sd["calls"]), "plans": len(pred), "timed": len(chosen)})
         del bind, ws
-        records.append({"index": int(i), "n": n, "calls": ncalls, "plans": count,
-                        "exhaustive": count <= per_script, "timed": timed})
-        if log:
-            log(f"script {i}: n={n} calls={ncalls} plans={count} timed={len(timed)}")
-    return records
+    return np.array(X, dtype=np.float64), np.array(y, dtype=np.float64), np.array(pu, dtype=np.float64), meta
 
 
 def he_uniform_params(d_in, seed, device):
-    """He-uniform weights from the seeded generator, zero biases (flat libkf layout)."""
+    """He-uniform weights from the seeded generator, zero biases (kf_mlp layout)."""
     H = kf.MLP_HIDDEN
     count = kf.kf_mlp_param_count(d_in)
     u = synth.uniform((count,), seed, synth.TID["mlp"]).double()
@@ -126,12 +137,16 @@ def he_uniform_params(d_in, seed, device):
     return out.float().to(device)
 
 
-def train(X, y, epochs=3000, lr=3e-3, seed=0, device="cuda"):
-    """Full-batch Adam on standardised features; returns (params, mu, sd, losses)."""
-    mu = X.mean(axis=0)
-    sd = X.std(axis=0) + 1e-6
-    Xs = torch.tensor((X - mu) / sd, dtype=torch.float32, device=device)
-    yt = torch.tensor(y, dtype=torch.float32, device=device)
+def train(X, ms, pred_us, analytic_weight=1.0, epochs=3000, lr=3e-3, seed=0, device="cuda"):
+    """Full-batch Adam, all steps in libkf kernels, on standardised features.
+    Target: ln(ms) - analytic_weight * ln(analytic ms), so that with weight
+    1 the network learns the analytic model's error and the score
+    ln(analytic ms) + f(x) ranks plans.  Returns (CostModel, loss history)."""
+    mean = X.mean(axis=0)
+    inv_std = 1.0 / (X.std(axis=0) + 1e-6)
+    Xs = torch.tensor((X - mean) * inv_std, dtype=torch.float32, device=device)
+    target = np.log(ms) - analytic_weight * np.log(np.maximum(pred_us, 1e-3) * 1e-3)
+    yt = torch.tensor(target, dtype=torch.float32, device=device)
     d = X.shape[1]
     p = he_uniform_params(d, seed, device)
     g = torch.empty_like(p)
@@ -139,85 +154,74 @@ def train(X, y, epochs=3000, lr=3e-3, seed=0, device="cuda"):
     v = torch.zeros_like(p)
     loss = torch.empty(1, device=device)
     ws = torch.zeros(kf.kf_mlp_workspace_size(d, X.shape[0]), dtype=torch.uint8, device=device)
-    losses = []
+    hist = []
     for t in range(1, epochs + 1):
         kf.kf_mlp_loss_grad(p, Xs, yt, g, loss, ws)
+        if t == 1 or t % 500 == 0:
+            hist.append((t, float(loss)))
         kf.kf_mlp_adam(p, g, m, v, t, lr=lr)
-        if t == 1 or t % 250 == 0:
-            losses.append((t, float(loss)))
     kf.kf_mlp_loss_grad(p, Xs, yt, g, loss, ws)
-    losses.append((epochs, float(loss)))
-    return p, mu, sd, losses
+    hist.append((epochs + 1, float(loss)))
+    return kf.CostModel(p, mean, inv_std, analytic_weight), hist
 
 
-def predict(p, mu, sd, X, device="cuda"):
-    Xs = torch.tensor((X - mu) / sd, dtype=torch.float32, device=device)
-    out = torch.empty(X.shape[0], device=device)
-    kf.kf_mlp_forward(p, Xs, out)
-    return out.double().cpu().numpy()
+def evaluate(seed, indices, kmin, kmax, model, reps, top_k=3, cap=2000, device="cuda"):
+    """Per held-out script: exhaustive timings, and each method's choice."""
+    rows = []
+    for i in indices:
+        n, sd, s = make(seed, i, kmin, kmax)
+        bind = bindings(sd, i, device)
+        unf = s.plan(kf.KF_PLAN_UNFUSED)
+        ws = torch.zeros(max(s.select_workspace_size(cap), unf.workspace_size(), 256), dtype=torch.uint8,
+                         device=device)
+        t = s.time_all(bind, ws, reps=reps, max_plans=cap)
+        nk = s.enumerate_info(cap)[2]
+        _, ia = s.select(kf.KF_SELECT_ANALYTIC, max_plans=cap)
+        _, i1 = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=1, max_plans=cap)
+        _, ik = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=top_k, reps=reps, max_plans=cap)
+        t_unf = unf.time(bind, ws, reps=reps)
+        best = float(t.min())
+        rows.append({"index": int(i), "n": n, "calls": len(sd["calls"]), "plans": len(t), "best_ms": best,
+                     "mlp": float(t[i1["index"]]) / best, "mlp_topk": float(t[ik["index"]]) / best,
+                     "analytic": float(t[ia["index"]]) / best, "greedy": float(t[int(np.argmin(nk))]) / best,
+                     "unfused": t_unf / best, "timed_topk": ik["timed"]})
+        del bind, ws
+    return rows
 
 
-def score(records, choose):
-    """Ratios t(choice)/t(best) over the records, with choose(record) -> timed index."""
-    r = []
-    for rec in records:
-        ts = np.array([t["ms"] for t in rec["timed"]])
-        j = choose(rec)
-        r.append(float(ts[j] / ts.min()))
-    r = np.array(r)
-    return {"mean_ratio": float(r.mean()), "geomean_ratio": float(np.exp(np.log(r).mean())),
-            "within_5pct": float((r <= 1.05).mean()), "worst": float(r.max()), "ratios": [round(x, 4) for x in r]}
+def summary(rows, key):
+    r = np.array([row[key] for row in rows])
+    return {"mean_ratio": round(float(r.mean()), 4), "geomean_ratio": round(float(np.exp(np.log(r).mean())), 4),
+            "within_5pct": round(float((r <= 1.05).mean()), 4), "worst": round(float(r.max()), 4)}
 
 
-def run(seed=0, scripts=500, ntrain=400, kmin=10, kmax=14, per_script=24, reps=3, epochs=3000, device="cuda",
-        log=print):
+def run(seed=0, scripts=500, ntrain=400, kmin=10, kmax=14, per_script=48, reps=5, epochs=3000, top_k=3,
+        analytic_weight=1.0, device="cuda", log=print):
     t0 = time.time()
-    recs = collect(seed, range(scripts), kmin, kmax, per_script, reps, device=device, log=None)
+    X, ms, pu, meta = collect(seed, range(ntrain), kmin, kmax, per_script, reps, device=device)
     t1 = time.time()
-    train_recs, test_recs = recs[:ntrain], recs[ntrain:]
-    X = np.array([t["feats"] for r in train_recs for t in r["timed"]], dtype=np.float64)
-    y = np.log(np.array([t["ms"] for r in train_recs for t in r["timed"]], dtype=np.float64))
-    p, mu, sd, losses = train(X, y, epochs=epochs, seed=seed, device=device)
+    model, hist = train(X, ms, pu, analytic_weight, epochs=epochs, seed=seed, device=device)
     t2 = time.time()
-
-    def mlp_choice(rec):
-        F = np.array([t["feats"] for t in rec["timed"]])
-        return int(np.argmin(predict(p, mu, sd, F, device)))
-
-    def mlp_top3(rec):
-        F = np.array([t["feats"] for t in rec["timed"]])
-        top = np.argsort(predict(p, mu, sd, F, device))[:3]
-        ts = np.array([rec["timed"][j]["ms"] for j in top])
-        return int(top[int(np.argmin(ts))])
-
-    def analytic_choice(rec):
-        return int(np.argmin([t["pred_us"] for t in rec["timed"]]))
-
-    def greedy_choice(rec):
-        return int(np.lexsort(([t["pred_us"] for t in rec["timed"]], [t["kernels"] for t in rec["timed"]]))[0])
-
-    def unfused_choice(rec):
-        k = [t["kernels"] for t in rec["timed"]]
-        return int(np.argmax(k))
-
+    rows = evaluate(seed, range(ntrain, scripts), kmin, kmax, model, reps, top_k=top_k, device=device)
+    t3 = time.time()
+    plans = np.array([r["plans"] for r in rows])
     out = {
         "config": {"seed": seed, "scripts": scripts, "train": ntrain, "test": scripts - ntrain,
                    "n": f"2^{kmin}..2^{kmax}", "per_script": per_script, "reps": reps, "epochs": epochs,
-                   "features": 16, "hidden": kf.MLP_HIDDEN},
-        "timed_plans": int(sum(len(r["timed"]) for r in recs)),
-        "fully_enumerated_scripts": int(sum(r["exhaustive"] for r in recs)),
-        "collect_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1),
-        "losses": losses,
-        "test": {"mlp": score(test_recs, mlp_choice), "mlp_top3_retimed": score(test_recs, mlp_top3),
-                 "analytic": score(test_recs, analytic_choice), "greedy": score(test_recs, greedy_choice),
-                 "unfused": score(test_recs, unfused_choice)},
-        "train_fit": {"mlp": score(train_recs, mlp_choice), "analytic": score(train_recs, analytic_choice)},
+                   "top_k": top_k, "analytic_weight": analytic_weight, "features": kf.NFEATURES,
+                   "hidden": kf.MLP_HIDDEN},
+        "train_plans_timed": int(len(ms)), "test_plans_timed": int(plans.sum()),
+        "test_plans_per_script": {"mean": float(plans.mean()), "max": int(plans.max())},
+        "seconds": {"collect": round(t1 - t0, 1), "train": round(t2 - t1, 2), "evaluate": round(t3 - t2, 1)},
+        "loss": hist,
+        "test": {k: summary(rows, k) for k in ("mlp", "mlp_topk", "analytic", "greedy", "unfused")},
+        "rows": rows,
     }
     if log:
         for k, v in out["test"].items():
-            log(f"{k:18s} mean {v['mean_ratio']:.4f}  geomean {v['geomean_ratio']:.4f}  "
+            log(f"{k:10s} mean {v['mean_ratio']:.4f}  geomean {v['geomean_ratio']:.4f}  "
                 f"within 5%: {v['within_5pct']:.3f}  worst {v['worst']:.3f}")
-    return out
+    return out, model
 
 
 def main(argv=None):
@@ -227,20 +231,23 @@ def main(argv=None):
     ap.add_argument("--train", type=int, default=400)
     ap.add_argument("--kmin", type=int, default=10)
     ap.add_argument("--kmax", type=int, default=14)
-    ap.add_argument("--per-script", type=int, default=24)
-    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--per-script", type=int, default=48)
+    ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--top-k", type=int, default=3)
+    ap.add_argument("--analytic-weight", type=float, default=1.0)
     ap.add_argument("--out", default="")
+    ap.add_argument("--save-model", default="")
     a = ap.parse_args(argv)
-    from . import _build
-    _build.build()
     kf.lib()
-    res = run(a.seed, a.scripts, a.train, a.kmin, a.kmax, a.per_script, a.reps, a.epochs)
+    res, model = run(a.seed, a.scripts, a.train, a.kmin, a.kmax, a.per_script, a.reps, a.epochs, a.top_k,
+                     a.analytic_weight)
     if a.out:
         with open(a.out, "w") as fh:
             json.dump(res, fh, indent=1)
-    print(json.dumps({k: v for k, v in res.items() if k != "train_fit"} | {
-        "test": {k: {kk: vv for kk, vv in v.items() if kk != "ratios"} for k, v in res["test"].items()}}))
+    if a.save_model:
+        model.save(a.save_model)
+    print(json.dumps({k: v for k, v in res.items() if k != "rows"}))
 
 
 if __name__ == "__main__":
