@@ -263,9 +263,14 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+DIGEST_FILES = ("matprog.cu", "matprog_impl.cuh", "matprog_f32sig.cu", "kf_device.cuh", "kf_internal.h")
+
+
 def kernel_digest() -> str:
+    """Digest of the sources of the BiCGK matrix pass (kernel template, its
+    instances, launch geometry)."""
     h = hashlib.sha256()
-    for f in ("matprog.cu", "kf_device.cuh", "kf_internal.h"):
+    for f in DIGEST_FILES:
         with open(os.path.join(ROOT, "paper_1305_1183_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
