@@ -123,6 +123,29 @@ kf_status kf_gemver(int64_t n, const float* A, int64_t lda, const float* u1, con
                     float beta, float* B, int64_t ldb, float* x, float* w, void* ws,
                     size_t ws_bytes, void* stream);
 
+/* GEMVER with row-scaled low-precision storage (not in the paper, whose
+ * kernels are FP32 only).  A is given as codes QA (fmt BF16 or FP8-E4M3,
+ * row stride lda elements) with per-row scales sA (kf_quantize_rows):
+ * Ahat_ij = sA_i QA_ij.  B = Ahat + u1 v1^T + u2 v2^T is stored in the same
+ * format, codes QB (row stride ldb, must not alias QA) and scales sB, by
+ * this rule (FP32 arithmetic, in this order; QMAX = 1 for BF16, 448 for
+ * E4M3):
+ *   sB_i  = (sA_i * QMAX + |u1_i| max_j |v1_j| + |u2_i| max_j |v2_j|) / QMAX
+ *           (1 when that is 0): a per-row bound on |B_ij|, so no code
+ *           saturates and no second pass over B is needed for its amax;
+ *   b_ij  = fma(u2_i, v2_j, fma(u1_i, v1_j, sA_i * QA_ij));
+ *   QB_ij = round-to-nearest-even of b_ij * (1 / sB_i) into the format
+ *           (E4M3 saturating).
+ * Then x = beta Bhat^T y + z and w = alpha Bhat x with Bhat_ij = sB_i QB_ij,
+ * the stored matrix, accumulated in FP32.  Launches: a norm pre-pass and
+ * the two matrix passes of kf_gemver.  ws: kf_workspace_size(KF_SEQ_GEMVER,
+ * n, n, fmt).  Errors: KF_ERR_DTYPE (fmt KF_F32), KF_ERR_SHAPE, KF_ERR_INVALID_ARG,
+ * KF_ERR_WORKSPACE. */
+kf_status kf_gemver_q(int64_t n, const void* QA, int64_t lda, kf_dtype fmt, const float* sA, const float* u1,
+                      const float* v1, const float* u2, const float* v2, const float* y, const float* z,
+                      float alpha, float beta, void* QB, int64_t ldb, float* sB, float* x, float* w, void* ws,
+                      size_t ws_bytes, void* stream);
+
 /* GESUMMV (Table 1): y = alpha A x + beta B x.  A, B: m x n with the same
  * leading dimension; x: length n; y: length m.  One launch; x is read once
  * per column strip for both matrices. */

@@ -68,6 +68,7 @@ def lib():
         L.kfo_abs_gemvt.argtypes = [i64, i64, d, i64, d, d]
         L.kfo_quantize_rows.argtypes = [i64, i64, fp, i64, ctypes.c_int, vp, fp]
         L.kfo_dequantize_rows.argtypes = [i64, i64, vp, ctypes.c_int, fp, d]
+        L.kfo_gemver_rowscaled_store.argtypes = [i64, vp, ctypes.c_int, fp, fp, fp, fp, fp, vp, fp]
         L.kfo_bf16_value.argtypes = [ctypes.c_uint16]
         L.kfo_bf16_value.restype = dbl
         L.kfo_e4m3_value.argtypes = [ctypes.c_uint8]
@@ -240,6 +241,25 @@ def dequantize_rows(codes, scale, fmt):
     lib().kfo_dequantize_rows(m, n, codes.ctypes.data_as(ctypes.c_void_p), fmt,
                               scale.ctypes.data_as(fp), _p(out))
     return out
+
+
+def gemver_rowscaled(QA, sA, fmt, u1, v1, u2, v2, y, z, alpha, beta):
+    """GEMVER on row-scaled codes: returns (QB, sB, Bhat, x, w) with the
+    storage rule of kfo_gemver_rowscaled_store, then x = beta Bhat^T y + z and
+    w = alpha Bhat x in double on the stored matrix Bhat_ij = sB_i QB_ij."""
+    QA = np.ascontiguousarray(QA)
+    n = QA.shape[0]
+    f32 = [np.ascontiguousarray(np.asarray(a, dtype=np.float32)) for a in (sA, u1, v1, u2, v2)]
+    QB = np.empty_like(QA)
+    sB = np.empty(n, dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib().kfo_gemver_rowscaled_store(n, QA.ctypes.data_as(ctypes.c_void_p), fmt,
+                                     *[a.ctypes.data_as(fp) for a in f32],
+                                     QB.ctypes.data_as(ctypes.c_void_p), sB.ctypes.data_as(fp))
+    Bhat = dequantize_rows(QB, sB, fmt)
+    x = gemvt(Bhat, y, alpha=beta, beta=1.0, x0=z)
+    w = gemv(Bhat, x, alpha=alpha)
+    return QB, sB, Bhat, x, w
 
 
 def bf16_value(code: int) -> float:

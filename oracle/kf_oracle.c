@@ -273,3 +273,41 @@ double kfo_bf16_value(uint16_t h) { return bf16_to_double(h); }
 double kfo_e4m3_value(uint8_t b) { return e4m3_to_double(b); }
 uint16_t kfo_bf16_code(float f) { return f32_to_bf16_rne(f); }
 uint8_t kfo_e4m3_code(float f) { return f32_to_e4m3_rne_sat(f); }
+
+/* GEMVER with row-scaled storage (the library's low-precision GEMVER; the
+ * paper is FP32 only).  A is given as codes QA with row scales sA.  The
+ * storage rule of B = Ahat + u1 v1^T + u2 v2^T, whose codes are integer
+ * decisions taken in FP32 (the precision the rule is stated in):
+ *   sB_i  = (sA_i * QMAX + |u1_i| max_j |v1_j| + |u2_i| max_j |v2_j|) / QMAX,
+ *           left to right, 1 when the bound is 0 (QMAX = 1 BF16, 448 E4M3);
+ *   b_ij  = fma(u2_i, v2_j, fma(u1_i, v1_j, sA_i * QA_ij));
+ *   QB_ij = round-to-nearest-even of b_ij * (1 / sB_i) (E4M3 saturating).
+ * Writes QB (n x n codes, row length n) and sB.  x and w follow in double
+ * from the stored matrix (kfo_dequantize_rows, kfo_gemvt, kfo_gemv). */
+void kfo_gemver_rowscaled_store(int64_t n, const void* qa, int fmt, const float* sa,
+                                const float* u1, const float* v1, const float* u2,
+                                const float* v2, void* qb, float* sb) {
+    const float qmax = (fmt == 2) ? 448.0f : 1.0f;
+    float n1 = 0.0f, n2 = 0.0f;
+    for (int64_t j = 0; j < n; ++j) {
+        if (fabsf(v1[j]) > n1) n1 = fabsf(v1[j]);
+        if (fabsf(v2[j]) > n2) n2 = fabsf(v2[j]);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        float bound = sa[i] * qmax;
+        bound = bound + fabsf(u1[i]) * n1;
+        bound = bound + fabsf(u2[i]) * n2;
+        const float s = (bound > 0.0f) ? bound / qmax : 1.0f;
+        const float inv = 1.0f / s;
+        sb[i] = s;
+        for (int64_t j = 0; j < n; ++j) {
+            const float q = (fmt == 2) ? (float)e4m3_to_double(((const uint8_t*)qa)[i * n + j])
+                                       : (float)bf16_to_double(((const uint16_t*)qa)[i * n + j]);
+            const float a = sa[i] * q;
+            const float b = fmaf(u2[i], v2[j], fmaf(u1[i], v1[j], a));
+            const float t = b * inv;
+            if (fmt == 2) ((uint8_t*)qb)[i * n + j] = f32_to_e4m3_rne_sat(t);
+            else ((uint16_t*)qb)[i * n + j] = f32_to_bf16_rne(t);
+        }
+    }
+}

@@ -284,6 +284,48 @@ kf_status kf_gemver(int64_t n, const float* A, int64_t lda, const float* u1, con
   return run_mat(Q, ws, ws_bytes, stream);
 }
 
+kf_status kf_gemver_q(int64_t n, const void* QA, int64_t lda, kf_dtype fmt, const float* sA, const float* u1,
+                      const float* v1, const float* u2, const float* v2, const float* y, const float* z,
+                      float alpha, float beta, void* QB, int64_t ldb, float* sB, float* x, float* w, void* ws,
+                      size_t ws_bytes, void* stream) {
+  REQ(fmt == KF_BF16_ROWSCALE || fmt == KF_FP8E4M3_ROWSCALE, KF_ERR_DTYPE, "kf_gemver_q takes BF16 or E4M3 codes");
+  CHK(check_mat(n, n, QA, lda));
+  CHK(check_mat(n, n, QB, ldb));
+  REQ(n == 0 || (sA != nullptr && sB != nullptr), KF_ERR_INVALID_ARG, "row scales required");
+  CHK(check_vec(n, u1, "u1")); CHK(check_vec(n, v1, "v1")); CHK(check_vec(n, u2, "u2"));
+  CHK(check_vec(n, v2, "v2")); CHK(check_vec(n, y, "y")); CHK(check_vec(n, z, "z"));
+  CHK(check_vec(n, x, "x")); CHK(check_vec(n, w, "w"));
+  REQ(QB != QA, KF_ERR_SHAPE, "QB must not alias QA");
+  if (n == 0) return KF_OK;
+  REQ(ws != nullptr && ws_bytes >= WS_HEADER, KF_ERR_WORKSPACE, "workspace required");
+  // max |v1|, max |v2| for the row-scale bound, in the workspace header
+  float* norms = reinterpret_cast<float*>(static_cast<char*>(ws) + WS_AUX);
+  const float* vs[2] = {v1, v2};
+  const char* why = nullptr;
+  CHK(from_launch(launch_colnorms(vs, 2, n, norms, stream, &why), why));
+  // Pass 1: B = Ahat + u1 v1^T + u2 v2^T stored as codes + row scales,
+  // x = beta Bhat^T y + z.
+  MatProg P = new_prog(n, n);
+  P.nmat = 1; P.fmt = (int)fmt; P.A[0] = QA; P.rscale[0] = sA; P.lda[0] = lda;
+  P.Bout[0] = static_cast<float*>(QB); P.ldb[0] = ldb; P.Bscale[0] = sB;
+  P.nops = 3;
+  P.ops[0] = op_ger(0, 1.f, u1, v1); P.ops[0].vnorm = norms;
+  P.ops[1] = op_ger(0, 1.f, u2, v2); P.ops[1].vnorm = norms + 1;
+  P.ops[2] = op_gemvt(0, 0, y);
+  P.nrow_res = 1; P.ncol_res = 1;
+  P.ncol_out = 1; P.col_out[0] = epi1(x, beta);
+  epi_add_ext(P.col_out[0], z, 1.f);
+  CHK(run_mat(P, ws, ws_bytes, stream));
+  // Pass 2: w = alpha Bhat x.
+  MatProg Q = new_prog(n, n);
+  Q.nmat = 1; Q.fmt = (int)fmt; Q.A[0] = QB; Q.rscale[0] = sB; Q.lda[0] = ldb;
+  Q.nops = 1;
+  Q.ops[0] = op_gemv(0, 0, x);
+  Q.nrow_res = 1; Q.ncol_res = 1;
+  Q.nrow_out = 1; Q.row_out[0] = epi1(w, alpha);
+  return run_mat(Q, ws, ws_bytes, stream);
+}
+
 kf_status kf_gesummv(int64_t m, int64_t n, const float* A, const float* B, int64_t lda,
                      const float* x, float alpha, float beta, float* y, void* ws, size_t ws_bytes,
                      void* stream) {

@@ -118,40 +118,46 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
   }
 }
 
-// y[c] = sum over blocks b (in order) of ypart[b][c].  256 threads = 32
-// float4 columns x 8 slices; slice s adds blocks s, s+8, ...; the slices are
-// added in slice order, so the result is independent of timing.
-__global__ void __launch_bounds__(256) atax_finish_kernel(const float* __restrict__ ypart, int nparts,
-                                                          int64_t n, float* __restrict__ y) {
+// y[c] = sum over blocks b (in order) of ypart[b][c].  A block covers
+// FIN_COLS float4 columns with FIN_SLICES slices of FIN_COLS threads; slice s
+// adds partials s, s + FIN_SLICES, ... in order, issuing FIN_LOADS loads
+// before their adds; the slices are then added in slice order, so the result
+// is independent of timing.  Narrow blocks spread the partials (a few MB,
+// mostly in L2) over every SM.
+constexpr int FIN_COLS = 8, FIN_SLICES = 32, FIN_LOADS = 8;
+
+__global__ void __launch_bounds__(FIN_COLS * FIN_SLICES) atax_finish_kernel(const float* __restrict__ ypart,
+                                                                            int nparts, int64_t n,
+                                                                            float* __restrict__ y) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  __shared__ float4 sh[8][32];
-  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  __shared__ float4 sh[FIN_SLICES][FIN_COLS];
+  const int col = threadIdx.x % FIN_COLS, slice = threadIdx.x / FIN_COLS;
   const int64_t n4 = n >> 2;
-  const int64_t c4 = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t c4 = (int64_t)blockIdx.x * FIN_COLS + col;
   float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
   if (c4 < n4) {
     const float4* p = reinterpret_cast<const float4*>(ypart) + c4;
     int b = slice;
-    // eight independent loads in flight per step, added in block order
-    for (; b + 7 * 8 < nparts; b += 8 * 8) {
-      float4 v[8];
+    for (; b + (FIN_LOADS - 1) * FIN_SLICES < nparts; b += FIN_LOADS * FIN_SLICES) {
+      float4 v[FIN_LOADS];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = __ldcg(p + (int64_t)(b + 8 * q) * n4);
+      for (int q = 0; q < FIN_LOADS; ++q) v[q] = __ldcg(p + (int64_t)(b + FIN_SLICES * q) * n4);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) { s.x += v[q].x; s.y += v[q].y; s.z += v[q].z; s.w += v[q].w; }
+      for (int q = 0; q < FIN_LOADS; ++q) { s.x += v[q].x; s.y += v[q].y; s.z += v[q].z; s.w += v[q].w; }
     }
-    for (; b < nparts; b += 8) {
+#pragma unroll 4
+    for (; b < nparts; b += FIN_SLICES) {
       const float4 v = __ldcg(p + (int64_t)b * n4);
       s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
     }
   }
-  sh[slice][lane] = s;
+  sh[slice][col] = s;
   __syncthreads();
   if (slice == 0 && c4 < n4) {
-    float4 r = sh[0][lane];
+    float4 r = sh[0][col];
 #pragma unroll
-    for (int q = 1; q < 8; ++q) {
-      r.x += sh[q][lane].x; r.y += sh[q][lane].y; r.z += sh[q][lane].z; r.w += sh[q][lane].w;
+    for (int q = 1; q < FIN_SLICES; ++q) {
+      r.x += sh[q][col].x; r.y += sh[q][col].y; r.z += sh[q][col].z; r.w += sh[q][col].w;
     }
     reinterpret_cast<float4*>(y)[c4] = r;
   }
@@ -213,8 +219,8 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
   if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
 
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((n / 4 + 31) / 32));
-  cfg.blockDim = dim3(256);
+  cfg.gridDim = dim3((unsigned)((n / 4 + FIN_COLS - 1) / FIN_COLS));
+  cfg.blockDim = dim3(FIN_COLS * FIN_SLICES);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = (cudaStream_t)stream;
   cudaLaunchAttribute attr[1];

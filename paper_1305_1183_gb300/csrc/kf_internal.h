@@ -29,6 +29,7 @@ constexpr int EPI_MAXOUT = 4;
 constexpr int MAT_MAXGROUPS = 128;     // bound on row groups (workspace sizing)
 constexpr int MAT_MAXSTAGES = 8;       // bound on the per-warp copy ring depth
 constexpr size_t WS_HEADER = 256;      // every workspace starts with a 256-byte header (error word at 0)
+constexpr size_t WS_AUX = 64;          // header offset of per-launch device scalars (vector norms)
 
 constexpr int VP_MAXIN = 6;
 constexpr int VP_MAXOUT = 4;
@@ -47,6 +48,7 @@ struct MatOp {
   float alpha;           // GER: coefficient of u v^T
   const float* colvec;   // GER: v (length n); GEMV: x (length n)
   const float* rowvec;   // GER: u (length m); GEMVT: y (length m)
+  const float* vnorm;    // GER into a low-precision matrix: device max_j |colvec_j|
 };
 
 // One epilogue output: dst[i] = sum_t coef[t] * (src[t] >= 0 ? raw_src[t][i] : ext[t][i])
@@ -66,8 +68,9 @@ struct MatProg {
   const void* A[2];
   const float* rscale[2];        // per-row scales (low-precision formats)
   int64_t lda[2];
-  float* Bout[2];                // updated matrix output or nullptr
+  float* Bout[2];                // updated matrix output or nullptr (codes when fmt is low precision)
   int64_t ldb[2];
+  float* Bscale[2];              // per-row scales written with a low-precision Bout
   int nops;
   MatOp ops[MAT_MAXOPS];
   int nrow_res, ncol_res;
@@ -117,6 +120,8 @@ struct VecTune {
 
 // Status codes mirror kf.h.
 int launch_matprog(MatProg& P, const MatTune& t, void* stream, const char** why);
+// out[k] = max_j |v_k[j]| for the nv <= 4 vectors v_k of length n (device).
+int launch_colnorms(const float* const* v, int nv, int64_t n, float* out, void* stream, const char** why);
 int launch_vecprog(VecProg& P, const VecTune& t, void* stream, const char** why);
 size_t matprog_workspace_bytes(int64_t m, int64_t n, int nrow_res, int ncol_res, int fmt);
 size_t vecprog_workspace_bytes(int ndot);

@@ -193,7 +193,9 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   const int eb = fmt_bytes(P.fmt);
   for (int t = 0; t < P.nmat; ++t) {
     if (!aligned16(P.A[t]) || ((P.lda[t] * eb) & 15) != 0) vec = false;
-    if (P.Bout[t] != nullptr && (!aligned16(P.Bout[t]) || ((P.ldb[t] * 4) & 15) != 0)) vec = false;
+    // a low-precision pass stores its matrix output as codes of the same format
+    const int ob = P.fmt == FMT_F32 ? 4 : eb;
+    if (P.Bout[t] != nullptr && (!aligned16(P.Bout[t]) || ((P.ldb[t] * ob) & 15) != 0)) vec = false;
   }
   MatTune t = tune;
   // op shape of the instance and its compile-time signature
@@ -232,6 +234,10 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
     if (it == R.end()) { *why = "no kernel instance for this op shape"; return -10; }
   }
   const mp::Entry& e = it->second;
+  if (P.fmt != FMT_F32 && P.Bout[0] != nullptr && (sig == 0 || e.sig != sig)) {
+    *why = "a low-precision matrix output needs a specialised op signature";
+    return -10;
+  }
   const int ch = fmt_ch(P.fmt);
   const int64_t sw = (int64_t)e.nw * 32 * e.v * ch;               // strip width (columns)
   const size_t batch = (size_t)P.nmat * e.u * e.nw * 32 * e.v * 16;  // one ring stage (bytes)

@@ -37,6 +37,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -166,6 +167,81 @@ __device__ __forceinline__ void store_row(float* B, int64_t ldb, int64_t row, in
   }
 }
 
+// Low-precision matrix output (a GER chain stored in the input's format with
+// a per-row scale sB): code = round-to-nearest-even of b * (1 / sB) into the
+// format (E4M3 saturating), then b is replaced by sB * code, the value later
+// readers of the stored matrix see.  One 16-byte chunk of codes per CH
+// values, the layout the loads decode.
+template <int FMT>
+__device__ __forceinline__ uint32_t encode1(float t) {
+  if constexpr (FMT == FMT_BF16) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(t));
+  } else {
+    return (uint32_t)__nv_cvt_float_to_fp8(t, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+template <int FMT>
+__device__ __forceinline__ float decode1(uint32_t c) {
+  if constexpr (FMT == FMT_BF16) {
+    return bf16_bits_to_f32(c);
+  } else {
+    float lo, hi;
+    e4m3x2_to_f32(c, lo, hi);
+    return lo;
+  }
+}
+
+template <int FMT, int V, bool VEC>
+__device__ __forceinline__ void quant_store_row(void* B, int64_t ldb, int64_t row, bool row_ok, int64_t col0,
+                                                int64_t n, int lane, float (&a)[V * FmtT<FMT>::CH], float sB,
+                                                float isB) {
+  constexpr int CH = FmtT<FMT>::CH;
+  constexpr int BYTES = FmtT<FMT>::BYTES;
+  char* rowp = static_cast<char*>(B) + (row * ldb) * BYTES;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    uint32_t code[CH];
+#pragma unroll
+    for (int e = 0; e < CH; ++e) {
+      code[e] = encode1<FMT>(__fmul_rn(a[v * CH + e], isB));
+      a[v * CH + e] = __fmul_rn(sB, decode1<FMT>(code[e]));
+    }
+    if (!row_ok) continue;
+    if constexpr (VEC) {
+      const int64_t c = col0 + coff<CH, V, VEC>(v, 0, lane);
+      if (c + CH <= n) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if constexpr (FMT == FMT_BF16) w[q] = code[2 * q] | (code[2 * q + 1] << 16);
+          else w[q] = code[4 * q] | (code[4 * q + 1] << 8) | (code[4 * q + 2] << 16) | (code[4 * q + 3] << 24);
+        }
+        asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(rowp + c * BYTES), "r"(w[0]),
+                     "r"(w[1]), "r"(w[2]), "r"(w[3])
+                     : "memory");
+      } else {
+#pragma unroll
+        for (int e = 0; e < CH; ++e) {
+          if (c + e < n) {
+            if constexpr (FMT == FMT_BF16) reinterpret_cast<unsigned short*>(rowp)[c + e] = (unsigned short)code[e];
+            else reinterpret_cast<unsigned char*>(rowp)[c + e] = (unsigned char)code[e];
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < CH; ++e) {
+        const int64_t c = col0 + coff<CH, V, VEC>(v, e, lane);
+        if (c < n) {
+          if constexpr (FMT == FMT_BF16) reinterpret_cast<unsigned short*>(rowp)[c] = (unsigned short)code[e];
+          else reinterpret_cast<unsigned char*>(rowp)[c] = (unsigned char)code[e];
+        }
+      }
+    }
+  }
+}
+
 template <int NR>
 __device__ __forceinline__ float pick(const float (&raw)[NR], int s) {
   float v = raw[0];
@@ -244,6 +320,17 @@ constexpr int SIG_BICGK = SIG_SPEC | sig_op(MOP_GEMV, 0) | (sig_op(MOP_GEMVT, 0)
 constexpr int SIG_GEMVER1 = SIG_SPEC | sig_op(MOP_GER, 0) | (sig_op(MOP_GER, 0) << 3) | (sig_op(MOP_GEMVT, 0) << 6);
 constexpr int SIG_GESUMMV = SIG_SPEC | sig_op(MOP_GEMV, 0) | (sig_op(MOP_GEMV, 1) << 3);
 
+// Index of the last GER of a specialised signature (-1: none).  A
+// low-precision instance with such a signature stores the GER chain's result
+// as codes with per-row scales (the kernel quantises right after that op).
+constexpr int sig_last_ger(int sig) {
+  int last = -1;
+  if (sig & SIG_SPEC)
+    for (int k = 0; k < 4; ++k)
+      if (sig_kind(sig, k) == MOP_GER) last = k;
+  return last;
+}
+
 // Resident blocks per SM asked of the register allocator: the one-chunk
 // FP32 forms are latency bound and need four blocks of eight warps.
 template <int NW, int V, int NMAT, int FMT>
@@ -264,6 +351,10 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   static_assert(U == 1 || U == 2 || U == 4 || U == 8, "U must divide 8");
   constexpr int NGA = NG > 0 ? NG : 1;
   constexpr bool SPEC = (SIG & SIG_SPEC) != 0;
+  constexpr int LASTGER = sig_last_ger(SIG);
+  constexpr bool QOUT = FMT != FMT_F32 && LASTGER >= 0;  // low-precision matrix output
+  static_assert(!QOUT || NMAT == 1, "low-precision output: one matrix");
+  constexpr float QMAX = FMT == FMT_E4M3 ? 448.f : 1.f;
   extern __shared__ float4 smem4[];
   __shared__ __align__(8) uint64_t full[STAGED ? MAT_MAXSTAGES : 1];
   __shared__ __align__(8) uint64_t empty[STAGED ? MAT_MAXSTAGES : 1];
@@ -417,6 +508,20 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
 #pragma unroll
       for (int t = 0; t < NMAT; ++t)
         rsc[t] = (FMT != FMT_F32 && lane_row_ok) ? __ldg(P.rscale[t] + row0 + lane) : 1.f;
+      // Per-row scale of a low-precision output: a bound on |B_ij| over the
+      // row, sA_i * QMAX + sum over the GERs of |alpha u_i| * max_j |v_j|,
+      // divided by QMAX (1 for an all-zero bound), in this order.
+      float sbrow = 1.f, isbrow = 1.f;
+      if constexpr (QOUT) {
+        float bound = __fmul_rn(rsc[0], QMAX);
+#pragma unroll
+        for (int k = 0; k <= LASTGER; ++k)
+          if (sig_kind(SIG, k) == MOP_GER)
+            bound = __fadd_rn(bound, __fmul_rn(fabsf(P.ops[k].alpha * rv[k]), __ldg(P.ops[k].vnorm)));
+        sbrow = bound > 0.f ? __fdiv_rn(bound, QMAX) : 1.f;
+        isbrow = __fdiv_rn(1.f, sbrow);
+        if (strip == 0 && warp == 0 && lane_row_ok) P.Bscale[0][row0 + lane] = sbrow;
+      }
       float rowdot[NGA];  // this warp's partial of row row0+lane
 
 #pragma unroll 1
@@ -484,10 +589,18 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
                 };
                 if (NMAT == 1 || opmat == 0) apply(a[0][u]);
                 else apply(a[NMAT - 1][u]);
+                if constexpr (QOUT) {
+                  if (k == LASTGER) {
+                    const int64_t row = row0 + rr;
+                    quant_store_row<FMT, V, VEC>(P.Bout[0], P.ldb[0], row, row < m, wcol0, n, lane, a[0][u],
+                                                 __shfl_sync(FULL_MASK, sbrow, rr),
+                                                 __shfl_sync(FULL_MASK, isbrow, rr));
+                  }
+                }
               }
             }
             const int64_t row = row0 + rr;
-            if (row < m) {
+            if (!QOUT && row < m) {
 #pragma unroll
               for (int t = 0; t < NMAT; ++t)
                 if (P.Bout[t] != nullptr)

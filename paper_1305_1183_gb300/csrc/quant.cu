@@ -51,6 +51,29 @@ __global__ void __launch_bounds__(256) quantize_rows_kernel(const float* __restr
   }
 }
 
+// out[b] = max_j |v_b[j]|: one block per vector, fixed reduction tree
+// (max is exact, so the result does not depend on the order anyway).
+struct NormArgs {
+  const float* v[4];
+};
+
+__global__ void __launch_bounds__(1024) colnorm_kernel(NormArgs a, int64_t n, float* __restrict__ out) {
+  __shared__ float s_max[32];
+  const float* v = a.v[blockIdx.x];
+  float mx = 0.f;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mx = fmaxf(mx, fabsf(__ldg(v + j)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = s_max[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+    if (threadIdx.x == 0) out[blockIdx.x] = mx;
+  }
+}
+
 }  // namespace
 
 int launch_quantize_rows(const float* A, int64_t lda, int64_t m, int64_t n, int fmt, void* Q,
@@ -58,6 +81,16 @@ int launch_quantize_rows(const float* A, int64_t lda, int64_t m, int64_t n, int 
   if (m == 0) return 0;
   if (m > 0x7fffffffLL) { *why = "too many rows"; return -2; }
   quantize_rows_kernel<<<(unsigned)m, 256, 0, (cudaStream_t)stream>>>(A, lda, m, n, fmt, Q, scale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
+  return 0;
+}
+
+int launch_colnorms(const float* const* v, int nv, int64_t n, float* out, void* stream, const char** why) {
+  if (nv < 1 || nv > 4) { *why = "one to four vectors"; return -1; }
+  NormArgs a{};
+  for (int k = 0; k < nv; ++k) a.v[k] = v[k];
+  colnorm_kernel<<<nv, 1024, 0, (cudaStream_t)stream>>>(a, n, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
   return 0;

@@ -50,6 +50,7 @@ _SIGS = {
     "kf_workspace_status": ([vp, vp], ci),
     "kf_bicgk": ([i64, i64, vp, i64, ci, vp, vp, vp, vp, vp, vp, sz, vp], ci),
     "kf_gemver": ([i64, vp, i64, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, sz, vp], ci),
+    "kf_gemver_q": ([i64, vp, i64, ci, vp, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, vp, sz, vp], ci),
     "kf_gesummv": ([i64, i64, vp, vp, i64, vp, f32, f32, vp, vp, sz, vp], ci),
     "kf_atax": ([i64, i64, vp, i64, vp, vp, vp, sz, vp], ci),
     "kf_axpydot": ([i64, vp, vp, vp, f32, vp, vp, vp, sz, vp], ci),
@@ -218,6 +219,14 @@ def kf_gemver(A, u1, v1, u2, v2, y, z, alpha, beta, B, x, w, ws, stream=None):
     n = A.shape[0]
     _ck(lib().kf_gemver(n, _p(A), A.stride(0), _p(u1), _p(v1), _p(u2), _p(v2), _p(y), _p(z),
                         alpha, beta, _p(B), B.stride(0), _p(x), _p(w), _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_gemver_q(QA, fmt, sA, u1, v1, u2, v2, y, z, alpha, beta, QB, sB, x, w, ws, stream=None):
+    """GEMVER on row-scaled codes (int16 BF16 or uint8 E4M3 tensors, n x n);
+    writes codes QB and scales sB of B, x and w."""
+    n = QA.shape[0]
+    _ck(lib().kf_gemver_q(n, _p(QA), QA.stride(0), fmt, _p(sA), _p(u1), _p(v1), _p(u2), _p(v2), _p(y), _p(z),
+                          alpha, beta, _p(QB), QB.stride(0), _p(sB), _p(x), _p(w), _p(ws), _nb(ws), _st(stream)))
 
 
 def kf_gesummv(A, B, x, alpha, beta, y, ws, stream=None):

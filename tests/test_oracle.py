@@ -304,6 +304,66 @@ def test_quantize_error_bound(fmt, rel):
     assert np.allclose(scale, (amax / np.float32(qmax)).astype(np.float32), rtol=0)
 
 
+# ------------------------------------------------------------------ row-scaled GEMVER storage
+
+def _rowscaled_case(fmt, n=40, u2_gain=1.0, zero_u=False, seed=0):
+    A = synth.uniform((n, n), seed, synth.TID["A"]).numpy()
+    QA, sA = oracle.quantize_rows(A, fmt)
+    v = {k: synth.uniform((n,), seed, synth.TID[k]).numpy() for k in ("u1", "v1", "u2", "v2", "y", "z")}
+    v["u2"] = (v["u2"] * np.float32(u2_gain)).astype(np.float32)
+    if zero_u:
+        v["u1"] = np.zeros(n, np.float32)
+        v["u2"] = np.zeros(n, np.float32)
+    return QA, sA, v
+
+
+@pytest.mark.parametrize("fmt,rel,floor", [(oracle.FMT_BF16, 2.0 ** -8, 2.0 ** -126),
+                                           (oracle.FMT_E4M3, 2.0 ** -4, 2.0 ** -6)])
+@pytest.mark.parametrize("u2_gain", [1.0, 64.0])
+def test_gemver_rowscaled_storage_bound(fmt, rel, floor, u2_gain):
+    """The stored B is within half a unit of the format of the exact
+    B = Ahat + u1 v1^T + u2 v2^T (plus the FP32 rounding of b and of
+    b / sB_i), and no row needs saturation: |B_ij| <= sB_i QMAX.  A large u2
+    makes its term dominate the row bound."""
+    QA, sA, v = _rowscaled_case(fmt, u2_gain=u2_gain)
+    QB, sB, Bhat, x, w = oracle.gemver_rowscaled(QA, sA, fmt, v["u1"], v["v1"], v["u2"], v["v2"], v["y"],
+                                                 v["z"], 1.5, 1.2)
+    Ahat = oracle.dequantize_rows(QA, sA, fmt)
+    d = {k: v[k].astype(np.float64) for k in v}
+    B = Ahat + np.outer(d["u1"], d["v1"]) + np.outer(d["u2"], d["v2"])
+    terms = np.abs(Ahat) + np.abs(np.outer(d["u1"], d["v1"])) + np.abs(np.outer(d["u2"], d["v2"]))
+    sBd = sB.astype(np.float64)[:, None]
+    bound = rel * np.maximum(np.abs(B), floor * sBd) * (1 + 2.0 ** -20) + 5 * 2.0 ** -24 * terms * (1 + rel)
+    assert np.all(np.abs(Bhat - B) <= bound)
+    qmax = 448.0 if fmt == oracle.FMT_E4M3 else 1.0
+    assert np.all(np.abs(B) <= sBd * qmax * (1 + 2.0 ** -20))
+    # the bound is tight for at least one row: some |B_ij| reaches a third of it
+    assert np.max(np.abs(B) / (sBd * qmax)) > 1.0 / 3.0
+
+
+@pytest.mark.parametrize("fmt", [oracle.FMT_BF16, oracle.FMT_E4M3])
+def test_gemver_rowscaled_no_update_keeps_codes(fmt):
+    """With u1 = u2 = 0, B = Ahat: the codes come back unchanged and the
+    scale equals the input's (to within one FP32 rounding for QMAX = 448)."""
+    QA, sA, v = _rowscaled_case(fmt, zero_u=True)
+    QB, sB, Bhat, x, w = oracle.gemver_rowscaled(QA, sA, fmt, v["u1"], v["v1"], v["u2"], v["v2"], v["y"],
+                                                 v["z"], 1.5, 1.2)
+    assert np.array_equal(QB, QA)
+    assert np.all(np.abs(sB.astype(np.float64) - sA) <= 2.0 ** -23 * sA)
+
+
+@pytest.mark.parametrize("fmt", [oracle.FMT_BF16, oracle.FMT_E4M3])
+def test_gemver_rowscaled_results_follow_the_stored_matrix(fmt):
+    """x and w are GEMVER's on the stored matrix: the FP64 GEMVER of Bhat with
+    zero updates gives the same x and w."""
+    QA, sA, v = _rowscaled_case(fmt, seed=3)
+    QB, sB, Bhat, x, w = oracle.gemver_rowscaled(QA, sA, fmt, v["u1"], v["v1"], v["u2"], v["v2"], v["y"],
+                                                 v["z"], 1.5, 1.2)
+    zero = np.zeros(len(sA))
+    _, x2, w2 = oracle.gemver(Bhat, zero, zero, zero, zero, v["y"], v["z"], 1.5, 1.2)
+    assert np.array_equal(x, x2) and np.array_equal(w, w2)
+
+
 # ------------------------------------------------------------------ MLP
 
 def _mlp_setup(d=7, H=5, B=11):
