@@ -402,6 +402,182 @@ def time_e2e(suite, steps, warmup, st, seqs):
     return a.elapsed_time(b), h2d, d2h
 
 
+# ---------------------------------------------------------------- precision forms
+
+def time_calls(fn, steps, warmup, st):
+    """Mean ms of fn(st) over `steps` runs on `st` after `warmup` runs (the
+    device is idle first: work queued on other streams would overlap)."""
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        for _ in range(warmup):
+            fn(st)
+    st.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        a.record(st)
+        for _ in range(steps):
+            fn(st)
+        b.record(st)
+    st.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def rel_diff(a, b):
+    """max |a - b| / max |b| (normwise difference of a result from the FP32 path's)."""
+    return float((a.double() - b.double()).abs().max() / b.double().abs().max().clamp_min(1e-300))
+
+
+def precision_section(kf, d, st, steps, warmup, n=16384):
+    """BiCGK and GEMVER at n with A stored FP32, BF16 or FP8-E4M3 (per-row
+    FP32 scales, FP32 vectors and accumulation).  GB/s counts the bytes each
+    form must move (codes, scales, vectors); the error column is the
+    low-precision result's normwise difference from the FP32 path's (the
+    errors against the FP64 oracle are checked by the full-size tests)."""
+    g = lambda shape, tid: synth.uniform(shape, 0, tid, device=d)  # noqa: E731
+    A = g((n, n), synth.TID["A"])
+    p, r = g((n,), synth.TID["p"]), g((n,), synth.TID["r"])
+    vs = {k: g((n,), synth.TID[k]) for k in ("u1", "v1", "u2", "v2", "y", "z")}
+    out = {"n": n, "bicgk": {}, "gemver": {}}
+    ref = {}
+    # FP32 paths
+    q, sv = torch.empty(n, device=d), torch.empty(n, device=d)
+    W = kf.workspace(kf.KF_SEQ_BICGK, n, n)
+    ms = time_calls(lambda s: kf.kf_bicgk(A, p, r, q, sv, W, stream=s), steps, warmup, st)
+    ref["bicgk"] = (q.clone(), sv.clone())
+    b32 = 4 * (n * n + 4 * n)
+    out["bicgk"]["f32"] = {"ms": ms, "gbs": b32 / (ms * 1e-3) / 1e9}
+    B = torch.empty(n, n, device=d)
+    x, w = torch.empty(n, device=d), torch.empty(n, device=d)
+    WG = kf.workspace(kf.KF_SEQ_GEMVER, n, n)
+    ms = time_calls(lambda s: kf.kf_gemver(A, vs["u1"], vs["v1"], vs["u2"], vs["v2"], vs["y"], vs["z"], ALPHA,
+                                           BETA, B, x, w, WG, stream=s), steps, warmup, st)
+    ref["gemver"] = (x.clone(), w.clone())
+    g32 = 4 * (3 * n * n + 9 * n)
+    out["gemver"]["f32"] = {"ms": ms, "gbs": g32 / (ms * 1e-3) / 1e9}
+    del B
+    for name, kfmt, tdt, nb in (("bf16", kf.KF_BF16_ROWSCALE, torch.int16, 2),
+                                ("e4m3", kf.KF_FP8E4M3_ROWSCALE, torch.uint8, 1)):
+        Q = torch.empty((n, n), dtype=tdt, device=d)
+        sA = torch.empty(n, device=d)
+        kf.kf_quantize_rows(A, kfmt, Q, sA)
+        W = kf.workspace(kf.KF_SEQ_BICGK, n, n, kfmt)
+        ms = time_calls(lambda s: kf.kf_bicgk(Q, p, r, q, sv, W, fmt=kfmt, row_scale=sA, n=n, stream=s),
+                        steps, warmup, st)
+        by = nb * n * n + 4 * n + 4 * 4 * n
+        out["bicgk"][name] = {"ms": ms, "gbs": by / (ms * 1e-3) / 1e9,
+                              "speedup_vs_f32": out["bicgk"]["f32"]["ms"] / ms,
+                              "q_rel_diff_vs_f32_path": rel_diff(q, ref["bicgk"][0]),
+                              "s_rel_diff_vs_f32_path": rel_diff(sv, ref["bicgk"][1])}
+        QB = torch.empty_like(Q)
+        sB = torch.empty(n, device=d)
+        WG = kf.workspace(kf.KF_SEQ_GEMVER, n, n, kfmt)
+        ms = time_calls(lambda s: kf.kf_gemver_q(Q, kfmt, sA, vs["u1"], vs["v1"], vs["u2"], vs["v2"], vs["y"],
+                                                 vs["z"], ALPHA, BETA, QB, sB, x, w, WG, stream=s),
+                        steps, warmup, st)
+        by = 3 * nb * n * n + 4 * (3 * n + 9 * n + 2 * n)
+        out["gemver"][name] = {"ms": ms, "gbs": by / (ms * 1e-3) / 1e9,
+                               "speedup_vs_f32": out["gemver"]["f32"]["ms"] / ms,
+                               "x_rel_diff_vs_f32_path": rel_diff(x, ref["gemver"][0]),
+                               "w_rel_diff_vs_f32_path": rel_diff(w, ref["gemver"][1])}
+        del Q, QB
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------- batched form
+
+def batched_shapes(count=4096, lo=32, hi=2048):
+    """(m_i, n_i), each log-uniform in [lo, hi] (seeded)."""
+    ms_ = synth.log_uniform_int(lo, hi, 0, synth.TID["sizes"], count).tolist()
+    ns_ = synth.log_uniform_int(lo, hi, 1, synth.TID["sizes"], count).tolist()
+    return list(zip(ms_, ns_))
+
+
+def make_batched(kind, d, shapes):
+    """Instances packed back to back (matrices with lda = n, vectors in
+    four long buffers) with their descriptors: (descs, views, buffers,
+    algorithmic bytes).  views[i] = (A_i, B_i or None, x_i, r_i, y_i, s_i)."""
+    offs, tot, vm, vn, tm, tn = [], 0, [], [], 0, 0
+    for m, n in shapes:
+        offs.append(tot); vm.append(tm); vn.append(tn)
+        tot += m * n; tm += m; tn += n
+    A = synth.uniform((max(tot, 1),), 0, synth.TID["A"], device=d)
+    Bm = synth.uniform((max(tot, 1),), 0, synth.TID["B"], device=d) if kind == "gesummv" else None
+    X = synth.uniform((max(tn, 1),), 0, synth.TID["x"], device=d)
+    R = synth.uniform((max(tm, 1),), 0, synth.TID["r"], device=d)
+    Y = torch.empty(max(tm, 1), device=d)
+    S = torch.empty(max(tn, 1), device=d)
+    descs, views = [], []
+    for i, (m, n) in enumerate(shapes):
+        a = A[offs[i]:offs[i] + m * n].view(m, n)
+        b = Bm[offs[i]:offs[i] + m * n].view(m, n) if Bm is not None else None
+        x, r = X[vn[i]:vn[i] + n], R[vm[i]:vm[i] + m]
+        y, sv = Y[vm[i]:vm[i] + m], S[vn[i]:vn[i] + n]
+        dd = {"m": m, "n": n, "lda": n, "A": a.data_ptr(), "x": x.data_ptr(), "r": r.data_ptr(),
+              "y": y.data_ptr(), "s": sv.data_ptr(), "alpha": ALPHA, "beta": BETA}
+        if b is not None:
+            dd["B"] = b.data_ptr()
+        descs.append(dd)
+        views.append((a, b, x, r, y, sv))
+    if kind == "bicgk":
+        nbytes = sum(4 * (m * n + 2 * (m + n)) for m, n in shapes)
+    else:
+        nbytes = sum(4 * (2 * m * n + m + n) for m, n in shapes)
+    return descs, views, (A, Bm, X, R, Y, S), nbytes
+
+
+def batched_section(kf, d, st, steps, warmup, count=4096, lo=32, hi=2048):
+    """`count` independent BiCGK and GESUMMV instances, m and n each
+    log-uniform in [lo, hi], matrices packed back to back (lda = n) with
+    offset tables: one persistent launch replayed from a CUDA graph, tile
+    height from the library's autotuner, against the same fused kernel
+    launched once per instance (a stream loop, and the loop captured in a
+    CUDA graph)."""
+    shapes = batched_shapes(count, lo, hi)
+    out = {"instances": count, "m_n_range": [lo, hi], "matrix_elements": sum(m * n for m, n in shapes)}
+    WB = kf.workspace(kf.KF_SEQ_BICGK, hi, hi)
+    WG = kf.workspace(kf.KF_SEQ_GESUMMV, hi, hi)
+    for kind in ("bicgk", "gesummv"):
+        descs, views, bufs, nbytes = make_batched(kind, d, shapes)
+        if kind == "bicgk":
+            seq = kf.KF_SEQ_BICGK
+
+            def one(s, v):
+                kf.kf_bicgk(v[0], v[2], v[3], v[4], v[5], WB, stream=s)
+        else:
+            seq = kf.KF_SEQ_GESUMMV
+
+            def one(s, v):
+                kf.kf_gesummv(v[0], v[1], v[2], ALPHA, BETA, v[4], WG, stream=s)
+        band, _ = kf.kf_batched_autotune(seq, descs, reps=3)
+        bt = kf.Batched(seq, descs, band)
+        ws = torch.zeros(max(bt.workspace_size(), 256), dtype=torch.uint8, device=d)
+        bt.upload(ws)
+        bt.capture(ws)
+        t_graph = time_calls(lambda s: bt.replay(s), steps, warmup, st)
+        loop_steps = max(1, min(steps, 3))
+        t_loop = time_calls(lambda s: [one(s, v) for v in views], loop_steps, 1, st)
+        t_loop_graph = None
+        try:
+            gph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gph, stream=st):
+                for v in views:
+                    one(None, v)
+            t_loop_graph = time_calls(lambda s: gph.replay(), loop_steps, 1, st)
+        except Exception as e:  # capture of per-instance launches is a comparison only
+            out.setdefault("notes", []).append(f"{kind}: per-instance graph capture failed: {e}")
+        out[kind] = {"band_rows": band, "bytes": nbytes, "ms": t_graph, "gbs": nbytes / (t_graph * 1e-3) / 1e9,
+                     "per_instance_loop_ms": t_loop,
+                     "per_instance_graph_ms": t_loop_graph,
+                     "speedup_vs_per_instance_loop": t_loop / t_graph,
+                     "speedup_vs_per_instance_graph": (t_loop_graph / t_graph) if t_loop_graph else None}
+        del bt, ws, bufs, views, descs
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- CPU oracle
 
 def oracle_sample(sizes, frac_rows: int):
@@ -507,6 +683,10 @@ def main():
     ap.add_argument("--seqs", default=",".join(SEQS), help="comma-separated subset of the suite")
     ap.add_argument("--bicgk", type=int, default=0, help="square BiCGK size override (profiling)")
     ap.add_argument("--mat-tuning", default="", help="warps,vec,unroll,groups,stages for matrix passes")
+    ap.add_argument("--no-precision", action="store_true", help="skip the BF16 / FP8 section")
+    ap.add_argument("--autotune", type=int, default=3,
+                    help="timed runs per candidate of the first-use tuning search (0: built-in defaults)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-instances section")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
 
@@ -538,6 +718,9 @@ def main():
 
     if args.mat_tuning:
         kf.kf_set_matrix_tuning(*[int(v) for v in args.mat_tuning.split(",")])
+    elif args.autotune > 0:
+        # every kernel shape is searched on its first (warm-up) launch
+        kf.kf_set_autotune(args.autotune)
     suite = Suite(kf, sizes, torch.device("cuda", local), seqs=seqs)
     st = torch.cuda.Stream()
     torch.cuda.synchronize()
@@ -557,6 +740,16 @@ def main():
     unf_total, unf_per = None, {}
     if not args.no_unfused:
         unf_total, unf_per = time_suite(suite, "unfused", args.steps, args.warmup, st, seqs)
+
+    extra = {}
+    if not args.small and args.bicgk == 0 and seqs == SEQS:
+        del suite
+        torch.cuda.empty_cache()
+        if not args.no_precision:
+            extra["precision"] = precision_section(kf, torch.device("cuda", local), st, args.steps, args.warmup)
+        if not args.no_batched:
+            extra["batched"] = batched_section(kf, torch.device("cuda", local), st, args.steps, args.warmup)
+        suite = Suite(kf, sizes, torch.device("cuda", local), seqs=seqs)
 
     e2e = None
     if not args.no_e2e:
@@ -603,6 +796,9 @@ def main():
                    else f"subset {seqs}, sizes {[sizes[s] for s in seqs]}",
                    "l2": "inputs larger than L2 (every matrix / long vector exceeds 129 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
+                   "tuning": (f"fixed {args.mat_tuning}" if args.mat_tuning else
+                              f"autotuned on first use ({args.autotune} timed runs per candidate)"
+                              if args.autotune > 0 else "built-in defaults"),
                    "alpha": ALPHA, "beta": BETA},
         "frac_of_peak": value / peak, "frac_of_nominal_8TBs": value / NOMINAL_HBM_GBS,
         "peak_hbm_gbs": peak, "peak_kind": peak_kind,
@@ -616,6 +812,7 @@ def main():
         line["e2e"] = {"value": world * step_bytes / (e2e_ms / e2e_steps * 1e-3) / 1e9, "unit": "GB/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": e2e_ms / e2e_steps}
+    line.update(extra)
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

@@ -222,7 +222,7 @@ kf_status kf_quantize_rows(int64_t m, int64_t n, const float* A, int64_t lda, kf
  * Tuning (Section 3.2: block size and serial iterations are part of a
  * fusion implementation).  A tuning applies to matrix passes launched
  * afterwards in the calling process.  warps in {4, 8}; vec (16-byte chunks
- * per lane per row) in {1, 2, 4}; unroll (rows per batch) in {1, 2, 4};
+ * per lane per row) in {1, 2, 4}; unroll (rows per batch) in {1, 2, 4, 8};
  * groups = row groups per column strip (0 = fill one wave of resident
  * blocks); stages = depth of each warp's bulk-copy ring (1..8), or 0 for
  * direct 16-byte loads.  warps = 0 restores the automatic choice (the
@@ -406,6 +406,18 @@ kf_status kf_plan_time_all(const kf_script* s, int max_plans, void* const* bindi
  * ---------------------------------------------------------------------- */
 kf_status kf_autotune_plan(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
                            void* stream, int reps, float* tuned_ms, float* auto_ms);
+/* Tuning on first use.  reps > 0: every automatic matrix- or vector-pass
+ * launch (any entry point, no tuning fixed by kf_set_matrix_tuning) whose
+ * tuning-cache key has no entry first runs the empirical search of
+ * kf_autotune_plan on its own operands, `reps` timed runs per candidate,
+ * synchronously, and stores the winner; later launches of the key take it
+ * from the cache.  The search runs the call's kernel repeatedly, so calls
+ * that update an operand in place (GER into its own input, in-place GEMVER)
+ * must not make a first launch of a key while it is enabled.  No search
+ * runs while the stream is being captured.  reps = 0 (the default) turns
+ * it off; reps > 100 is KF_ERR_INVALID_ARG. */
+kf_status kf_set_autotune(int reps);
+kf_status kf_get_autotune(int* reps);
 kf_status kf_tune_cache_clear(void);
 kf_status kf_tune_cache_entries(int* n);
 kf_status kf_tune_cache_save(const char* path);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -20,6 +21,7 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
                        const char** why);
 int launch_quantize_rows(const float* A, int64_t lda, int64_t m, int64_t n, int fmt, void* Q,
                          float* scale, void* stream, const char** why);
+extern std::atomic<int> g_autotune_reps;
 
 namespace {
 thread_local std::string g_err;
@@ -508,6 +510,18 @@ kf_status kf_quantize_rows(int64_t m, int64_t n, const float* A, int64_t lda, kf
   return from_launch(launch_quantize_rows(A, lda, m, n, (int)fmt, Q, row_scale, stream, &why), why);
 }
 
+kf_status kf_set_autotune(int reps) {
+  REQ(reps >= 0 && reps <= 100, KF_ERR_INVALID_ARG, "reps must be in 0..100");
+  g_autotune_reps.store(reps);
+  return KF_OK;
+}
+
+kf_status kf_get_autotune(int* reps) {
+  REQ(reps != nullptr, KF_ERR_INVALID_ARG, "null output");
+  *reps = g_autotune_reps.load();
+  return KF_OK;
+}
+
 kf_status kf_set_matrix_tuning(int warps, int vec, int unroll, int groups, int stages) {
   if (warps == 0) {  // back to the automatic choice
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -516,7 +530,7 @@ kf_status kf_set_matrix_tuning(int warps, int vec, int unroll, int groups, int s
   }
   REQ(warps == 4 || warps == 8, KF_ERR_INVALID_ARG, "warps must be 4 or 8 (0 = automatic)");
   REQ(vec == 1 || vec == 2 || vec == 4, KF_ERR_INVALID_ARG, "vec must be 1, 2 or 4");
-  REQ(unroll == 1 || unroll == 2 || unroll == 4, KF_ERR_INVALID_ARG, "unroll must be 1, 2 or 4");
+  REQ(unroll == 1 || unroll == 2 || unroll == 4 || unroll == 8, KF_ERR_INVALID_ARG, "unroll must be 1, 2, 4 or 8");
   REQ(groups >= 0 && groups <= MAT_MAXGROUPS, KF_ERR_INVALID_ARG, "groups out of range");
   REQ(stages >= 0 && stages <= MAT_MAXSTAGES, KF_ERR_INVALID_ARG, "stages out of range");
   std::lock_guard<std::mutex> g(g_tune_mu);

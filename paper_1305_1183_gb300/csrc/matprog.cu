@@ -2,6 +2,7 @@
 // matprog_impl.cuh for the requested op shape, storage format and tuning,
 // sizes the grid to one wave of resident blocks, and binds the workspace.
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -185,6 +186,18 @@ void op_shape(const MatProg& P, int* sig, int* shape_nops, int* shape_ng, int* n
   *ngemv_out = ngemv;
 }
 
+int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* best_ms, float* auto_ms);
+
+// Tuning on first use (kf_set_autotune): timed runs per candidate, 0 = off.
+std::atomic<int> g_autotune_reps{0};
+thread_local bool g_in_search = false;
+
+bool tune_on_first_use(void* stream) {
+  if (g_autotune_reps.load() <= 0 || g_in_search) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing((cudaStream_t)stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+
 int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** why) {
   ensure_registry();
   auto& R = mp::registry();
@@ -203,13 +216,26 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   op_shape(P, &sig, &shape_nops, &shape_ng, &ngemv);
   if (ngemv > 2 || P.nrow_res > 2) { *why = "at most two GEMV results per matrix pass"; return -10; }
   if (t.warps == 0) {
-    // automatic: the tuning cache, else the best measured forms on GB300
-    // (BiCGK 16384^2, GEMVER and GESUMMV 8192^2): direct 16-byte loads,
-    // one chunk per lane, 4 rows per batch
+    // automatic: the tuning cache; on a miss, the empirical search when
+    // tuning on first use is enabled (not inside a search, not while the
+    // stream is being captured), else the best measured forms on GB300
+    // (BiCGK 16384^2, GEMVER and GESUMMV 8192^2): direct 16-byte loads, one
+    // chunk per lane, 4 rows per batch for FP32, 8 for the row-scaled formats
     if (!tune_cache_get_mat(mat_cache_key(P, sig, shape_nops, shape_ng), &t)) {
-      if (P.fmt == FMT_BF16) t = MatTune{8, 2, 2, 0, 0};
-      else if (P.fmt == FMT_E4M3) t = MatTune{8, 1, 2, 0, 0};
-      else t = MatTune{8, 1, 4, 0, 0};
+      bool tuned = false;
+      if (tune_on_first_use(stream)) {
+        MatTune bt{};
+        float bm = 0.f;
+        g_in_search = true;
+        tuned = autotune_matprog(P, stream, g_autotune_reps.load(), &bt, &bm, nullptr) == 0;
+        g_in_search = false;
+        if (tuned) t = bt;
+      }
+      if (!tuned) {
+        // row-scaled formats: packed chunks, 8 rows in flight
+        if (P.fmt != FMT_F32) t = MatTune{8, 1, 8, 0, 0};
+        else t = MatTune{8, 1, 4, 0, 0};
+      }
     }
   }
   bool staged = vec && t.stages > 0;

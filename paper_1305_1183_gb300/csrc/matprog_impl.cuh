@@ -139,6 +139,38 @@ __device__ __forceinline__ void load_row(const void* A, int64_t lda, int64_t row
   }
 }
 
+// Raw 16-byte chunks of a row (low-precision formats, 16-byte loads): the
+// codes stay packed until the row is used, so a batch of rows in flight
+// costs 4 registers per chunk instead of CH.  Chunks past the end of the
+// row are assembled element by element (code 0 beyond n).
+template <int FMT, int V>
+__device__ __forceinline__ void load_row_raw(const void* A, int64_t lda, int64_t row, bool row_ok, int64_t col0,
+                                             int64_t n, int lane, uint4 (&q)[V]) {
+  constexpr int CH = FmtT<FMT>::CH;
+  constexpr int BYTES = FmtT<FMT>::BYTES;
+  const char* rowp = static_cast<const char*>(A) + (row * lda) * BYTES;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int64_t c = col0 + coff<CH, V, true>(v, 0, lane);
+    if (row_ok && c + CH <= n) {
+      q[v] = ld_stream16(rowp + c * BYTES);
+    } else {
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      if (row_ok) {
+#pragma unroll
+        for (int e = 0; e < CH; ++e) {
+          if (c + e < n) {
+            const uint32_t code = BYTES == 2 ? (uint32_t) reinterpret_cast<const unsigned short*>(rowp)[c + e]
+                                             : (uint32_t) reinterpret_cast<const unsigned char*>(rowp)[c + e];
+            w[e * BYTES / 4] |= code << (8 * ((e * BYTES) & 3));
+          }
+        }
+      }
+      q[v] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
 template <int CH, int V, bool VEC>
 __device__ __forceinline__ void store_row(float* B, int64_t ldb, int64_t row, int64_t col0,
                                           int64_t n, int lane, const float (&a)[V * CH]) {
@@ -333,11 +365,17 @@ constexpr int sig_last_ger(int sig) {
 
 // Resident blocks per SM asked of the register allocator: the one-chunk
 // FP32 forms are latency bound and need four blocks of eight warps.
-template <int NW, int V, int NMAT, int FMT>
-constexpr int min_blocks() { return (NW == 8 && V == 1 && NMAT == 1 && FMT == FMT_F32) ? 4 : 1; }
+template <int NW, int V, int NMAT, int FMT, bool VEC>
+constexpr int min_blocks() {
+  return (NW == 8 && V == 1 && NMAT == 1 && FMT == FMT_F32) ? 4 : ((FMT != FMT_F32 && VEC) ? 2 : 1);
+}
+
+// Registers of one batch of rows: decoded floats, or packed chunks.
+template <bool RAW, int NMAT, int U, int V, int W> struct BatchOf { using type = float[NMAT][U][W]; };
+template <int NMAT, int U, int V, int W> struct BatchOf<true, NMAT, U, V, W> { using type = uint4[NMAT][U][V]; };
 
 template <int NW, int V, int U, int NOPS, int NMAT, int NG, int FMT, bool VEC, bool STAGED, int SIG>
-__global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, V, NMAT, FMT>()))
+__global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, V, NMAT, FMT, VEC>()))
     matprog_kernel(const __grid_constant__ MatProg P) {
   constexpr int CH = FmtT<FMT>::CH;
   constexpr int BYTES = FmtT<FMT>::BYTES;
@@ -355,6 +393,9 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   constexpr bool QOUT = FMT != FMT_F32 && LASTGER >= 0;  // low-precision matrix output
   static_assert(!QOUT || NMAT == 1, "low-precision output: one matrix");
   constexpr float QMAX = FMT == FMT_E4M3 ? 448.f : 1.f;
+  // low-precision 16-byte loads keep their chunks packed until the row is used
+  constexpr bool RAW = FMT != FMT_F32 && VEC;
+  using BatchT = typename BatchOf<RAW, NMAT, U, V, W>::type;
   extern __shared__ float4 smem4[];
   __shared__ __align__(8) uint64_t full[STAGED ? MAT_MAXSTAGES : 1];
   __shared__ __align__(8) uint64_t empty[STAGED ? MAT_MAXSTAGES : 1];
@@ -449,7 +490,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
     }
     bool dead = false;  // block-uniform in effect: set from s_abort
 
-    auto load_batch = [&](int64_t row0, int r, int64_t jj, float (&a)[NMAT][U][W]) {
+    auto load_batch = [&](int64_t row0, int r, int64_t jj, BatchT& a) {
       if (ring) {
         const int s = (int)(jj % S);
         bool ok = false;
@@ -470,7 +511,11 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
           for (int t = 0; t < NMAT; ++t)
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-              if (row_ok) {
+              if constexpr (RAW) {
+                a[t][u][v] = row_ok ? *reinterpret_cast<const uint4*>(stage + (size_t)(t * U + u) * SEG +
+                                                                        (size_t)(v * 32 + lane) * 16)
+                                    : make_uint4(0u, 0u, 0u, 0u);
+              } else if (row_ok) {
                 const uint4 q = *reinterpret_cast<const uint4*>(stage + (size_t)(t * U + u) * SEG +
                                                                  (size_t)(v * 32 + lane) * 16);
                 decode16<FMT>(q, &a[t][u][v * CH]);
@@ -487,8 +532,10 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
         for (int u = 0; u < U; ++u) {
           const int64_t row = row0 + r + u;
 #pragma unroll
-          for (int t = 0; t < NMAT; ++t)
-            load_row<FMT, V, VEC>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u]);
+          for (int t = 0; t < NMAT; ++t) {
+            if constexpr (RAW) load_row_raw<FMT, V>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u]);
+            else load_row<FMT, V, VEC>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u]);
+          }
         }
       }
     };
@@ -534,22 +581,29 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
 #pragma unroll
         for (int r16 = 0; r16 < 8; r16 += U) {
           const int r = h * 8 + r16;
-          float a[NMAT][U][W];
+          BatchT a;
           load_batch(row0, r, j, a);
           ++j;
-          if constexpr (FMT != FMT_F32) {
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-              for (int t = 0; t < NMAT; ++t) {
-                const float sc = __shfl_sync(FULL_MASK, rsc[t], r + u);
-#pragma unroll
-                for (int e = 0; e < W; ++e) a[t][u][e] *= sc;
-              }
-          }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int rr = r + u;
+            // the row's values: decoded, then scaled by the row's scale
+            float ar[NMAT][W];
+#pragma unroll
+            for (int t = 0; t < NMAT; ++t) {
+              if constexpr (RAW) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) decode16<FMT>(a[t][u][v], &ar[t][v * CH]);
+              } else {
+#pragma unroll
+                for (int e = 0; e < W; ++e) ar[t][e] = a[t][u][e];
+              }
+              if constexpr (FMT != FMT_F32) {
+                const float sc = __shfl_sync(FULL_MASK, rsc[t], rr);
+#pragma unroll
+                for (int e = 0; e < W; ++e) ar[t][e] *= sc;
+              }
+            }
 #pragma unroll
             for (int k = 0; k < NOPS; ++k) {
               if (SPEC || k < nops) {
@@ -587,12 +641,12 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
                     for (int e = 0; e < W; ++e) cv[k][e] = fmaf(t[e], y, cv[k][e]);
                   }
                 };
-                if (NMAT == 1 || opmat == 0) apply(a[0][u]);
-                else apply(a[NMAT - 1][u]);
+                if (NMAT == 1 || opmat == 0) apply(ar[0]);
+                else apply(ar[NMAT - 1]);
                 if constexpr (QOUT) {
                   if (k == LASTGER) {
                     const int64_t row = row0 + rr;
-                    quant_store_row<FMT, V, VEC>(P.Bout[0], P.ldb[0], row, row < m, wcol0, n, lane, a[0][u],
+                    quant_store_row<FMT, V, VEC>(P.Bout[0], P.ldb[0], row, row < m, wcol0, n, lane, ar[0],
                                                  __shfl_sync(FULL_MASK, sbrow, rr),
                                                  __shfl_sync(FULL_MASK, isbrow, rr));
                   }
@@ -604,7 +658,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
 #pragma unroll
               for (int t = 0; t < NMAT; ++t)
                 if (P.Bout[t] != nullptr)
-                  store_row<CH, V, VEC>(P.Bout[t], P.ldb[t], row, wcol0, n, lane, a[t][u]);
+                  store_row<CH, V, VEC>(P.Bout[t], P.ldb[t], row, wcol0, n, lane, ar[t]);
             }
           }
         }
@@ -797,6 +851,15 @@ void reg_sigs() {
   reg<NW, V, U, 2, 1, 1, FMT, VEC, STAGED, SIG_BICGK>();
   reg<NW, V, U, 3, 1, 0, FMT, VEC, STAGED, SIG_GEMVER1>();
   reg<NW, V, U, 2, 2, 2, FMT, VEC, STAGED, SIG_GESUMMV>();
+}
+
+// Signatures a row-scaled matrix takes (BiCGK, GEMV, GEMVT, GEMVER pass 1).
+template <int NW, int V, int U, int FMT, bool VEC, bool STAGED>
+void reg_lowp_sigs() {
+  reg<NW, V, U, 1, 1, 1, FMT, VEC, STAGED, SIG_GEMV>();
+  reg<NW, V, U, 1, 1, 0, FMT, VEC, STAGED, SIG_GEMVT>();
+  reg<NW, V, U, 2, 1, 1, FMT, VEC, STAGED, SIG_BICGK>();
+  reg<NW, V, U, 3, 1, 0, FMT, VEC, STAGED, SIG_GEMVER1>();
 }
 
 void register_f32_staged();

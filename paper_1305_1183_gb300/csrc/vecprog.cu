@@ -9,6 +9,7 @@
 // count), writes each output once, and reduces the dot products per block;
 // the last block to finish adds the per-block partials in block order
 // (Section 3.2.2, option (ii)), in double when the vectors are long.
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -274,12 +275,27 @@ size_t vecprog_workspace_bytes(int ndot) {
 
 std::string vec_cache_key(const VecProg& P);
 bool tune_cache_get_vec(const std::string& k, VecTune* t);
+extern std::atomic<int> g_autotune_reps;
+extern thread_local bool g_in_search;
+bool tune_on_first_use(void* stream);
+int autotune_vecprog(VecProg& P, void* stream, int reps, VecTune* best, float* best_ms, float* auto_ms);
 void tune_cache_put_vec(const std::string& k, const VecTune& t);
 
 int launch_vecprog(VecProg& P, const VecTune& tune_in, void* stream, const char** why) {
   ensure_vregistry();
   VecTune tune = tune_in;
-  if (tune.unroll == 0 && !tune_cache_get_vec(vec_cache_key(P), &tune)) tune = VecTune{256, 4, 0};
+  if (tune.unroll == 0 && !tune_cache_get_vec(vec_cache_key(P), &tune)) {
+    bool tuned = false;
+    if (tune_on_first_use(stream)) {
+      VecTune bt{};
+      float bm = 0.f;
+      g_in_search = true;
+      tuned = autotune_vecprog(P, stream, g_autotune_reps.load(), &bt, &bm, nullptr) == 0;
+      g_in_search = false;
+      if (tuned) tune = bt;
+    }
+    if (!tuned) tune = VecTune{256, 4, 0};
+  }
   bool vec = true;
   for (int k = 0; k < P.nin; ++k) vec = vec && al16(P.in[k]);
   for (int j = 0; j < P.nout; ++j) vec = vec && al16(P.out[j]);

@@ -108,6 +108,8 @@ _SIGS = {
     "kf_plan_execute": ([vp, ctypes.POINTER(vp), ci, vp, sz, vp], ci),
     "kf_plan_time": ([vp, ctypes.POINTER(vp), ci, vp, sz, vp, ci, ctypes.POINTER(ctypes.c_float)], ci),
     "kf_get_matrix_tuning": ([ctypes.POINTER(ci)] * 5, ci),
+    "kf_set_autotune": ([ci], ci),
+    "kf_get_autotune": ([ctypes.POINTER(ci)], ci),
     "kf_plan_select_workspace_size": ([vp, ci, ctypes.POINTER(sz)], ci),
     "kf_plan_select": ([vp, vp, vp, ctypes.POINTER(vp), ci, vp, sz, vp, ctypes.POINTER(vp), vp], ci),
     "kf_plan_time_all": ([vp, ci, ctypes.POINTER(vp), ci, vp, sz, vp, ci, ctypes.POINTER(ctypes.c_float),
@@ -613,6 +615,17 @@ class Batched:
 
     def replay(self, stream=None):
         _ck(lib().kf_batched_graph_launch(self.graph, _st(stream)))
+
+
+def kf_set_autotune(reps):
+    """Tuning on first use: reps > 0 searches every new tuning key on its first launch."""
+    _ck(lib().kf_set_autotune(reps))
+
+
+def kf_get_autotune():
+    r = ci(0)
+    _ck(lib().kf_get_autotune(ctypes.byref(r)))
+    return r.value
 
 
 def kf_tune_cache_clear():

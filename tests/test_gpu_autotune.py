@@ -84,3 +84,48 @@ def test_batched_autotune(built):
         descs.append({"m": m, "n": n, "lda": n, "A": A, "x": x, "r": r, "y": y, "s": s})
     br, t = kf.kf_batched_autotune(kf.KF_SEQ_BICGK, descs, reps=3)
     assert br in (32, 64, 128, 256, 512) and t > 0
+
+
+def test_tune_on_first_use(built):
+    """kf_set_autotune: the first automatic launch of a key runs the search
+    and fills the cache (matrix and vector passes); results keep parity; a
+    second launch of the key adds no entry; capture does not search."""
+    kf = built
+    kf.kf_tune_cache_clear()
+    kf.kf_set_autotune(2)
+    try:
+        m, n = 3000, 2048
+        b = bind_bicgk(m, n)
+        W = kf.workspace(kf.KF_SEQ_BICGK, m, n)
+        kf.kf_bicgk(b["A"], b["p"], b["r"], b["q"], b["s"], W)
+        e1 = kf.kf_tune_cache_entries()
+        assert e1 == 1
+        kf.kf_bicgk(b["A"], b["p"], b["r"], b["q"], b["s"], W)
+        assert kf.kf_tune_cache_entries() == e1
+        Ah, ph, rh = host(b["A"]), host(b["p"]), host(b["r"])
+        qo, so = oracle.bicgk(Ah, ph, rh)
+        check_reduce(host(b["q"]), qo, oracle.abs_gemv(Ah, ph), n, "q")
+        check_reduce(host(b["s"]), so, oracle.abs_gemvt(Ah, rh), m, "s")
+        # a vector pass: AXPYDOT
+        k = 1 << 20
+        w, v, u = (synth.uniform((k,), 0, t, device=dev()) for t in (10, 11, 12))
+        z = torch.empty(k, device=dev()); r = torch.empty(1, device=dev())
+        kf.kf_axpydot(w, v, u, 1.5, z, r, kf.workspace(kf.KF_SEQ_AXPYDOT, 1, k))
+        assert kf.kf_tune_cache_entries() == e1 + 1
+        zo, ro = oracle.axpydot(host(w), host(v), host(u), 1.5)
+        assert abs(float(r[0]) - ro) <= 1e-5 * np.sqrt(k) * float(np.sum(np.abs(zo) * np.abs(host(u))))
+        # capture: a new key is not searched (and the launch is recorded)
+        b2 = bind_bicgk(700, 900)
+        W2 = kf.workspace(kf.KF_SEQ_BICGK, 700, 900)
+        st = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            kf.kf_bicgk(b2["A"], b2["p"], b2["r"], b2["q"], b2["s"], W2)
+        assert kf.kf_tune_cache_entries() == e1 + 1
+        g.replay()
+        torch.cuda.synchronize()
+        Ah, ph = host(b2["A"]), host(b2["p"])
+        check_reduce(host(b2["q"]), oracle.gemv(Ah, ph), oracle.abs_gemv(Ah, ph), 900, "q captured")
+    finally:
+        kf.kf_set_autotune(0)
