@@ -346,6 +346,7 @@ class ClockSampler:
 def time_suite(suite, mode, steps, warmup, st, seqs):
     """Warm up, then time `steps` passes; per-sequence CUDA events on `st`."""
     call = suite.fused if mode == "fused" else suite.unfused
+    torch.cuda.synchronize()  # inputs come from other streams
     with torch.cuda.stream(st):
         for _ in range(warmup):
             for s in seqs:
@@ -387,6 +388,7 @@ def time_e2e(suite, steps, warmup, st, seqs):
             for dst, src in zip(hout[s], suite.outputs(s)):
                 dst.copy_(src, non_blocking=True)
 
+    torch.cuda.synchronize()
     with torch.cuda.stream(st):
         for _ in range(warmup):
             one()

@@ -394,13 +394,15 @@ kf_status kf_plan_time_all(const kf_script* s, int max_plans, void* const* bindi
  * kf_autotune_plan runs, for every kernel of the plan on the bound data,
  * each compiled implementation that fits its op shape (warps, 16-byte chunks
  * per lane, rows per batch, direct loads or a bulk-copy ring of depth 2..4;
- * for vector passes rows in flight and grid size) `reps` times and stores
- * the fastest in a process-wide tuning cache keyed by op signature, storage
+ * for vector passes rows in flight and grid size), each timed as the mean
+ * of `reps` back-to-back launches (best of two rounds, after a warm-up of
+ * the current choice), and stores the fastest in a process-wide tuning
+ * cache keyed by op signature, storage
  * format and size class (powers of two of m and n).  Automatic launches
  * (every entry point, unless kf_set_matrix_tuning fixed a tuning) consult
  * the cache.  Synchronous; it writes the plan's outputs and in-place
- * operands.  *tuned_ms / *auto_ms: sum over kernels of the best median and
- * of the median with the tuning the cache had before.  The cache can be
+ * operands.  *tuned_ms / *auto_ms: sum over kernels of the best time and
+ * of the time with the tuning the cache had before.  The cache can be
  * saved and loaded (text, keyed by device name and SM count; entries for
  * another device are ignored).
  * ---------------------------------------------------------------------- */

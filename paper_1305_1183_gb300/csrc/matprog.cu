@@ -226,9 +226,7 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
       if (tune_on_first_use(stream)) {
         MatTune bt{};
         float bm = 0.f;
-        g_in_search = true;
         tuned = autotune_matprog(P, stream, g_autotune_reps.load(), &bt, &bm, nullptr) == 0;
-        g_in_search = false;
         if (tuned) t = bt;
       }
       if (!tuned) {
@@ -307,7 +305,15 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
 // 2/3/4) is launched `reps` times after one warm-up and the median event
 // time kept; the best goes to the tuning cache.  Synchronous; P must be
 // bound (pointers and workspace).  In-place operands are overwritten.
+// Marks the calling thread as inside a search (no nested first-use tuning).
+struct SearchScope {
+  bool was;
+  SearchScope() : was(g_in_search) { g_in_search = true; }
+  ~SearchScope() { g_in_search = was; }
+};
+
 int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* best_ms, float* auto_ms) {
+  SearchScope scope;
   ensure_registry();
   auto& R = mp::registry();
   int sig = 0, shape_nops = 0, shape_ng = 0, ngemv = 0;
@@ -330,25 +336,32 @@ int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* b
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
+  // Mean of `reps` back-to-back launches between one pair of events (the
+  // GPU stays busy, so host launch latency is not timed), best of two rounds.
   auto time_one = [&](const MatTune& t, float* ms) -> int {
     const char* why = nullptr;
     int rc = launch_matprog(P, t, stream, &why);
     if (rc != 0) return rc;
-    std::vector<float> v;
-    for (int r = 0; r < reps; ++r) {
+    float bestr = 1e30f;
+    for (int round = 0; round < 2; ++round) {
       cudaEventRecord(a, st);
-      rc = launch_matprog(P, t, stream, &why);
+      for (int r = 0; r < reps && rc == 0; ++r) rc = launch_matprog(P, t, stream, &why);
       cudaEventRecord(b, st);
       cudaEventSynchronize(b);
+      if (rc != 0) return rc;
       float x = 0.f;
       cudaEventElapsedTime(&x, a, b);
-      v.push_back(x);
-      if (rc != 0) return rc;
+      bestr = std::min(bestr, x / (float)reps);
     }
-    std::sort(v.begin(), v.end());
-    *ms = v[v.size() / 2];
+    *ms = bestr;
     return 0;
   };
+  // warm the GPU (clocks, caches, TLB) with the current choice before timing
+  {
+    float ms = 0.f;
+    time_one(MatTune{0, 0, 0, 0, 0}, &ms);
+    time_one(MatTune{0, 0, 0, 0, 0}, &ms);
+  }
   float bm = 1e30f;
   MatTune bt = cands[0];
   for (const MatTune& t : cands) {

@@ -289,9 +289,7 @@ int launch_vecprog(VecProg& P, const VecTune& tune_in, void* stream, const char*
     if (tune_on_first_use(stream)) {
       VecTune bt{};
       float bm = 0.f;
-      g_in_search = true;
       tuned = autotune_vecprog(P, stream, g_autotune_reps.load(), &bt, &bm, nullptr) == 0;
-      g_in_search = false;
       if (tuned) tune = bt;
     }
     if (!tuned) tune = VecTune{256, 4, 0};
@@ -330,28 +328,38 @@ int launch_vecprog(VecProg& P, const VecTune& tune_in, void* stream, const char*
 // Empirical search over rows in flight (2 or 4 chunks per input) and grid
 // size (2, 4 or 8 blocks per SM); best to the tuning cache.  Synchronous.
 int autotune_vecprog(VecProg& P, void* stream, int reps, VecTune* best, float* best_ms, float* auto_ms) {
+  struct Scope {  // no nested first-use tuning inside the search
+    bool was;
+    Scope() : was(g_in_search) { g_in_search = true; }
+    ~Scope() { g_in_search = was; }
+  } scope;
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
+  // Mean of `reps` back-to-back launches between one pair of events, best of
+  // two rounds (host launch latency is not timed).
   auto time_one = [&](const VecTune& t, float* ms) -> int {
     const char* why = nullptr;
     int rc = launch_vecprog(P, t, stream, &why);
-    std::vector<float> v;
-    for (int r = 0; r < reps && rc == 0; ++r) {
+    float bestr = 1e30f;
+    for (int round = 0; round < 2 && rc == 0; ++round) {
       cudaEventRecord(a, st);
-      rc = launch_vecprog(P, t, stream, &why);
+      for (int r = 0; r < reps && rc == 0; ++r) rc = launch_vecprog(P, t, stream, &why);
       cudaEventRecord(b, st);
       cudaEventSynchronize(b);
       float x = 0.f;
       cudaEventElapsedTime(&x, a, b);
-      v.push_back(x);
+      bestr = std::min(bestr, x / (float)reps);
     }
     if (rc != 0) return rc;
-    std::sort(v.begin(), v.end());
-    *ms = v[v.size() / 2];
+    *ms = bestr;
     return 0;
   };
+  {  // warm the GPU with the current choice before timing
+    float ms = 0.f;
+    time_one(VecTune{0, 0, 0}, &ms);
+  }
   float bm = 1e30f;
   VecTune bt{256, 4, 0};
   for (int u : {2, 4})

@@ -47,6 +47,7 @@ def test_validation_without_gpu(kf):
     assert L.kf_set_matrix_tuning(3, 2, 2, 0, 4) == -1
     assert L.kf_set_matrix_tuning(8, 2, 2, 0, 9) == -1
     assert L.kf_set_matrix_tuning(8, 2, 2, 0, 4) == 0
+    assert L.kf_set_matrix_tuning(0, 0, 0, 0, 0) == 0      # back to automatic
     assert L.kf_set_autotune(-1) == -1 and L.kf_set_autotune(101) == -1
     assert L.kf_set_autotune(0) == 0 and kf.kf_get_autotune() == 0
     b = ctypes.c_size_t(0)

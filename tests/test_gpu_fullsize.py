@@ -32,6 +32,7 @@ def suite_for(kf, seqs):
     import bench
     s = bench.Suite(kf, bench.FULL, dev(), seqs=seqs)
     st = torch.cuda.Stream()
+    torch.cuda.synchronize()  # the inputs are generated on the default stream
     with torch.cuda.stream(st):
         for q in seqs:
             s.fused(q, st)

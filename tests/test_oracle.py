@@ -438,3 +438,44 @@ def test_generator_grid_range_and_subsets():
     assert int(s.min()) >= 32 and int(s.max()) <= 2048
     ls = torch.log(s.double())
     assert abs(float(ls.mean()) - (np.log(32) + np.log(2048)) / 2) < 0.1
+
+
+# ------------------------------------------------------------------ hand-worked examples
+
+def _golden():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.txt")
+    cases, cur = {}, None
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        if line.startswith("["):
+            cur = cases.setdefault(line.strip("[]"), {})
+            continue
+        k, v = (t.strip() for t in line.split("=", 1))
+        rows = [[float(x) for x in r.split()] for r in v.split(";")]
+        cur[k] = np.array(rows) if len(rows) > 1 else (np.array(rows[0]) if len(rows[0]) > 1 else rows[0][0])
+    return cases
+
+
+def test_hand_worked_examples():
+    """The oracle reproduces tiny examples worked by hand from Table 1's
+    definitions (tests/golden/hand_examples.txt)."""
+    g = _golden()
+    close = lambda a, b: np.testing.assert_allclose(np.asarray(a, dtype=np.float64), b, rtol=1e-13, atol=1e-13)  # noqa: E731
+    c = g["bicgk"]
+    q, s = oracle.bicgk(c["A"], c["p"], c["r"])
+    close(q, c["q"]); close(s, c["s"])
+    c = g["gemver"]
+    B, x, w = oracle.gemver(c["A"], c["u1"], c["v1"], c["u2"], c["v2"], c["y"], c["z"], c["alpha"], c["beta"])
+    close(B, c["B"]); close(x, c["x"]); close(w, c["w"])
+    c = g["gesummv"]
+    close(oracle.gesummv(c["A"], c["B"], c["x"], c["alpha"], c["beta"]), c["y"])
+    c = g["atax"]
+    close(oracle.atax(c["A"], c["x"])[0], c["y"])
+    c = g["axpydot"]
+    z, r = oracle.axpydot(c["w"], c["v"], c["u"], c["alpha"])
+    close(z, c["z"]); close(r, c["r"])
+    c = g["waxpby"]
+    close(oracle.waxpby(c["alpha"], c["x"], c["beta"], c["y"]), c["w"])
