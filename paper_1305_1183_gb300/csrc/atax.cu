@@ -35,8 +35,9 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
   __shared__ __align__(8) uint64_t full[ATAX_MAXSTAGES];
   __shared__ float red[2][NT / 32];
 
-  // Let the finishing kernel launch now; it waits for this grid itself.
-  asm volatile("griddepcontrol.launch_dependents;");
+  // Wait for the previous kernel of the stream (programmatic launch), then
+  // let the finishing kernel launch now; it waits for this grid itself.
+  pdl_enter();
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = m * blockIdx.x / gridDim.x;
@@ -215,7 +216,7 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
   int nparts = (int)grid;
   void* args[] = {(void*)&A, (void*)&lda, (void*)&m, (void*)&n, (void*)&x, (void*)&ypart,
                   (void*)&stages, (void*)&rowcap, (void*)&err};
-  cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(512), args, smem, (cudaStream_t)stream);
+  cudaError_t e = launch_pdl(fn, dim3((unsigned)grid), dim3(512), args, smem, stream);
   if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
 
   cudaLaunchConfig_t cfg = {};

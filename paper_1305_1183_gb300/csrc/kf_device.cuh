@@ -105,4 +105,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 // Error word written by kernels whose waits ran out (read by the host).
 constexpr unsigned KF_DEVERR_TIMEOUT = 1u;
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while the previous kernel of its stream drains:
+// it waits here until that kernel has completed and its writes are visible,
+// then lets its own dependents be scheduled (they wait the same way).
+// Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+}
+
 }  // namespace kf

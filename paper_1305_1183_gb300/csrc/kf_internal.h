@@ -120,6 +120,9 @@ struct VecTune {
 
 // Status codes mirror kf.h.
 int launch_matprog(MatProg& P, const MatTune& t, void* stream, const char** why);
+// cudaLaunchKernelExC with programmatic stream serialization (the kernel
+// must begin with pdl_enter()).
+cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, void* stream);
 // out[k] = max_j |v_k[j]| for the nv <= 4 vectors v_k of length n (device).
 int launch_colnorms(const float* const* v, int nv, int64_t n, float* out, void* stream, const char** why);
 int launch_vecprog(VecProg& P, const VecTune& t, void* stream, const char** why);

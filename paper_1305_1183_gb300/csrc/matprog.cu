@@ -186,6 +186,24 @@ void op_shape(const MatProg& P, int* sig, int* shape_nops, int* shape_ng, int* n
   *ngemv_out = ngemv;
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the previous kernel of the stream drains (its blocks wait in
+// pdl_enter until that kernel's writes are visible), hiding launch latency
+// between the passes of a sequence.
+cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, void* stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* best_ms, float* auto_ms);
 
 // Tuning on first use (kf_set_autotune): timed runs per candidate, 0 = off.
@@ -294,7 +312,7 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   P.stages = stages;
   dim3 grid((unsigned)strips, (unsigned)G);
   void* args[] = {&P};
-  cudaError_t err = cudaLaunchKernel(e.fn, grid, dim3(threads), args, smem, (cudaStream_t)stream);
+  cudaError_t err = launch_pdl(e.fn, grid, dim3(threads), args, smem, stream);
   if (err != cudaSuccess) { *why = cudaGetErrorString(err); return -7; }
   return 0;
 }

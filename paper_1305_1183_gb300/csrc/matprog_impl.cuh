@@ -395,6 +395,9 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   constexpr float QMAX = FMT == FMT_E4M3 ? 448.f : 1.f;
   // low-precision 16-byte loads keep their chunks packed until the row is used
   constexpr bool RAW = FMT != FMT_F32 && VEC;
+  // Without a GER the row scale is applied once per row (to the row dot and
+  // to the GEMVT row value) instead of once per element.
+  constexpr bool FOLD = RAW && SPEC && LASTGER < 0;
   using BatchT = typename BatchOf<RAW, NMAT, U, V, W>::type;
   extern __shared__ float4 smem4[];
   __shared__ __align__(8) uint64_t full[STAGED ? MAT_MAXSTAGES : 1];
@@ -403,6 +406,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   __shared__ int s_last[2];
   __shared__ int s_abort;
 
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int strip = blockIdx.x;
@@ -589,19 +593,28 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
             const int rr = r + u;
             // the row's values: decoded, then scaled by the row's scale
             float ar[NMAT][W];
+            float rowfac[NMAT];  // scale still to apply to this row's results (FOLD)
 #pragma unroll
             for (int t = 0; t < NMAT; ++t) {
+              rowfac[t] = 1.f;
               if constexpr (RAW) {
+                const float sc = __shfl_sync(FULL_MASK, rsc[t], rr);
 #pragma unroll
                 for (int v = 0; v < V; ++v) decode16<FMT>(a[t][u][v], &ar[t][v * CH]);
+                if constexpr (FOLD) {
+                  rowfac[t] = sc;
+                } else {
+#pragma unroll
+                  for (int e = 0; e < W; ++e) ar[t][e] = __fmul_rn(ar[t][e], sc);
+                }
               } else {
 #pragma unroll
                 for (int e = 0; e < W; ++e) ar[t][e] = a[t][u][e];
-              }
-              if constexpr (FMT != FMT_F32) {
-                const float sc = __shfl_sync(FULL_MASK, rsc[t], rr);
+                if constexpr (FMT != FMT_F32) {
+                  const float sc = __shfl_sync(FULL_MASK, rsc[t], rr);
 #pragma unroll
-                for (int e = 0; e < W; ++e) ar[t][e] *= sc;
+                  for (int e = 0; e < W; ++e) ar[t][e] *= sc;
+                }
               }
             }
 #pragma unroll
@@ -632,11 +645,14 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
                       } else {
                         slot0 = (op.res == 0);
                       }
-                      if (NG == 1 || slot0) dacc[0][r16 + u] += d0 + d1;
-                      else dacc[NGA - 1][r16 + u] += d0 + d1;
+                      float d = d0 + d1;
+                      if constexpr (FOLD) d *= rowfac[NMAT == 1 ? 0 : opmat];
+                      if (NG == 1 || slot0) dacc[0][r16 + u] += d;
+                      else dacc[NGA - 1][r16 + u] += d;
                     }
                   } else if (kind == MOP_GEMVT) {
-                    const float y = __shfl_sync(FULL_MASK, rv[k], rr);
+                    float y = __shfl_sync(FULL_MASK, rv[k], rr);
+                    if constexpr (FOLD) y *= rowfac[NMAT == 1 ? 0 : opmat];
 #pragma unroll
                     for (int e = 0; e < W; ++e) cv[k][e] = fmaf(t[e], y, cv[k][e]);
                   }

@@ -58,6 +58,7 @@ __device__ __forceinline__ float lin1(const float (&c)[VP_MAXIN], const float (&
 
 template <int NIN, int NOUT, int NDOT, int U>
 __global__ void __launch_bounds__(256) vecprog_kernel(const __grid_constant__ VecProg P) {
+  pdl_enter();
   constexpr int ND = NDOT > 0 ? NDOT : 1;
   __shared__ float s_red[ND][8];
   __shared__ int s_last;
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(256) vecprog_kernel(const __grid_constant__ Ve
 // Element-wise variant for vectors whose base addresses are not 16-byte aligned.
 template <int NIN, int NOUT, int NDOT>
 __global__ void __launch_bounds__(256) vecprog_scalar_kernel(const __grid_constant__ VecProg P) {
+  pdl_enter();
   constexpr int ND = NDOT > 0 ? NDOT : 1;
   __shared__ float s_red[ND][8];
   __shared__ int s_last;
@@ -318,8 +320,7 @@ int launch_vecprog(VecProg& P, const VecTune& tune_in, void* stream, const char*
   }
   blocks = std::min<int64_t>(blocks, VP_MAXBLOCKS);
   void* args[] = {&P};
-  cudaError_t err = cudaLaunchKernel(e->fn, dim3((unsigned)blocks), dim3(threads), args, 0,
-                                     (cudaStream_t)stream);
+  cudaError_t err = launch_pdl(e->fn, dim3((unsigned)blocks), dim3(threads), args, 0, stream);
   if (err != cudaSuccess) { *why = cudaGetErrorString(err); return -7; }
   return 0;
 }
