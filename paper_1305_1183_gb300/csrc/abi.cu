@@ -18,7 +18,9 @@ bool atax_single_pass_ok(int64_t m, int64_t n, int64_t lda, const void* A, const
 size_t atax_workspace_bytes(int64_t n);
 int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y,
                        void* ws, size_t ws_bytes, int stages_req, int ctas_per_sm, void* stream,
-                       const char** why);
+                       const char** why, int rows_per_round);
+int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, void* ws,
+                      size_t ws_bytes, void* stream, const char** why);
 int launch_quantize_rows(const float* A, int64_t lda, int64_t m, int64_t n, int fmt, void* Q,
                          float* scale, void* stream, const char** why);
 extern std::atomic<int> g_autotune_reps;
@@ -355,7 +357,7 @@ kf_status kf_atax(int64_t m, int64_t n, const float* A, int64_t lda, const float
   if (atax_single_pass_ok(m, n, lda, A, x, y)) {
     const char* why = nullptr;
     if (ws == nullptr) return fail(KF_ERR_WORKSPACE, "workspace required");
-    return from_launch(launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, 0, 0, stream, &why), why);
+    return from_launch(launch_atax_tuned(A, lda, m, n, x, y, ws, ws_bytes, stream, &why), why);
   }
   // Two passes (the paper's form): t = A x, then y = A^T t.
   // The first 256 bytes stay reserved for the device error word.

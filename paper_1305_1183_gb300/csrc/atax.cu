@@ -15,17 +15,27 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <string>
 
 #include "kf_device.cuh"
 #include "kf_internal.h"
 
 namespace kf {
 
+bool tune_cache_get_mat(const std::string& k, MatTune* t);
+void tune_cache_put_mat(const std::string& k, const MatTune& t);
+bool tune_on_first_use(void* stream);
+extern std::atomic<int> g_autotune_reps;
+
 constexpr int ATAX_MAXSTAGES = 8;
 
 namespace {
 
-template <int NT, int VA>
+// RP rows per round: their dots share one block barrier.  With RP = 2 the
+// vector x is read through L1 instead of being held in registers, which
+// pays for the second row's values.
+template <int NT, int VA, int RP>
 __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const float* __restrict__ A, int64_t lda, int64_t m,
                                                         int64_t n, const float* __restrict__ x,
                                                         float* __restrict__ ypart, int stages,
@@ -33,7 +43,7 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
   extern __shared__ float4 ring4[];
   float* ring = reinterpret_cast<float*>(ring4);
   __shared__ __align__(8) uint64_t full[ATAX_MAXSTAGES];
-  __shared__ float red[2][NT / 32];
+  __shared__ float red[2][RP][NT / 32];
 
   // Wait for the previous kernel of the stream (programmatic launch), then
   // let the finishing kernel launch now; it waits for this grid itself.
@@ -45,6 +55,7 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
   const int64_t nrows = r1 - r0;
   const unsigned bytes = (unsigned)(n * sizeof(float));
   const int64_t n4 = n >> 2;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
 
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
@@ -58,32 +69,43 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
     }
   }
 
-  float4 xr[VA], yacc[VA];
+  float4 xr[RP == 1 ? VA : 1], yacc[VA];
 #pragma unroll
   for (int k = 0; k < VA; ++k) {
     const int64_t c4 = (int64_t)k * NT + tid;
-    xr[k] = c4 < n4 ? reinterpret_cast<const float4*>(x)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (RP == 1) xr[k] = c4 < n4 ? x4[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
     yacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 
-  for (int64_t j = 0; j < nrows; ++j) {
-    const int s = (int)(j % stages);
-    const unsigned par = (unsigned)((j / stages) & 1);
-    const bool ok = mbar_wait_bounded(&full[s], par);
-    float4 a[VA];
-    float d0 = 0.f, d1 = 0.f;
-    const float4* row = reinterpret_cast<const float4*>(ring + s * rowcap);
+  int64_t round = 0;
+  for (int64_t j = 0; j < nrows; j += RP, ++round) {
+    float4 a[RP][VA];
+    bool ok = true;
 #pragma unroll
-    for (int k = 0; k < VA; ++k) {
-      const int64_t c4 = (int64_t)k * NT + tid;
-      a[k] = (ok && c4 < n4) ? row[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
-      d0 = fmaf(a[k].x, xr[k].x, d0);
-      d1 = fmaf(a[k].y, xr[k].y, d1);
-      d0 = fmaf(a[k].z, xr[k].z, d0);
-      d1 = fmaf(a[k].w, xr[k].w, d1);
+    for (int rp = 0; rp < RP; ++rp) {
+      const int64_t row = j + rp;
+      const bool valid = row < nrows;
+      const int s = (int)(row % stages);
+      const bool got = valid ? mbar_wait_bounded(&full[s], (unsigned)((row / stages) & 1)) : true;
+      ok = ok && got;
+      float d0 = 0.f, d1 = 0.f;
+      const float4* rowp = reinterpret_cast<const float4*>(ring + s * rowcap);
+#pragma unroll
+      for (int k = 0; k < VA; ++k) {
+        const int64_t c4 = (int64_t)k * NT + tid;
+        const bool in = valid && got && c4 < n4;
+        a[rp][k] = in ? rowp[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 xv;
+        if constexpr (RP == 1) xv = xr[k];
+        else xv = in ? __ldg(x4 + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        d0 = fmaf(a[rp][k].x, xv.x, d0);
+        d1 = fmaf(a[rp][k].y, xv.y, d1);
+        d0 = fmaf(a[rp][k].z, xv.z, d0);
+        d1 = fmaf(a[rp][k].w, xv.w, d1);
+      }
+      const float d = warp_sum(d0 + d1);
+      if (lane == 0) red[round & 1][rp][warp] = d;
     }
-    const float d = warp_sum(d0 + d1);
-    if (lane == 0) red[j & 1][warp] = d;
     if (__syncthreads_or(!ok)) {
       // A copy never completed: report, let the other copies land (bounded), stop.
       if (tid == 0) {
@@ -94,21 +116,31 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
       __syncthreads();
       return;
     }
-    // Every thread has its row values in registers: the stage can be refilled.
-    if (tid == 0 && j + stages < nrows) {
-      fence_proxy_async_smem();
-      mbar_expect_tx(&full[s], bytes);
-      bulk_g2s(ring + s * rowcap, A + (r0 + j + stages) * lda, bytes, &full[s]);
+    // Every thread has its rows' values in registers: the stages can be refilled.
+    if (tid == 0) {
+#pragma unroll
+      for (int rp = 0; rp < RP; ++rp) {
+        const int64_t row = j + rp;
+        if (row < nrows && row + stages < nrows) {
+          const int s = (int)(row % stages);
+          fence_proxy_async_smem();
+          mbar_expect_tx(&full[s], bytes);
+          bulk_g2s(ring + s * rowcap, A + (r0 + row + stages) * lda, bytes, &full[s]);
+        }
+      }
     }
-    float t = 0.f;
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) t += red[j & 1][w];
+    for (int rp = 0; rp < RP; ++rp) {
+      float t = 0.f;
 #pragma unroll
-    for (int k = 0; k < VA; ++k) {
-      yacc[k].x = fmaf(t, a[k].x, yacc[k].x);
-      yacc[k].y = fmaf(t, a[k].y, yacc[k].y);
-      yacc[k].z = fmaf(t, a[k].z, yacc[k].z);
-      yacc[k].w = fmaf(t, a[k].w, yacc[k].w);
+      for (int w = 0; w < NT / 32; ++w) t += red[round & 1][rp][w];
+#pragma unroll
+      for (int k = 0; k < VA; ++k) {
+        yacc[k].x = fmaf(t, a[rp][k].x, yacc[k].x);
+        yacc[k].y = fmaf(t, a[rp][k].y, yacc[k].y);
+        yacc[k].z = fmaf(t, a[rp][k].z, yacc[k].z);
+        yacc[k].w = fmaf(t, a[rp][k].w, yacc[k].w);
+      }
     }
   }
   float4* yp = reinterpret_cast<float4*>(ypart + (int64_t)blockIdx.x * n);
@@ -125,7 +157,7 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
 // before their adds; the slices are then added in slice order, so the result
 // is independent of timing.  Narrow blocks spread the partials (a few MB,
 // mostly in L2) over every SM.
-constexpr int FIN_COLS = 8, FIN_SLICES = 32, FIN_LOADS = 8;
+constexpr int FIN_COLS = 4, FIN_SLICES = 64, FIN_LOADS = 5;
 
 __global__ void __launch_bounds__(FIN_COLS * FIN_SLICES) atax_finish_kernel(const float* __restrict__ ypart,
                                                                             int nparts, int64_t n,
@@ -170,8 +202,8 @@ struct AEntry {
 };
 
 template <int VA>
-const void* atax_fn() {
-  return (const void*)&atax_rows_kernel<512, VA>;
+const void* atax_fn(int rp) {
+  return rp == 2 ? (const void*)&atax_rows_kernel<512, VA, 2> : (const void*)&atax_rows_kernel<512, VA, 1>;
 }
 
 }  // namespace
@@ -189,10 +221,9 @@ size_t atax_workspace_bytes(int64_t n) {
 
 int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y,
                        void* ws, size_t ws_bytes, int stages_req, int ctas_per_sm, void* stream,
-                       const char** why) {
+                       const char** why, int rows_per_round) {
   const int VA = (int)((n / 4 + 511) / 512);
   const int va = VA <= 1 ? 1 : (VA <= 2 ? 2 : (VA <= 4 ? 4 : 8));
-  const void* fn = va == 1 ? atax_fn<1>() : va == 2 ? atax_fn<2>() : va == 4 ? atax_fn<4>() : atax_fn<8>();
   const int64_t rowcap = (n + 31) / 32 * 32;  // 128-byte aligned stages
   const size_t rowbytes = (size_t)rowcap * sizeof(float);
   const int cps = ctas_per_sm > 0 ? ctas_per_sm : 2;
@@ -201,7 +232,21 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
   if (stages < 2) stages = std::min<int>(2, (int)((size_t)(220 * 1024) / rowbytes));
   if (stages < 1) { *why = "row too long for the shared-memory ring"; return -10; }
   stages = std::min(stages, ATAX_MAXSTAGES);
+  // two rows per barrier need both rows' stages in the ring at once
+  const int rp = rows_per_round == 2 && va <= 4 && stages >= 2 ? 2 : 1;
+  const void* fn = va == 1 ? atax_fn<1>(rp) : va == 2 ? atax_fn<2>(rp) : va == 4 ? atax_fn<4>(rp) : atax_fn<8>(rp);
   const size_t smem = (size_t)stages * rowbytes;
+  {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, fn);
+    if ((int64_t)smem + (int64_t)fa.sharedSizeBytes > (int64_t)optin) {
+      *why = "copy ring does not fit in shared memory";
+      return -10;
+    }
+  }
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 512, smem) != cudaSuccess || occ < 1) occ = 1;
@@ -233,6 +278,67 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
   e = cudaLaunchKernelEx(&cfg, atax_finish_kernel, yp, nparts, n, y);
   if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
   return 0;
+}
+
+// ATAX with the tuning cache: key "atax log2(m) log2(n)" holding the
+// copy-ring depth (stages field), resident blocks per SM (groups field) and
+// rows per barrier (unroll field).  On a miss, with tuning on first use
+// enabled, every fitting (rows per barrier in {1, 2}, blocks per SM in
+// {1, 2}, stages in {2, 3, 4, 6}) is timed on the call's operands (mean of
+// back-to-back launches, best of two rounds) and the fastest stored.
+int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, void* ws,
+                      size_t ws_bytes, void* stream, const char** why) {
+  auto cls = [](int64_t v) {
+    int b = 0;
+    while (b < 62 && (int64_t(1) << (b + 1)) <= v) ++b;
+    return b;
+  };
+  const std::string key = "atax " + std::to_string(cls(m)) + " " + std::to_string(cls(n));
+  MatTune t{0, 0, 0, 0, 0};
+  if (!tune_cache_get_mat(key, &t)) {
+    t = MatTune{0, 0, 0, 0, 0};
+    if (tune_on_first_use(stream)) {
+      const int reps = std::max(1, g_autotune_reps.load());
+      cudaStream_t st = (cudaStream_t)stream;
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      float best = 1e30f;
+      MatTune bt = t;
+      // warm up with the built-in choice
+      for (int r = 0; r < 2; ++r) launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, 0, 0, stream, why, 1);
+      for (int rp : {1, 2})
+      for (int cps : {1, 2})
+        for (int stg : {2, 3, 4, 6}) {
+          if (launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, stg, cps, stream, why, rp) != 0) {
+            (void)cudaGetLastError();
+            continue;
+          }
+          float tb = 1e30f;
+          for (int round = 0; round < 2; ++round) {
+            cudaEventRecord(a, st);
+            for (int r = 0; r < reps; ++r) launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, stg, cps, stream, why, rp);
+            cudaEventRecord(b, st);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            tb = std::min(tb, ms / (float)reps);
+          }
+          if (tb < best * 0.999f) {
+            best = tb;
+            bt = MatTune{1, 0, rp, cps, stg};
+          }
+        }
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      if (best < 1e29f) {
+        tune_cache_put_mat(key, bt);
+        t = bt;
+      }
+    }
+  }
+  return launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, t.stages, t.groups, stream, why,
+                            t.unroll == 2 ? 2 : 1);
 }
 
 }  // namespace kf

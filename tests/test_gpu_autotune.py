@@ -133,3 +133,29 @@ def test_tune_on_first_use(built):
         check_reduce(host(b2["q"]), oracle.gemv(Ah, ph), oracle.abs_gemv(Ah, ph), 900, "q captured")
     finally:
         kf.kf_set_autotune(0)
+
+
+def test_tune_on_first_use_atax(built, tmp_path):
+    """ATAX's ring depth and blocks per SM go through the same first-use
+    search and cache (saved and loaded with the rest); results keep parity."""
+    kf = built
+    kf.kf_tune_cache_clear()
+    kf.kf_set_autotune(2)
+    try:
+        m, n = 3000, 4096
+        A = synth.uniform((m, n), 0, 1, device=dev())
+        x = synth.uniform((n,), 0, 3, device=dev())
+        y = torch.empty(n, device=dev())
+        kf.kf_atax(A, x, y, kf.workspace(kf.KF_SEQ_ATAX, m, n))
+        assert kf.kf_tune_cache_entries() == 1
+        Ah, xh = host(A), host(x)
+        yo, _ = oracle.atax(Ah, xh)
+        check_reduce(host(y), yo, oracle.abs_gemvt(Ah, oracle.abs_gemv(Ah, xh)), m, "atax tuned")
+        path = tmp_path / "tune.txt"
+        kf.kf_tune_cache_save(path)
+        assert "atax " in open(path).read()
+        kf.kf_tune_cache_clear()
+        assert kf.kf_tune_cache_load(path) == 1
+    finally:
+        kf.kf_set_autotune(0)
+        kf.kf_tune_cache_clear()
