@@ -349,9 +349,8 @@ def time_suite(suite, mode, steps, warmup, st, seqs):
     Returns (total ms, {sequence: mean ms}).  The total comes from one pair
     of CUDA events around the `steps` passes, issued back to back as a user
     would (consecutive kernels may overlap their launch through programmatic
-    dependent launch); the per-sequence means come from a second timed pass
-    with an event pair around every sequence (events serialise the stream,
-    so their sum is a little above the total)."""
+    dependent launch); each sequence's mean comes from one event pair around
+    `steps` back-to-back calls of that sequence alone."""
     call = suite.fused if mode == "fused" else suite.unfused
     torch.cuda.synchronize()  # inputs come from other streams
     with torch.cuda.stream(st):
@@ -370,16 +369,17 @@ def time_suite(suite, mode, steps, warmup, st, seqs):
         t1.record(st)
     st.synchronize()
     total_ms = t0.elapsed_time(t1)
-    ev = {s: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)] for s in seqs}
-    with torch.cuda.stream(st):
-        for k in range(steps):
-            for s in seqs:
-                ev[s][k][0].record(st)
+    per = {}
+    for s in seqs:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            a.record(st)
+            for k in range(steps):
                 call(s, st)
-                ev[s][k][1].record(st)
-    st.synchronize()
-    per = {s: float(np.mean([a.elapsed_time(b) for a, b in ev[s]])) for s in seqs}
+            b.record(st)
+        st.synchronize()
+        per[s] = a.elapsed_time(b) / steps
     return total_ms, per
 
 
@@ -810,8 +810,8 @@ def main():
                    else f"subset {seqs}, sizes {[sizes[s] for s in seqs]}",
                    "l2": "inputs larger than L2 (every matrix / long vector exceeds 129 MB)",
                    "timing": ("value: one CUDA-event pair around the timed steps issued back to back; "
-                              "sequences and roofline: an event pair around every sequence in a second "
-                              "timed pass"),
+                              "sequences and roofline: one event pair around the same number of "
+                              "back-to-back calls of each sequence alone"),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "tuning": (f"fixed {args.mat_tuning}" if args.mat_tuning else
                               f"autotuned on first use ({args.autotune} timed runs per candidate)"
