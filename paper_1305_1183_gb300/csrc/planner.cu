@@ -632,26 +632,25 @@ std::string make_plan(const Script& s, const std::vector<std::vector<int>>& grou
 
 void features(const Script& s, const Plan& p, std::vector<float>* f) {
   f->assign(NFEATURES, 0.f);
-  float nk = (float)p.kernels.size(), nmat = 0, nvec = 0, matb = 0, vecb = 0, maxops = 0;
-  float ngemv = 0, ngemvt = 0, nger = 0, ndot = 0, nepi = 0, nstore = 0;
+  float nk = (float)p.kernels.size(), nmat = 0, nvec = 0, maxops = 0;
+  double matb = 0, vecb = 0, minb = 1e300;
+  float rowfin = 0, colfin = 0, dotk = 0, nepi = 0, nstore = 0;
   int64_t nmax = 1;
   for (const auto& K : p.kernels) {
+    minb = std::min(minb, K.bytes);
     if (K.is_mat) {
       nmat += 1;
-      matb += (float)(4.0 * K.m * K.n * K.mp.nmat);
-      vecb += (float)(K.bytes - 4.0 * K.m * K.n * K.mp.nmat);
+      matb += 4.0 * K.m * K.n * K.mp.nmat;
+      vecb += K.bytes - 4.0 * K.m * K.n * K.mp.nmat;
       maxops = std::max(maxops, (float)K.mp.nops);
-      for (int k = 0; k < K.mp.nops; ++k) {
-        ngemv += K.mp.ops[k].kind == MOP_GEMV;
-        ngemvt += K.mp.ops[k].kind == MOP_GEMVT;
-        nger += K.mp.ops[k].kind == MOP_GER;
-      }
+      rowfin += K.mp.nrow_res > 0;  // a second, dependent phase for row results
+      colfin += K.mp.ncol_res > 0;  // ... and for column results
       nepi += (float)(K.mp.nrow_out + K.mp.ncol_out);
       nmax = std::max<int64_t>(nmax, std::max(K.m, K.n));
     } else {
       nvec += 1;
-      vecb += (float)K.bytes;
-      ndot += (float)K.vp.ndot;
+      vecb += K.bytes;
+      dotk += K.vp.ndot > 0;
       nmax = std::max<int64_t>(nmax, K.n);
     }
   }
@@ -659,20 +658,20 @@ void features(const Script& s, const Plan& p, std::vector<float>* f) {
     for (const auto& b : K.bind)
       for (int t = 0; t < 2; ++t)
         if (K.is_mat && (size_t)(uintptr_t)b.first == off(K.mp, &K.mp.Bout[t])) nstore += 1;
+  // byte counts span orders of magnitude across sizes: log scale
   (*f)[0] = nk;
   (*f)[1] = nmat;
   (*f)[2] = nvec;
-  // byte counts span orders of magnitude across sizes: log scale
   (*f)[3] = (float)std::log2(1.0 + p.bytes);
-  (*f)[4] = (float)std::log2(1.0 + (double)matb);
-  (*f)[5] = (float)std::log2(1.0 + (double)vecb);
+  (*f)[4] = (float)std::log2(1.0 + matb);
+  (*f)[5] = (float)std::log2(1.0 + vecb);
   (*f)[6] = (float)std::log2((double)nmax);
   (*f)[7] = nk > 0 ? (float)s.calls.size() / nk : 0.f;
   (*f)[8] = maxops;
-  (*f)[9] = ngemv;
-  (*f)[10] = ngemvt;
-  (*f)[11] = nger;
-  (*f)[12] = ndot;
+  (*f)[9] = rowfin;
+  (*f)[10] = colfin;
+  (*f)[11] = dotk;
+  (*f)[12] = (float)std::log2(1.0 + (nk > 0 ? minb : 0.0));
   (*f)[13] = (float)std::log2(1.0 + p.predicted_us);
   (*f)[14] = nepi;
   (*f)[15] = nstore;

@@ -102,7 +102,7 @@ def training_subset(seed, i, pred, nk, ncalls, per_script):
 
 def collect(seed, indices, kmin, kmax, per_script, reps, cap=2000, device="cuda"):
     """Training data: features and measured ms of a subset of each script's plans."""
-    X, y, pu, meta = [], [], [], []
+    X, y, pu, sid, meta = [], [], [], [], []
     for i in indices:
         n, sd, s = make(seed, i, kmin, kmax)
         feats, pred, nk = s.enumerate_info(cap)
@@ -116,10 +116,12 @@ def collect(seed, indices, kmin, kmax, per_script, reps, cap=2000, device="cuda"
                 ws = torch.zeros(need, dtype=torch.uint8, device=device)
             X.append(feats[j])
             pu.append(pred[j])
+            sid.append(int(i))
             y.append(p.time(bind, ws, reps=reps))
         meta.append({"index": int(i), "n": n, "calls": len(sd["calls"]), "plans": len(pred), "timed": len(chosen)})
         del bind, ws
-    return np.array(X, dtype=np.float64), np.array(y, dtype=np.float64), np.array(pu, dtype=np.float64), meta
+    return (np.array(X, dtype=np.float64), np.array(y, dtype=np.float64), np.array(pu, dtype=np.float64),
+            np.array(sid, dtype=np.int64), meta)
 
 
 def he_uniform_params(d_in, seed, device):
@@ -137,15 +139,22 @@ def he_uniform_params(d_in, seed, device):
     return out.float().to(device)
 
 
-def train(X, ms, pred_us, analytic_weight=1.0, epochs=3000, lr=3e-3, seed=0, device="cuda"):
+def train(X, ms, pred_us, script_ids=None, analytic_weight=1.0, epochs=3000, lr=3e-3, seed=0, device="cuda"):
     """Full-batch Adam, all steps in libkf kernels, on standardised features.
     Target: ln(ms) - analytic_weight * ln(analytic ms), so that with weight
     1 the network learns the analytic model's error and the score
-    ln(analytic ms) + f(x) ranks plans.  Returns (CostModel, loss history)."""
+    ln(analytic ms) + f(x) ranks plans.  With script ids the target is
+    centred per script: only differences between the plans of one script
+    decide a choice, so the script's common level is removed from what the
+    network has to fit.  Returns (CostModel, loss history)."""
     mean = X.mean(axis=0)
     inv_std = 1.0 / (X.std(axis=0) + 1e-6)
     Xs = torch.tensor((X - mean) * inv_std, dtype=torch.float32, device=device)
     target = np.log(ms) - analytic_weight * np.log(np.maximum(pred_us, 1e-3) * 1e-3)
+    if script_ids is not None:
+        for sidv in np.unique(script_ids):
+            sel = script_ids == sidv
+            target[sel] -= target[sel].mean()
     yt = torch.tensor(target, dtype=torch.float32, device=device)
     d = X.shape[1]
     p = he_uniform_params(d, seed, device)
@@ -179,10 +188,12 @@ def evaluate(seed, indices, kmin, kmax, model, reps, top_k=3, cap=2000, device="
         _, ia = s.select(kf.KF_SELECT_ANALYTIC, max_plans=cap)
         _, i1 = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=1, max_plans=cap)
         _, ik = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=top_k, reps=reps, max_plans=cap)
+        _, i5 = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=2 * top_k, reps=reps, max_plans=cap)
         t_unf = unf.time(bind, ws, reps=reps)
         best = float(t.min())
         rows.append({"index": int(i), "n": n, "calls": len(sd["calls"]), "plans": len(t), "best_ms": best,
                      "mlp": float(t[i1["index"]]) / best, "mlp_topk": float(t[ik["index"]]) / best,
+                     "mlp_top2k": float(t[i5["index"]]) / best,
                      "analytic": float(t[ia["index"]]) / best, "greedy": float(t[int(np.argmin(nk))]) / best,
                      "unfused": t_unf / best, "timed_topk": ik["timed"]})
         del bind, ws
@@ -195,12 +206,13 @@ def summary(rows, key):
             "within_5pct": round(float((r <= 1.05).mean()), 4), "worst": round(float(r.max()), 4)}
 
 
-def run(seed=0, scripts=500, ntrain=400, kmin=10, kmax=14, per_script=48, reps=5, epochs=3000, top_k=3,
-        analytic_weight=1.0, device="cuda", log=print):
+def run(seed=0, scripts=500, ntrain=400, kmin=10, kmax=14, per_script=64, reps=5, epochs=3000, top_k=3,
+        analytic_weight=1.0, centre=True, device="cuda", log=print):
     t0 = time.time()
-    X, ms, pu, meta = collect(seed, range(ntrain), kmin, kmax, per_script, reps, device=device)
+    X, ms, pu, sid, meta = collect(seed, range(ntrain), kmin, kmax, per_script, reps, device=device)
     t1 = time.time()
-    model, hist = train(X, ms, pu, analytic_weight, epochs=epochs, seed=seed, device=device)
+    model, hist = train(X, ms, pu, sid if centre else None, analytic_weight, epochs=epochs, seed=seed,
+                        device=device)
     t2 = time.time()
     rows = evaluate(seed, range(ntrain, scripts), kmin, kmax, model, reps, top_k=top_k, device=device)
     t3 = time.time()
@@ -208,13 +220,14 @@ def run(seed=0, scripts=500, ntrain=400, kmin=10, kmax=14, per_script=48, reps=5
     out = {
         "config": {"seed": seed, "scripts": scripts, "train": ntrain, "test": scripts - ntrain,
                    "n": f"2^{kmin}..2^{kmax}", "per_script": per_script, "reps": reps, "epochs": epochs,
-                   "top_k": top_k, "analytic_weight": analytic_weight, "features": kf.NFEATURES,
+                   "top_k": top_k, "analytic_weight": analytic_weight, "centred_per_script": centre,
+                   "features": kf.NFEATURES,
                    "hidden": kf.MLP_HIDDEN},
         "train_plans_timed": int(len(ms)), "test_plans_timed": int(plans.sum()),
         "test_plans_per_script": {"mean": float(plans.mean()), "max": int(plans.max())},
         "seconds": {"collect": round(t1 - t0, 1), "train": round(t2 - t1, 2), "evaluate": round(t3 - t2, 1)},
         "loss": hist,
-        "test": {k: summary(rows, k) for k in ("mlp", "mlp_topk", "analytic", "greedy", "unfused")},
+        "test": {k: summary(rows, k) for k in ("mlp", "mlp_topk", "mlp_top2k", "analytic", "greedy", "unfused")},
         "rows": rows,
     }
     if log:
@@ -231,17 +244,18 @@ def main(argv=None):
     ap.add_argument("--train", type=int, default=400)
     ap.add_argument("--kmin", type=int, default=10)
     ap.add_argument("--kmax", type=int, default=14)
-    ap.add_argument("--per-script", type=int, default=48)
+    ap.add_argument("--per-script", type=int, default=64)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--top-k", type=int, default=3)
     ap.add_argument("--analytic-weight", type=float, default=1.0)
+    ap.add_argument("--no-centre", action="store_true", help="absolute targets instead of per-script centred")
     ap.add_argument("--out", default="")
     ap.add_argument("--save-model", default="")
     a = ap.parse_args(argv)
     kf.lib()
     res, model = run(a.seed, a.scripts, a.train, a.kmin, a.kmax, a.per_script, a.reps, a.epochs, a.top_k,
-                     a.analytic_weight)
+                     a.analytic_weight, centre=not a.no_centre)
     if a.out:
         with open(a.out, "w") as fh:
             json.dump(res, fh, indent=1)
