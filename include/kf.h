@@ -278,7 +278,7 @@ typedef enum {
 typedef enum {
   KF_PLAN_UNFUSED = 0,   /* one kernel per call                                   */
   KF_PLAN_GREEDY = 1,    /* fewest kernels                                        */
-  KF_PLAN_ANALYTIC = 2,  /* least predicted time: bytes / bandwidth + launch cost */
+  KF_PLAN_ANALYTIC = 2,  /* least predicted time (kf_plan_predicted_us)           */
   KF_PLAN_INDEX = 3      /* the index-th plan of the enumeration                  */
 } kf_plan_mode;
 
@@ -306,8 +306,11 @@ kf_status kf_plan_build(const kf_script* s, const kf_plan_options* opt, kf_plan*
 void kf_plan_destroy(kf_plan* p);
 kf_status kf_plan_workspace_size(const kf_plan* p, size_t* bytes);
 kf_status kf_plan_kernel_count(const kf_plan* p, int* n);
-/* Analytic prediction (microseconds): sum over kernels of bytes moved /
- * model bandwidth + a fixed launch cost (kf_planner_set_model). */
+/* Analytic prediction (microseconds), the paper's predictor (Section 3.2:
+ * transfer and compute times summed separately, max(t_t, t_c)) plus a fixed
+ * cost per kernel: sum over kernels of max(bytes moved / model bandwidth,
+ * flops / FP32 rate) + launch cost (bandwidth and launch cost set by
+ * kf_planner_set_model). */
 kf_status kf_plan_predicted_us(const kf_plan* p, double* us);
 kf_status kf_planner_set_model(double bw_gbs, double launch_us);
 /* Features of a plan for the learned cost model (16 floats). */

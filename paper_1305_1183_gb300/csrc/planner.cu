@@ -378,8 +378,31 @@ void enumerate(const Script& s, size_t cap, std::vector<std::vector<std::vector<
 
 namespace {
 
-double g_bw = 6.5e12;        // bytes/s used by the analytic model
+// Analytic model (the paper's predictor, Section 3.2, sums transfer time t_t
+// and compute time t_c of a fusion separately and predicts max(t_t, t_c)):
+// t_t = bytes moved / g_bw, t_c = flops / g_flops, plus a fixed cost per
+// kernel, which the paper's predictor leaves out (Section 4.3 names that
+// omission as the cause of its AXPYDOT misprediction).  For these
+// memory-bound calls t_c is far below t_t.
+double g_bw = 6.5e12;        // bytes/s
+double g_flops = 80e12;      // FP32 FMA rate of the GPU (152 SMs x 128 lanes x 2 x 2.07 GHz)
 double g_launch_us = 2.0;    // fixed cost per kernel
+
+// Floating-point operations of one call (2 per multiply-add).
+double call_flops(const Script& s, const Call& c) {
+  const Var& o = s.vars[c.outs.empty() ? c.ins[0] : c.outs[0]];
+  switch (c.op) {
+    case OP_GEMV:
+    case OP_GEMVT:
+    case OP_GER: {
+      const Var& A = s.vars[c.ins[0]];
+      return 2.0 * (double)A.m * (double)A.n;
+    }
+    case OP_DOT: return 2.0 * (double)s.vars[c.ins[0]].n;
+    case OP_SCAL: return (double)o.n;
+    default: return 3.0 * (double)o.n;  // AXPBY, VADD
+  }
+}
 
 template <typename T>
 size_t off(const T& base, const void* field) {
@@ -615,16 +638,15 @@ std::string make_plan(const Script& s, const std::vector<std::vector<int>>& grou
     std::string e = depth == 2 ? build_mat_kernel(s, g, &K) : build_vec_kernel(s, g, &K);
     if (!e.empty()) return e;
     if (K.is_mat) {
-      int nro = 0;
-      for (int i = 0; i < K.mp.nrow_out; ++i) nro++;
-      (void)nro;
       const size_t w = matprog_workspace_bytes(K.mp.m, K.mp.n, std::max(K.mp.nrow_res, 1), std::max(K.mp.ncol_res, 1), FMT_F32);
       p->ws_bytes = std::max(p->ws_bytes, vec_region + w);
     } else {
       p->ws_bytes = std::max(p->ws_bytes, vec_region);
     }
     p->bytes += K.bytes;
-    p->predicted_us += K.bytes / g_bw * 1e6 + g_launch_us;
+    double flops = 0.0;
+    for (int c : g) flops += call_flops(s, s.calls[c]);
+    p->predicted_us += std::max(K.bytes / g_bw, flops / g_flops) * 1e6 + g_launch_us;
     p->kernels.push_back(std::move(K));
   }
   return "";
