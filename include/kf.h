@@ -387,7 +387,7 @@ kf_status kf_plan_select(const kf_script* s, const kf_select_options* opt, const
                          kf_select_info* info);
 /* Median time (ms) of every enumerated plan, in KF_PLAN_INDEX order (ms:
  * room for max_plans floats): the data of the exhaustive search, which
- * judges the cost models.  Workspace and timing as kf_plan_select. */
+ * scores the cost models.  Workspace and timing as kf_plan_select. */
 kf_status kf_plan_time_all(const kf_script* s, int max_plans, void* const* bindings, int n_bindings, void* ws,
                            size_t ws_bytes, void* stream, int reps, float* ms, int* count);
 

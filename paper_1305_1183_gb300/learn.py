@@ -1,5 +1,5 @@
 """Learned planner: train the plan cost model on timings the planner
-measures, and judge its choices against exhaustive empirical search.
+measures, and score its choices against exhaustive empirical search.
 
 The paper ranks fusion implementations with an additive predictor of
 benchmarked routine times and can search them empirically (Section 3.2; the
@@ -16,7 +16,7 @@ all of them when there are that few, else the best-predicted half by the
 analytic model, the fewest-kernel plan, the one-kernel-per-call plan and a
 seeded uniform sample of the rest.
 
-Judge.  For a held-out script every enumerated plan is timed
+Scoring.  For a held-out script every enumerated plan is timed
 (kf_plan_time_all); each method's choice is scored by t(choice) / t(best)
 on that table: the MLP's first choice (no timing), the MLP's top-k re-timed
 (kf_plan_select, KF_SELECT_MLP), the analytic model, the fewest-kernel plan

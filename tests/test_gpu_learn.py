@@ -80,7 +80,7 @@ def test_select_errors(built):
 
 
 def test_learned_model_beats_analytic(built):
-    """Train on 200 random scripts (n = 2^10..2^14), judge on 50 held-out
+    """Train on 200 random scripts (n = 2^10..2^14), score on 50 held-out
     ones by exhaustive timing: the trained model's choices land closer to
     the best plan than the analytic predictor's (the method without the
     network), its re-timed top 3 within 10% of the best on (geometric)
