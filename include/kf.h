@@ -202,6 +202,13 @@ kf_status kf_scal(int64_t n, float alpha, const float* x, float* out, void* stre
 kf_status kf_vadd3(int64_t n, const float* w, const float* y, const float* z, float* out,
                    void* stream);
 
+/* C = A + B (MADD of Table 1).  m x n matrices with leading dimensions
+ * lda, ldb, ldc >= n; C may be A or B (in place).  Contiguous operands take
+ * one vector pass over m n elements.  Errors: KF_ERR_INVALID_ARG (null
+ * operand), KF_ERR_SHAPE (leading dimension below n). */
+kf_status kf_madd(int64_t m, int64_t n, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                  int64_t ldc, void* stream);
+
 /* *out = x . y (one device float). */
 kf_status kf_dot(int64_t n, const float* x, const float* y, float* out, void* ws, size_t ws_bytes,
                  void* stream);

@@ -21,6 +21,8 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
                        const char** why, int rows_per_round);
 int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, void* ws,
                       size_t ws_bytes, void* stream, const char** why);
+int launch_madd_strided(int64_t m, int64_t n, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                        int64_t ldc, void* stream, const char** why);
 int launch_quantize_rows(const float* A, int64_t lda, int64_t m, int64_t n, int fmt, void* Q,
                          float* scale, void* stream, const char** why);
 extern std::atomic<int> g_autotune_reps;
@@ -488,6 +490,23 @@ kf_status kf_vadd3(int64_t n, const float* w, const float* y, const float* z, fl
   P.nin = 3; P.in[0] = w; P.in[1] = y; P.in[2] = z;
   P.nout = 1; P.out[0] = out; P.C[0][0] = 1.f; P.C[0][1] = 1.f; P.C[0][2] = 1.f;
   return run_vec(P, nullptr, 0, stream);
+}
+
+kf_status kf_madd(int64_t m, int64_t n, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                  int64_t ldc, void* stream) {
+  CHK(check_mat(m, n, A, lda));
+  CHK(check_mat(m, n, B, ldb));
+  CHK(check_mat(m, n, C, ldc));
+  if (m == 0 || n == 0) return KF_OK;
+  if (lda == n && ldb == n && ldc == n) {
+    // contiguous: one vector pass over m n elements
+    VecProg P = new_vec(m * n);
+    P.nin = 2; P.in[0] = A; P.in[1] = B;
+    P.nout = 1; P.out[0] = C; P.C[0][0] = 1.f; P.C[0][1] = 1.f;
+    return run_vec(P, nullptr, 0, stream);
+  }
+  const char* why = nullptr;
+  return from_launch(launch_madd_strided(m, n, A, lda, B, ldb, C, ldc, stream, &why), why);
 }
 
 kf_status kf_dot(int64_t n, const float* x, const float* y, float* out, void* ws, size_t ws_bytes,

@@ -381,4 +381,29 @@ int autotune_vecprog(VecProg& P, void* stream, int reps, VecTune* best, float* b
   return 0;
 }
 
+// C = A + B for matrices with leading dimensions (MADD of Table 1) when the
+// rows are not contiguous: a grid-stride map over rows, threads over columns.
+namespace {
+__global__ void __launch_bounds__(256) madd_strided_kernel(int64_t m, int64_t n, const float* __restrict__ A,
+                                                           int64_t lda, const float* __restrict__ B, int64_t ldb,
+                                                           float* __restrict__ C, int64_t ldc) {
+  pdl_enter();
+  for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+    const float* a = A + i * lda;
+    const float* b = B + i * ldb;
+    float* c = C + i * ldc;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) c[j] = __fadd_rn(__ldg(a + j), __ldg(b + j));
+  }
+}
+}  // namespace
+
+int launch_madd_strided(int64_t m, int64_t n, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                        int64_t ldc, void* stream, const char** why) {
+  const int64_t grid = std::min<int64_t>(m, (int64_t)device_sm_count() * 8);
+  void* args[] = {(void*)&m, (void*)&n, (void*)&A, (void*)&lda, (void*)&B, (void*)&ldb, (void*)&C, (void*)&ldc};
+  cudaError_t e = launch_pdl((const void*)&madd_strided_kernel, dim3((unsigned)grid), dim3(256), args, 0, stream);
+  if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
+  return 0;
+}
+
 }  // namespace kf

@@ -50,6 +50,7 @@ _SIGS = {
     "kf_workspace_status": ([vp, vp], ci),
     "kf_bicgk": ([i64, i64, vp, i64, ci, vp, vp, vp, vp, vp, vp, sz, vp], ci),
     "kf_gemver": ([i64, vp, i64, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, sz, vp], ci),
+    "kf_madd": ([i64, i64, vp, i64, vp, i64, vp, i64, vp], ci),
     "kf_gemver_q": ([i64, vp, i64, ci, vp, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, vp, sz, vp], ci),
     "kf_gesummv": ([i64, i64, vp, vp, i64, vp, f32, f32, vp, vp, sz, vp], ci),
     "kf_atax": ([i64, i64, vp, i64, vp, vp, vp, sz, vp], ci),
@@ -287,6 +288,12 @@ def kf_scal(alpha, x, out, stream=None):
 
 def kf_vadd3(w, y, z, out, stream=None):
     _ck(lib().kf_vadd3(w.numel(), _p(w), _p(y), _p(z), _p(out), _st(stream)))
+
+
+def kf_madd(A, B, C, stream=None):
+    """C = A + B (2-D tensors with unit column stride)."""
+    m, n = A.shape
+    _ck(lib().kf_madd(m, n, _p(A), A.stride(0), _p(B), B.stride(0), _p(C), C.stride(0), _st(stream)))
 
 
 def kf_dot(x, y, out, ws, stream=None):

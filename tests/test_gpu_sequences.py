@@ -321,3 +321,24 @@ def test_blas1_elementaries(built, n):
     yy = y.clone()
     kf.kf_axpby(0.5, x, 1.0, yy, yy)                          # AXPY in place
     check_map(host(yy), oracle.axpby(0.5, xh, 1.0, yh), 0.5 * np.abs(xh) + np.abs(yh), "axpy in place")
+
+
+# ------------------------------------------------------------------ MADD
+
+@pytest.mark.parametrize("m,n,pad", [(1, 1, 0), (37, 1001, 0), (1024, 1024, 0), (300, 517, 3), (2048, 96, 32)])
+def test_madd_parity(built, m, n, pad):
+    """C = A + B (Table 1's MADD): contiguous operands (one vector pass) and
+    padded leading dimensions (the strided map); one rounding per element,
+    so the result is the correctly rounded sum."""
+    kf = built
+    A = U((m, n + pad), 1)[:, :n]
+    B = U((m, n + 2 * pad), 2)[:, :n]
+    C = torch.full((m, n + pad), float("nan"), device=dev())[:, :n]
+    kf.kf_madd(A, B, C)
+    Ah, Bh = host(A), host(B)
+    want = (Ah + Bh).astype(np.float32).astype(np.float64)   # the correctly rounded FP32 sum
+    assert np.array_equal(host(C), want)
+    check_map(host(C), oracle.madd(Ah, Bh), np.abs(Ah) + np.abs(Bh), "C")
+    # in place
+    kf.kf_madd(A, B, A)
+    assert np.array_equal(host(A), want)
