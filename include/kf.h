@@ -409,7 +409,8 @@ kf_status kf_plan_time_all(const kf_script* s, int max_plans, void* const* bindi
  * for vector passes rows in flight and grid size), each timed as the mean
  * of `reps` back-to-back launches (best of two rounds, after a warm-up of
  * the current choice), and stores the fastest in a process-wide tuning
- * cache keyed by op signature, storage
+ * cache (keeping the current choice unless the fastest gains more than 2 %,
+ * since short timings are noisy), keyed by op signature, storage
  * format and size class (powers of two of m and n).  Automatic launches
  * (every entry point, unless kf_set_matrix_tuning fixed a tuning) consult
  * the cache.  Synchronous; it writes the plan's outputs and in-place

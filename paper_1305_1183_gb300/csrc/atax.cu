@@ -285,7 +285,8 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
 // rows per barrier (unroll field).  On a miss, with tuning on first use
 // enabled, every fitting (rows per barrier in {1, 2}, blocks per SM in
 // {1, 2}, stages in {2, 3, 4, 6}) is timed on the call's operands (mean of
-// back-to-back launches, best of two rounds) and the fastest stored.
+// back-to-back launches, best of two rounds) and the fastest stored, unless
+// it gains less than 2 % over the built-in choice.
 int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, void* ws,
                       size_t ws_bytes, void* stream, const char** why) {
   auto cls = [](int64_t v) {
@@ -303,10 +304,20 @@ int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const f
       cudaEvent_t a, b;
       cudaEventCreate(&a);
       cudaEventCreate(&b);
+      // warm up with the built-in choice, then time it
+      for (int r = 0; r < 2; ++r) launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, 0, 0, stream, why, 1);
+      float base = 1e30f;
+      for (int round = 0; round < 2; ++round) {
+        cudaEventRecord(a, st);
+        for (int r = 0; r < reps; ++r) launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, 0, 0, stream, why, 1);
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        base = std::min(base, ms / (float)reps);
+      }
       float best = 1e30f;
       MatTune bt = t;
-      // warm up with the built-in choice
-      for (int r = 0; r < 2; ++r) launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, 0, 0, stream, why, 1);
       for (int rp : {1, 2})
       for (int cps : {1, 2})
         for (int stg : {2, 3, 4, 6}) {
@@ -331,6 +342,8 @@ int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const f
         }
       cudaEventDestroy(a);
       cudaEventDestroy(b);
+      // keep the built-in choice unless a candidate gains more than 2 %
+      if (best > base * 0.98f) bt = MatTune{1, 0, 1, 0, 0};
       if (best < 1e29f) {
         tune_cache_put_mat(key, bt);
         t = bt;

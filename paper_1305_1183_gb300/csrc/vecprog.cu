@@ -357,9 +357,14 @@ int autotune_vecprog(VecProg& P, void* stream, int reps, VecTune* best, float* b
     *ms = bestr;
     return 0;
   };
-  {  // warm the GPU with the current choice before timing
+  // the current choice: the cache's entry, else the built-in default
+  VecTune cur{};
+  if (!tune_cache_get_vec(vec_cache_key(P), &cur)) cur = VecTune{256, 4, 0};
+  float am = 1e30f;
+  {  // warm the GPU with the current choice, then time it
     float ms = 0.f;
     time_one(VecTune{0, 0, 0}, &ms);
+    if (time_one(VecTune{0, 0, 0}, &ms) == 0) am = ms;
   }
   float bm = 1e30f;
   VecTune bt{256, 4, 0};
@@ -369,11 +374,18 @@ int autotune_vecprog(VecProg& P, void* stream, int reps, VecTune* best, float* b
       float ms = 0.f;
       if (time_one(t, &ms) == 0 && ms < bm * 0.999f) { bm = ms; bt = t; }
     }
-  float am = 0.f;
-  time_one(VecTune{0, 0, 0}, &am);
+  {
+    float ms = 0.f;
+    if (time_one(VecTune{0, 0, 0}, &ms) == 0) am = std::min(am, ms);
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (bm >= 1e29f) return -7;
+  // switch away from the current choice only for a gain of more than 2 %
+  if (am < 1e29f && bm > am * 0.98f) {
+    bt = cur;
+    bm = am;
+  }
   tune_cache_put_vec(vec_cache_key(P), bt);
   *best = bt;
   *best_ms = bm;
