@@ -403,9 +403,7 @@ kf_status kf_plan_time_all(const kf_script* s, int max_plans, void* const* bindi
  * fusion implementation; routines are benchmarked once per architecture).
  * kf_autotune_plan runs, for every kernel of the plan on the bound data,
  * each compiled implementation that fits its op shape (warps, 16-byte chunks
- * per lane, rows per batch, direct loads with or without a bulk L2
- * prefetch of the block's row segments 16 rows ahead, or a bulk-copy ring of
- * depth 2..4;
+ * per lane, rows per batch, direct loads or a bulk-copy ring of depth 2..4;
  * for vector passes rows in flight and grid size), each timed as the mean
  * of `reps` back-to-back launches (best of two rounds, after a warm-up of
  * the current choice), and stores the fastest in a process-wide tuning

@@ -86,7 +86,6 @@ struct MatProg {
   float* colpart;                // [ncol_res][n_groups][n]
   unsigned* counters;            // [n_strips + n_groups], zero between launches
   unsigned* errword;             // device error word (bounded waits that ran out)
-  int pf;                        // direct loads: rows ahead whose strip segment is prefetched into L2 (0: off)
 };
 
 struct VecProg {
@@ -110,7 +109,6 @@ struct MatTune {
   int unroll;     // rows loaded together: 1, 2 or 4
   int groups;     // row groups (0 = automatic)
   int stages;     // bulk-copy ring depth per warp; 0 = direct 16-byte loads
-  int pf = 0;     // direct loads: rows ahead prefetched into L2 (0 = off)
 };
 
 // Tuning knobs of a vector-pass launch.

@@ -121,7 +121,7 @@ void tune_cache_dump(std::vector<std::string>* lines) {
   for (auto& kv : g_mat_cache)
     lines->push_back(kv.first + " : " + std::to_string(kv.second.warps) + " " + std::to_string(kv.second.vec) + " " +
                      std::to_string(kv.second.unroll) + " " + std::to_string(kv.second.groups) + " " +
-                     std::to_string(kv.second.stages) + " " + std::to_string(kv.second.pf));
+                     std::to_string(kv.second.stages));
   for (auto& kv : g_vec_cache)
     lines->push_back(kv.first + " : " + std::to_string(kv.second.threads) + " " + std::to_string(kv.second.unroll) +
                      " " + std::to_string(kv.second.blocks));
@@ -308,7 +308,6 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   if (strips > 0x7fffffffLL) { *why = "matrix too wide"; return -2; }
   P.n_strips = (int)strips;
   P.n_groups = (int)G;
-  P.pf = e.staged ? 0 : std::max(0, t.pf);
   P.blocks_per_group = bpg;
   P.stages = stages;
   dim3 grid((unsigned)strips, (unsigned)G);
@@ -347,7 +346,7 @@ int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* b
     if (e.staged) {
       for (int st : {2, 3, 4}) cands.push_back(MatTune{e.nw, e.v, e.u, 0, st});
     } else {
-      for (int pf : {0, 16}) cands.push_back(MatTune{e.nw, e.v, e.u, 0, 0, pf});
+      cands.push_back(MatTune{e.nw, e.v, e.u, 0, 0});
     }
   }
   if (cands.empty()) return -10;

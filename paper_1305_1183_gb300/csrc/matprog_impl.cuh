@@ -585,17 +585,6 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
 #pragma unroll
         for (int r16 = 0; r16 < 8; r16 += U) {
           const int r = h * 8 + r16;
-          if constexpr (VEC && !STAGED) {
-            // one lane per (matrix, row) of the batch prefetches the block's
-            // segment of the row P.pf rows ahead into L2, so the direct loads
-            // of the later rows find it there
-            if (P.pf > 0 && warp == 0 && lane < NMAT * U && col0 + SW <= n) {
-              const int t = lane / U, u = lane % U;
-              const int64_t prow = row0 + r + u + P.pf;
-              if (prow < min(m, rb_end << 5))
-                prefetch_l2(static_cast<const char*>(P.A[t]) + (prow * P.lda[t] + col0) * BYTES, (unsigned)SEG);
-            }
-          }
           BatchT a;
           load_batch(row0, r, j, a);
           ++j;
