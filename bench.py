@@ -701,6 +701,9 @@ def main():
     ap.add_argument("--autotune", type=int, default=3,
                     help="timed runs per candidate of the first-use tuning search (0: built-in defaults)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-instances section")
+    ap.add_argument("--only", default="", choices=["", "batched", "precision"],
+                    help="run only this section and print its JSON (profiling)")
+    ap.add_argument("--batched-count", type=int, default=4096, help="instances per batched launch")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
 
@@ -735,6 +738,14 @@ def main():
     elif args.autotune > 0:
         # every kernel shape is searched on its first (warm-up) launch
         kf.kf_set_autotune(args.autotune)
+    if args.only:
+        d = torch.device("cuda", local)
+        st = torch.cuda.Stream()
+        sec = (batched_section(kf, d, st, args.steps, args.warmup, count=args.batched_count)
+               if args.only == "batched" else precision_section(kf, d, st, args.steps, args.warmup))
+        if rank == 0:
+            print(json.dumps({args.only: sec}), flush=True)
+        return
     suite = Suite(kf, sizes, torch.device("cuda", local), seqs=seqs)
     st = torch.cuda.Stream()
     torch.cuda.synchronize()
@@ -762,7 +773,8 @@ def main():
         if not args.no_precision:
             extra["precision"] = precision_section(kf, torch.device("cuda", local), st, args.steps, args.warmup)
         if not args.no_batched:
-            extra["batched"] = batched_section(kf, torch.device("cuda", local), st, args.steps, args.warmup)
+            extra["batched"] = batched_section(kf, torch.device("cuda", local), st, args.steps, args.warmup,
+                                               count=args.batched_count)
         suite = Suite(kf, sizes, torch.device("cuda", local), seqs=seqs)
 
     e2e = None
