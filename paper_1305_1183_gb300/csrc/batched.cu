@@ -14,6 +14,11 @@
 // The queue and the counters reset themselves, so the launch can be
 // replayed from a CUDA graph.
 //
+// GESUMMV instances use a width-adapted strip (batched_rows_kernel): cw x 128
+// columns, cw in {1, 2, 4, 8}, with the block's 8 / cw warp rows taking
+// turns over the band's 32-row blocks, so narrow matrices do not leave
+// warps on masked columns.
+//
 // Loads are element-interleaved (lane l of a warp reads columns l, l+32,
 // l+64, l+96 of its 128-column slice), so every load instruction covers 128
 // contiguous bytes for any row length and alignment.
@@ -44,7 +49,7 @@ struct BDesc {
   float* s;         // BiCGK s
   float alpha, beta;
   int64_t rowpart_off, colpart_off;
-  int ntiles, nstrips, nbands, pad;
+  int ntiles, nstrips, nbands, cw;  // cw: warps side by side across the strip (width-adapted form)
 };
 
 struct BTile {
@@ -214,6 +219,191 @@ __global__ void __launch_bounds__(BNW * 32, 4)
   }
 }
 
+// Width-adapted form (used for GESUMMV): cw warps side by side across a
+// strip of cw x 128 columns, the 8 / cw warp rows taking turns over the
+// band's 32-row blocks; 3 blocks per SM.  KIND as above.
+template <int KIND>
+__global__ void __launch_bounds__(BNW * 32, 3)
+    batched_rows_kernel(const BDesc* __restrict__ D, const BTile* __restrict__ T, int ntiles, int band_rows,
+                   float* __restrict__ rowpart, float* __restrict__ colpart, unsigned* __restrict__ inst_count,
+                   unsigned* __restrict__ queue) {
+  constexpr int NM = KIND == 0 ? 1 : 2;   // matrices
+  constexpr int NR = KIND == 0 ? 1 : 2;   // row results
+  __shared__ int s_tile;
+  __shared__ int s_last;
+  __shared__ BDesc s_desc;  // the tile's instance, read field by field (keeps registers free)
+  __shared__ float red[2][NR][BNW][32];
+  __shared__ float csum[KIND == 0 ? BNW : 1][128];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  for (;;) {
+    __syncthreads();  // previous tile's shared-memory use is over
+    if (threadIdx.x == 0) {
+      const int tt = (int)atomicAdd(&queue[0], 1u);
+      s_tile = tt;
+      if (tt < ntiles) s_desc = D[T[tt].inst];
+    }
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const BTile tl = T[t];
+    const BDesc& d = s_desc;
+    const int64_t m = d.m, n = d.n;
+    // cw warps side by side cover the strip (cw * 128 columns); the block's
+    // rw = 8 / cw warp rows take turns over the band's 32-row blocks
+    const int cw = d.cw, rw = BNW / cw;
+    const int wcol = warp % cw, wrow = warp / cw;
+    const int64_t r0 = (int64_t)tl.band * band_rows;
+    const int64_t r1 = min(m, r0 + band_rows);
+    const int64_t wc = (int64_t)tl.strip * cw * 128 + wcol * 128;  // this warp's slice
+
+    float xv[4], acc[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t c = wc + e * 32 + lane;
+      xv[e] = c < n ? __ldg(d.x + c) : 0.f;
+      acc[e] = 0.f;
+    }
+    const int64_t nblk = (r1 - r0 + 31) >> 5;
+    const int64_t iters = (nblk + rw - 1) / rw;  // the same for every warp (barriers below)
+    for (int64_t it = 0; it < iters; ++it) {
+      const int64_t k = it * rw + wrow;
+      const bool blk_ok = k < nblk;  // warp-uniform
+      const int64_t row0 = r0 + k * 32;
+      const bool lane_ok = blk_ok && row0 + lane < r1;
+      const float rv = (KIND == 0 && lane_ok) ? __ldg(d.r + row0 + lane) : 0.f;
+      float rowdot[NR];
+#pragma unroll
+      for (int g = 0; g < NR; ++g) rowdot[g] = 0.f;
+      if (blk_ok) {
+#pragma unroll 1
+        for (int h = 0; h < 4; ++h) {
+          float dacc[NR][8];
+#pragma unroll
+          for (int g = 0; g < NR; ++g)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dacc[g][i] = 0.f;
+#pragma unroll
+          for (int b = 0; b < 8; b += 4) {
+            float a[NM][4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int64_t row = row0 + h * 8 + b + u;
+              const bool rok = row < r1;
+#pragma unroll
+              for (int kk = 0; kk < NM; ++kk) {
+                const float* rowp = (kk == 0 ? d.A : d.B) + row * d.lda;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const int64_t c = wc + e * 32 + lane;
+                  a[kk][u][e] = (rok && c < n) ? __ldcs(rowp + c) : 0.f;
+                }
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+              for (int kk = 0; kk < NM; ++kk) {
+                float dd = 0.f;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dd = fmaf(a[kk][u][e], xv[e], dd);
+                dacc[kk][b + u] += dd;
+              }
+              if (KIND == 0) {
+                const float y = __shfl_sync(FULL_MASK, rv, h * 8 + b + u);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[e] = fmaf(a[0][u][e], y, acc[e]);
+              }
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < NR; ++g) {
+            const float v = reduce8(dacc[g], lane);
+            if ((lane >> 3) == h) rowdot[g] = v;
+          }
+        }
+      }
+      // row dots across the cw warps of this warp row, in fixed warp order
+      if (cw == 1) {
+        if (lane_ok)
+#pragma unroll
+          for (int g = 0; g < NR; ++g)
+            rowpart[d.rowpart_off + ((int64_t)g * d.nstrips + tl.strip) * m + row0 + lane] = rowdot[g];
+      } else {
+        const int buf = (int)(it & 1);
+#pragma unroll
+        for (int g = 0; g < NR; ++g) red[buf][g][warp][lane] = rowdot[g];
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + wrow), "r"(cw * 32) : "memory");
+        if (wcol < NR && lane_ok) {
+          float sum = 0.f;
+          for (int w = 0; w < cw; ++w) sum += red[buf][wcol][wrow * cw + w][lane];
+          rowpart[d.rowpart_off + ((int64_t)wcol * d.nstrips + tl.strip) * m + row0 + lane] = sum;
+        }
+      }
+    }
+    if (KIND == 0) {
+      // column sums of the strip: the rw warp rows added in row order
+      if (rw == 1) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t c = wc + e * 32 + lane;
+          if (c < n) colpart[d.colpart_off + (int64_t)tl.band * n + c] = acc[e];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) csum[warp][e * 32 + lane] = acc[e];
+        __syncthreads();
+        if (wrow == 0) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float sum = 0.f;
+            for (int q = 0; q < rw; ++q) sum += csum[q * cw + wcol][e * 32 + lane];
+            const int64_t c = wc + e * 32 + lane;
+            if (c < n) colpart[d.colpart_off + (int64_t)tl.band * n + c] = sum;
+          }
+        }
+      }
+    }
+    // last tile of the instance finishes it
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&inst_count[tl.inst], 1u) == (unsigned)d.ntiles - 1u;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+        float v[NR];
+#pragma unroll
+        for (int g = 0; g < NR; ++g) {
+          float sum = 0.f;
+          for (int st = 0; st < d.nstrips; ++st)
+            sum += __ldcg(rowpart + d.rowpart_off + ((int64_t)g * d.nstrips + st) * m + i);
+          v[g] = sum;
+        }
+        if (KIND == 0) d.y[i] = v[0];
+        else d.y[i] = __fadd_rn(__fmul_rn(d.alpha, v[0]), __fmul_rn(d.beta, v[NR - 1]));
+      }
+      if (KIND == 0) {
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+          float sum = 0.f;
+          for (int bnd = 0; bnd < d.nbands; ++bnd) sum += __ldcg(colpart + d.colpart_off + (int64_t)bnd * n + j);
+          d.s[j] = sum;
+        }
+      }
+      if (threadIdx.x == 0) inst_count[tl.inst] = 0u;
+    }
+  }
+  // the last block out resets the queue for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&queue[1], 1u) == gridDim.x - 1u) {
+      queue[0] = 0u;
+      queue[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -268,7 +458,11 @@ kf_status kf_batched_create(kf_seq seq, const kf_batch_desc* descs, int count, i
     d.m = u.m; d.n = u.n; d.lda = u.lda;
     d.A = u.A; d.B = u.B; d.x = u.x; d.r = u.r; d.y = u.y; d.s = u.s;
     d.alpha = u.alpha; d.beta = u.beta;
-    d.nstrips = (int)std::max<int64_t>(1, (u.n + BSW - 1) / BSW);
+    // GESUMMV: narrow matrices take fewer warps per row (more row blocks in
+    // flight, batched_rows_kernel); BiCGK keeps all 8 warps across the row
+    // (batched_kernel: measured faster for it)
+    d.cw = b->kind == 0 ? BNW : (u.n <= 128 ? 1 : u.n <= 256 ? 2 : u.n <= 512 ? 4 : BNW);
+    d.nstrips = (int)std::max<int64_t>(1, (u.n + d.cw * 128 - 1) / (d.cw * 128));
     d.nbands = (int)std::max<int64_t>(1, (u.m + band_rows - 1) / band_rows);
     d.ntiles = d.nstrips * d.nbands;
     d.rowpart_off = b->rowpart_floats;
@@ -284,7 +478,8 @@ kf_status kf_batched_create(kf_seq seq, const kf_batch_desc* descs, int count, i
   auto tsize = [&](const BTile& t) {
     const BDesc& d = b->desc[t.inst];
     const int64_t rows = std::min<int64_t>(band_rows, d.m - (int64_t)t.band * band_rows);
-    const int64_t cols = std::min<int64_t>(BSW, d.n - (int64_t)t.strip * BSW);
+    const int64_t sw = (int64_t)d.cw * 128;
+    const int64_t cols = std::min<int64_t>(sw, d.n - (int64_t)t.strip * sw);
     return rows * cols;
   };
   std::stable_sort(b->tiles.begin(), b->tiles.end(), [&](const BTile& x, const BTile& y) { return tsize(x) > tsize(y); });
@@ -339,7 +534,7 @@ kf_status kf_batched_launch(const kf_batched* b, void* ws, size_t ws_bytes, void
   }
   if (b->tiles.empty()) return KF_OK;
   char* w = static_cast<char*>(ws);
-  const void* fn = b->kind == 0 ? (const void*)&batched_kernel<0> : (const void*)&batched_kernel<1>;
+  const void* fn = b->kind == 0 ? (const void*)&batched_kernel<0> : (const void*)&batched_rows_kernel<1>;
   static int occ[2] = {0, 0};
   if (occ[b->kind] == 0) {
     int o = 0;
