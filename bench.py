@@ -386,47 +386,33 @@ def time_suite(suite, mode, steps, warmup, st, seqs):
 def time_e2e(suite, steps, warmup, st, seqs):
     """Same metric through the public API from pinned host buffers: every step
     copies the inputs host->device, runs the fused suite and reads the results
-    back device->host.  The read-back of step k runs on a second stream while
-    step k+1's inputs are copied in (the link carries both directions at
-    once); step k+1's kernels wait until step k's results have been read."""
+    back device->host."""
     hin = {s: [t.detach().cpu().pin_memory() for t in suite.inputs(s)] for s in seqs}
     hout = {s: [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in suite.outputs(s)] for s in seqs}
     h2d = sum(t.numel() * t.element_size() for s in seqs for t in hin[s])
     d2h = sum(t.numel() * t.element_size() for s in seqs for t in hout[s])
-    rd = torch.cuda.Stream()
-    state = {"read": None}
 
     def one():
-        with torch.cuda.stream(st):
-            for s in seqs:
-                for dst, src in zip(suite.inputs(s), hin[s]):
-                    dst.copy_(src, non_blocking=True)
-            if state["read"] is not None:
-                st.wait_event(state["read"])  # previous results read back: outputs free
-            for s in seqs:
-                suite.fused(s, st)
-            done = torch.cuda.Event()
-            done.record(st)
-        rd.wait_event(done)
-        with torch.cuda.stream(rd):
-            for s in seqs:
-                for dst, src in zip(hout[s], suite.outputs(s)):
-                    dst.copy_(src, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(rd)
-        state["read"] = ev
+        for s in seqs:
+            for dst, src in zip(suite.inputs(s), hin[s]):
+                dst.copy_(src, non_blocking=True)
+            suite.fused(s, st)
+            for dst, src in zip(hout[s], suite.outputs(s)):
+                dst.copy_(src, non_blocking=True)
 
     torch.cuda.synchronize()
-    for _ in range(warmup):
-        one()
-    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        for _ in range(warmup):
+            one()
+    st.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
-    a.record(st)
-    for _ in range(steps):
-        one()
-    b.record(rd)  # after the last read-back, which follows the last kernels
-    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        a.record(st)
+        for _ in range(steps):
+            one()
+        b.record(st)
+    st.synchronize()
     return a.elapsed_time(b), h2d, d2h
 
 
@@ -793,8 +779,8 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e_steps = max(1, min(args.steps, 10))
-        e2e_ms, h2d, d2h = time_e2e(suite, e2e_steps, 1, st, seqs)
+        e2e_ms, h2d, d2h = time_e2e(suite, max(1, min(args.steps, 5)), 1, st, seqs)
+        e2e_steps = max(1, min(args.steps, 5))
 
     step_bytes = sum(algorithmic_bytes(s, sizes[s]) for s in seqs)
     t_max = total_ms
