@@ -196,11 +196,6 @@ __global__ void __launch_bounds__(FIN_COLS * FIN_SLICES) atax_finish_kernel(cons
   }
 }
 
-struct AEntry {
-  const void* fn;
-  int occ_for_stages[ATAX_MAXSTAGES + 1];
-};
-
 template <int VA>
 const void* atax_fn(int rp) {
   return rp == 2 ? (const void*)&atax_rows_kernel<512, VA, 2> : (const void*)&atax_rows_kernel<512, VA, 1>;
