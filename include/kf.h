@@ -369,6 +369,9 @@ typedef struct {
   int max_plans;  /* enumeration cap (<= 0: 2000)            */
   int top_k;      /* KF_SELECT_MLP: best-ranked plans timed  */
   int reps;       /* timed runs per plan (<= 0: 3)           */
+  float margin;   /* KF_SELECT_MLP: also time every plan whose score is
+                     within `margin` of the best score (ln(ms) units; at
+                     most 64 plans in all); 0: top_k only             */
 } kf_select_options;
 
 typedef struct {

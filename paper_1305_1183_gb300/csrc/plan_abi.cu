@@ -657,7 +657,15 @@ kf_status kf_plan_select(const kf_script* s, const kf_select_options* opt, const
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return y[a] < y[b]; });
     chosen = order[0];
     predicted = y[chosen];
-    if (opt->top_k > 1) cand.assign(order.begin(), order.begin() + std::min(opt->top_k, count));
+    // the top_k best-ranked plans, plus (margin > 0) every plan scored within
+    // `margin` of the best, at most 64: ambiguous rankings are settled by timing
+    int ntime = opt->top_k > 1 ? std::min(opt->top_k, count) : 0;
+    if (opt->margin > 0.f) {
+      int nm = 0;
+      while (nm < count && nm < 64 && y[order[nm]] - y[order[0]] <= opt->margin) ++nm;
+      if (nm > 1) ntime = std::max(ntime, nm);
+    }
+    if (ntime > 1) cand.assign(order.begin(), order.begin() + ntime);
   } else if (opt->mode == KF_SELECT_EXHAUSTIVE) {
     cand.resize(count);
     for (int i = 0; i < count; ++i) cand[i] = i;

@@ -327,7 +327,7 @@ NFEATURES = 16
 
 
 class _SelectOptions(ctypes.Structure):
-    _fields_ = [("mode", ci), ("max_plans", ci), ("top_k", ci), ("reps", ci)]
+    _fields_ = [("mode", ci), ("max_plans", ci), ("top_k", ci), ("reps", ci), ("margin", ctypes.c_float)]
 
 
 class _CostModel(ctypes.Structure):
@@ -453,9 +453,10 @@ class Script:
         _ck(lib().kf_plan_select_workspace_size(self.h, max_plans, ctypes.byref(b)))
         return b.value
 
-    def select(self, mode, bindings=None, ws=None, model=None, top_k=1, reps=3, max_plans=0, stream=None):
+    def select(self, mode, bindings=None, ws=None, model=None, top_k=1, reps=3, max_plans=0, margin=0.0,
+               stream=None):
         """kf_plan_select: (Plan, info dict with index, count, timed, best_ms, predicted)."""
-        opt = _SelectOptions(mode, max_plans, top_k, reps)
+        opt = _SelectOptions(mode, max_plans, top_k, reps, margin)
         cm = model._c() if model is not None else None
         arr, nv = self._bind(bindings) if bindings else (None, 0)
         h = vp()

@@ -174,7 +174,7 @@ def train(X, ms, pred_us, script_ids=None, analytic_weight=1.0, epochs=3000, lr=
     return kf.CostModel(p, mean, inv_std, analytic_weight), hist
 
 
-def evaluate(seed, indices, kmin, kmax, model, reps, top_k=3, cap=2000, device="cuda"):
+def evaluate(seed, indices, kmin, kmax, model, reps, top_k=3, cap=2000, margin=0.1, device="cuda"):
     """Per held-out script: exhaustive timings, and each method's choice."""
     rows = []
     for i in indices:
@@ -189,11 +189,13 @@ def evaluate(seed, indices, kmin, kmax, model, reps, top_k=3, cap=2000, device="
         _, i1 = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=1, max_plans=cap)
         _, ik = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=top_k, reps=reps, max_plans=cap)
         _, i5 = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=2 * top_k, reps=reps, max_plans=cap)
+        _, im = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=top_k, reps=reps, max_plans=cap, margin=margin)
         t_unf = unf.time(bind, ws, reps=reps)
         best = float(t.min())
         rows.append({"index": int(i), "n": n, "calls": len(sd["calls"]), "plans": len(t), "best_ms": best,
                      "mlp": float(t[i1["index"]]) / best, "mlp_topk": float(t[ik["index"]]) / best,
                      "mlp_top2k": float(t[i5["index"]]) / best,
+                     "mlp_margin": float(t[im["index"]]) / best, "timed_margin": im["timed"],
                      "analytic": float(t[ia["index"]]) / best, "greedy": float(t[int(np.argmin(nk))]) / best,
                      "unfused": t_unf / best, "timed_topk": ik["timed"]})
         del bind, ws
@@ -207,27 +209,32 @@ def summary(rows, key):
 
 
 def run(seed=0, scripts=500, ntrain=400, kmin=10, kmax=14, per_script=64, reps=5, epochs=3000, top_k=3,
-        analytic_weight=1.0, centre=True, device="cuda", log=print):
+        analytic_weight=1.0, centre=True, margin=0.1, device="cuda", log=print):
     t0 = time.time()
     X, ms, pu, sid, meta = collect(seed, range(ntrain), kmin, kmax, per_script, reps, device=device)
     t1 = time.time()
     model, hist = train(X, ms, pu, sid if centre else None, analytic_weight, epochs=epochs, seed=seed,
                         device=device)
     t2 = time.time()
-    rows = evaluate(seed, range(ntrain, scripts), kmin, kmax, model, reps, top_k=top_k, device=device)
+    rows = evaluate(seed, range(ntrain, scripts), kmin, kmax, model, reps, top_k=top_k, margin=margin,
+                    device=device)
     t3 = time.time()
     plans = np.array([r["plans"] for r in rows])
     out = {
         "config": {"seed": seed, "scripts": scripts, "train": ntrain, "test": scripts - ntrain,
                    "n": f"2^{kmin}..2^{kmax}", "per_script": per_script, "reps": reps, "epochs": epochs,
-                   "top_k": top_k, "analytic_weight": analytic_weight, "centred_per_script": centre,
+                   "top_k": top_k, "margin": margin, "analytic_weight": analytic_weight,
+                   "centred_per_script": centre,
                    "features": kf.NFEATURES,
                    "hidden": kf.MLP_HIDDEN},
         "train_plans_timed": int(len(ms)), "test_plans_timed": int(plans.sum()),
         "test_plans_per_script": {"mean": float(plans.mean()), "max": int(plans.max())},
         "seconds": {"collect": round(t1 - t0, 1), "train": round(t2 - t1, 2), "evaluate": round(t3 - t2, 1)},
         "loss": hist,
-        "test": {k: summary(rows, k) for k in ("mlp", "mlp_topk", "mlp_top2k", "analytic", "greedy", "unfused")},
+        "test": {k: summary(rows, k) for k in ("mlp", "mlp_topk", "mlp_top2k", "mlp_margin", "analytic", "greedy",
+                                                "unfused")},
+        "timed_per_script": {"topk": float(np.mean([r["timed_topk"] for r in rows])),
+                             "margin": float(np.mean([r["timed_margin"] for r in rows]))},
         "rows": rows,
     }
     if log:
@@ -250,12 +257,13 @@ def main(argv=None):
     ap.add_argument("--top-k", type=int, default=3)
     ap.add_argument("--analytic-weight", type=float, default=1.0)
     ap.add_argument("--no-centre", action="store_true", help="absolute targets instead of per-script centred")
+    ap.add_argument("--margin", type=float, default=0.1, help="score margin (ln ms) of plans also re-timed")
     ap.add_argument("--out", default="")
     ap.add_argument("--save-model", default="")
     a = ap.parse_args(argv)
     kf.lib()
     res, model = run(a.seed, a.scripts, a.train, a.kmin, a.kmax, a.per_script, a.reps, a.epochs, a.top_k,
-                     a.analytic_weight, centre=not a.no_centre)
+                     a.analytic_weight, centre=not a.no_centre, margin=a.margin)
     if a.out:
         with open(a.out, "w") as fh:
             json.dump(res, fh, indent=1)
