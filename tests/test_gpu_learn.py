@@ -65,6 +65,12 @@ def test_select_mlp_first_choice_is_model_argmin(built):
     # top_k at least the plan count: every plan is timed (exhaustive fallback)
     _, info = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=10 ** 6, reps=1)
     assert info["timed"] == info["count"]
+    # a margin covering every score times every plan, at most 64
+    _, info = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=1, reps=1, margin=1e9)
+    assert info["timed"] == min(info["count"], 64)
+    # a zero margin and top_k 1 time nothing
+    _, info = s.select(kf.KF_SELECT_MLP, bind, ws, model, top_k=1, margin=0.0)
+    assert info["timed"] == 0
 
 
 def test_select_errors(built):
