@@ -2,26 +2,25 @@
 // persistent launch.
 //
 // The host cuts every instance into tiles (row bands of `band_rows` rows x
-// column strips of NW*128 columns) and sorts them largest first.  Blocks
-// pull tiles from an atomic queue; a tile is processed like one block of
-// the matrix pass (warps side by side across the strip, row dots kept as
-// per-lane partials of 8 rows, column sums in registers), writing the
-// tile's row partial (per strip) and column partial (per band) of its
-// instance.  The last tile of an instance to finish (a per-instance
-// counter) adds the partials in strip / band order and writes the outputs
-// (Section 3.2.2, option (ii)), so each instance's result does not depend
-// on which block ran which tile, and equals the same instance run alone.
-// The queue and the counters reset themselves, so the launch can be
-// replayed from a CUDA graph.
-//
-// GESUMMV instances use a width-adapted strip (batched_rows_kernel): cw x 128
-// columns, cw in {1, 2, 4, 8}, with the block's 8 / cw warp rows taking
-// turns over the band's 32-row blocks, so narrow matrices do not leave
-// warps on masked columns.
+// column strips) and sorts them largest first.  An instance's strip is as
+// wide as the instance needs, cw x 128 columns with cw in {1, 2, 4, 8}
+// warps side by side; the block's 8 / cw warp rows take turns over the
+// band's 32-row blocks, so narrow matrices do not leave warps on masked
+// columns.  Blocks pull tiles from an atomic queue; in a tile, row dots are
+// kept as per-lane partials of 8 rows, reduced across the cw warps of a warp
+// row (a named barrier per warp row), and column sums are added across the
+// warp rows in row order at the end of the tile; the tile writes its
+// instance's row partial (per strip) and column partial (per band).  The
+// last tile of an instance to finish (a per-instance counter) adds the
+// partials in strip / band order and writes the outputs (Section 3.2.2,
+// option (ii)), so each instance's result does not depend on which block ran
+// which tile, and equals the same instance run alone.  The queue and the
+// counters reset themselves, so the launch can be replayed from a CUDA graph.
 //
 // Loads are element-interleaved (lane l of a warp reads columns l, l+32,
 // l+64, l+96 of its 128-column slice), so every load instruction covers 128
-// contiguous bytes for any row length and alignment.
+// contiguous bytes for any row length and alignment; a warp keeps 8 rows
+// of one matrix (BiCGK) or 4 rows of two (GESUMMV) in flight.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,7 +56,6 @@ struct BTile {
 };
 
 constexpr int BNW = 8;             // warps per block (side by side)
-constexpr int BSW = BNW * 128;     // strip width (columns)
 
 __device__ __forceinline__ float reduce8(float (&d)[8], int lane) {
 #pragma unroll
@@ -77,158 +75,17 @@ __device__ __forceinline__ float reduce8(float (&d)[8], int lane) {
   return d[0];
 }
 
-// KIND 0: BiCGK (q = A p, s = A^T r);  KIND 1: GESUMMV (y = a A x + b B x)
+// KIND 0: BiCGK (q = A p, s = A^T r);  KIND 1: GESUMMV (y = a A x + b B x).
+// cw warps side by side across a strip of cw x 128 columns, the 8 / cw warp
+// rows taking turns over the band's 32-row blocks; 3 blocks per SM.
 template <int KIND>
-__global__ void __launch_bounds__(BNW * 32, 4)
+__global__ void __launch_bounds__(BNW * 32, 3)
     batched_kernel(const BDesc* __restrict__ D, const BTile* __restrict__ T, int ntiles, int band_rows,
                    float* __restrict__ rowpart, float* __restrict__ colpart, unsigned* __restrict__ inst_count,
                    unsigned* __restrict__ queue) {
   constexpr int NM = KIND == 0 ? 1 : 2;   // matrices
   constexpr int NR = KIND == 0 ? 1 : 2;   // row results
-  __shared__ int s_tile;
-  __shared__ int s_last;
-  __shared__ float red[2][NR][BNW][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  for (;;) {
-    __syncthreads();  // previous tile's shared-memory use is over
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&queue[0], 1u);
-    __syncthreads();
-    const int t = s_tile;
-    if (t >= ntiles) break;
-    const BTile tl = T[t];
-    const BDesc d = D[tl.inst];
-    const int64_t m = d.m, n = d.n;
-    const int64_t r0 = (int64_t)tl.band * band_rows;
-    const int64_t r1 = min(m, r0 + band_rows);
-    const int64_t wc = (int64_t)tl.strip * BSW + warp * 128;  // this warp's slice
-
-    float xv[4], acc[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int64_t c = wc + e * 32 + lane;
-      xv[e] = c < n ? __ldg(d.x + c) : 0.f;
-      acc[e] = 0.f;
-    }
-    for (int64_t row0 = r0; row0 < r1; row0 += 32) {
-      const bool lane_ok = row0 + lane < r1;
-      const float rv = (KIND == 0 && lane_ok) ? __ldg(d.r + row0 + lane) : 0.f;
-      float rowdot[NR];
-#pragma unroll 1
-      for (int h = 0; h < 4; ++h) {
-        float dacc[NR][8];
-#pragma unroll
-        for (int g = 0; g < NR; ++g)
-#pragma unroll
-          for (int i = 0; i < 8; ++i) dacc[g][i] = 0.f;
-#pragma unroll
-        for (int b = 0; b < 8; b += 4) {
-          float a[NM][4][4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int64_t row = row0 + h * 8 + b + u;
-            const bool rok = row < r1;
-#pragma unroll
-            for (int k = 0; k < NM; ++k) {
-              const float* rowp = (k == 0 ? d.A : d.B) + row * d.lda;
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const int64_t c = wc + e * 32 + lane;
-                a[k][u][e] = (rok && c < n) ? __ldcs(rowp + c) : 0.f;
-              }
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-#pragma unroll
-            for (int k = 0; k < NM; ++k) {
-              float dd = 0.f;
-#pragma unroll
-              for (int e = 0; e < 4; ++e) dd = fmaf(a[k][u][e], xv[e], dd);
-              dacc[k][b + u] += dd;
-            }
-            if (KIND == 0) {
-              const float y = __shfl_sync(FULL_MASK, rv, h * 8 + b + u);
-#pragma unroll
-              for (int e = 0; e < 4; ++e) acc[e] = fmaf(a[0][u][e], y, acc[e]);
-            }
-          }
-        }
-#pragma unroll
-        for (int g = 0; g < NR; ++g) {
-          const float v = reduce8(dacc[g], lane);
-          if ((lane >> 3) == h) rowdot[g] = v;
-        }
-      }
-      // row dots across the warps of the strip, fixed warp order
-      const int buf = (int)((row0 >> 5) & 1);
-#pragma unroll
-      for (int g = 0; g < NR; ++g) red[buf][g][warp][lane] = rowdot[g];
-      __syncthreads();
-      if (warp < NR && lane_ok) {
-        float sum = 0.f;
-#pragma unroll
-        for (int w = 0; w < BNW; ++w) sum += red[buf][warp][w][lane];
-        rowpart[d.rowpart_off + ((int64_t)warp * d.nstrips + tl.strip) * m + row0 + lane] = sum;
-      }
-    }
-    if (KIND == 0) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int64_t c = wc + e * 32 + lane;
-        if (c < n) colpart[d.colpart_off + (int64_t)tl.band * n + c] = acc[e];
-      }
-    }
-    // last tile of the instance finishes it
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&inst_count[tl.inst], 1u) == (unsigned)d.ntiles - 1u;
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-        float v[NR];
-#pragma unroll
-        for (int g = 0; g < NR; ++g) {
-          float sum = 0.f;
-          for (int st = 0; st < d.nstrips; ++st)
-            sum += __ldcg(rowpart + d.rowpart_off + ((int64_t)g * d.nstrips + st) * m + i);
-          v[g] = sum;
-        }
-        if (KIND == 0) d.y[i] = v[0];
-        else d.y[i] = __fadd_rn(__fmul_rn(d.alpha, v[0]), __fmul_rn(d.beta, v[NR - 1]));
-      }
-      if (KIND == 0) {
-        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-          float sum = 0.f;
-          for (int bnd = 0; bnd < d.nbands; ++bnd) sum += __ldcg(colpart + d.colpart_off + (int64_t)bnd * n + j);
-          d.s[j] = sum;
-        }
-      }
-      if (threadIdx.x == 0) inst_count[tl.inst] = 0u;
-    }
-  }
-  // the last block out resets the queue for the next launch
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&queue[1], 1u) == gridDim.x - 1u) {
-      queue[0] = 0u;
-      queue[1] = 0u;
-      __threadfence();
-    }
-  }
-}
-
-// Width-adapted form (used for GESUMMV): cw warps side by side across a
-// strip of cw x 128 columns, the 8 / cw warp rows taking turns over the
-// band's 32-row blocks; 3 blocks per SM.  KIND as above.
-template <int KIND>
-__global__ void __launch_bounds__(BNW * 32, 3)
-    batched_rows_kernel(const BDesc* __restrict__ D, const BTile* __restrict__ T, int ntiles, int band_rows,
-                   float* __restrict__ rowpart, float* __restrict__ colpart, unsigned* __restrict__ inst_count,
-                   unsigned* __restrict__ queue) {
-  constexpr int NM = KIND == 0 ? 1 : 2;   // matrices
-  constexpr int NR = KIND == 0 ? 1 : 2;   // row results
+  constexpr int BU = KIND == 0 ? 8 : 4;   // rows loaded together (the same bytes in flight for one matrix as for two)
   __shared__ int s_tile;
   __shared__ int s_last;
   __shared__ BDesc s_desc;  // the tile's instance, read field by field (keeps registers free)
@@ -284,10 +141,10 @@ __global__ void __launch_bounds__(BNW * 32, 3)
 #pragma unroll
             for (int i = 0; i < 8; ++i) dacc[g][i] = 0.f;
 #pragma unroll
-          for (int b = 0; b < 8; b += 4) {
-            float a[NM][4][4];
+          for (int b = 0; b < 8; b += BU) {
+            float a[NM][BU][4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < BU; ++u) {
               const int64_t row = row0 + h * 8 + b + u;
               const bool rok = row < r1;
 #pragma unroll
@@ -301,7 +158,7 @@ __global__ void __launch_bounds__(BNW * 32, 3)
               }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < BU; ++u) {
 #pragma unroll
               for (int kk = 0; kk < NM; ++kk) {
                 float dd = 0.f;
@@ -458,10 +315,8 @@ kf_status kf_batched_create(kf_seq seq, const kf_batch_desc* descs, int count, i
     d.m = u.m; d.n = u.n; d.lda = u.lda;
     d.A = u.A; d.B = u.B; d.x = u.x; d.r = u.r; d.y = u.y; d.s = u.s;
     d.alpha = u.alpha; d.beta = u.beta;
-    // GESUMMV: narrow matrices take fewer warps per row (more row blocks in
-    // flight, batched_rows_kernel); BiCGK keeps all 8 warps across the row
-    // (batched_kernel: measured faster for it)
-    d.cw = b->kind == 0 ? BNW : (u.n <= 128 ? 1 : u.n <= 256 ? 2 : u.n <= 512 ? 4 : BNW);
+    // narrow matrices take fewer warps per row and more row blocks at once
+    d.cw = u.n <= 128 ? 1 : u.n <= 256 ? 2 : u.n <= 512 ? 4 : BNW;
     d.nstrips = (int)std::max<int64_t>(1, (u.n + d.cw * 128 - 1) / (d.cw * 128));
     d.nbands = (int)std::max<int64_t>(1, (u.m + band_rows - 1) / band_rows);
     d.ntiles = d.nstrips * d.nbands;
@@ -534,7 +389,7 @@ kf_status kf_batched_launch(const kf_batched* b, void* ws, size_t ws_bytes, void
   }
   if (b->tiles.empty()) return KF_OK;
   char* w = static_cast<char*>(ws);
-  const void* fn = b->kind == 0 ? (const void*)&batched_kernel<0> : (const void*)&batched_rows_kernel<1>;
+  const void* fn = b->kind == 0 ? (const void*)&batched_kernel<0> : (const void*)&batched_kernel<1>;
   static int occ[2] = {0, 0};
   if (occ[b->kind] == 0) {
     int o = 0;
