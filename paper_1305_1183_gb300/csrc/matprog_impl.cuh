@@ -365,9 +365,10 @@ constexpr int sig_last_ger(int sig) {
 
 // Resident blocks per SM asked of the register allocator: the one-chunk
 // FP32 forms are latency bound and need four blocks of eight warps.
-template <int NW, int V, int NMAT, int FMT, bool VEC>
+template <int NW, int V, int NMAT, int FMT, bool VEC, int U>
 constexpr int min_blocks() {
-  return (NW == 8 && V == 1 && NMAT == 1 && FMT == FMT_F32) ? 4 : ((FMT != FMT_F32 && VEC) ? 2 : 1);
+  return (NW == 8 && V == 1 && NMAT == 1 && FMT == FMT_F32) ? (U >= 8 ? 3 : 4)
+                                                              : ((FMT != FMT_F32 && VEC) ? 2 : 1);
 }
 
 // Registers of one batch of rows: decoded floats, or packed chunks.
@@ -375,7 +376,7 @@ template <bool RAW, int NMAT, int U, int V, int W> struct BatchOf { using type =
 template <int NMAT, int U, int V, int W> struct BatchOf<true, NMAT, U, V, W> { using type = uint4[NMAT][U][V]; };
 
 template <int NW, int V, int U, int NOPS, int NMAT, int NG, int FMT, bool VEC, bool STAGED, int SIG>
-__global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, V, NMAT, FMT, VEC>()))
+__global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, V, NMAT, FMT, VEC, U>()))
     matprog_kernel(const __grid_constant__ MatProg P) {
   constexpr int CH = FmtT<FMT>::CH;
   constexpr int BYTES = FmtT<FMT>::BYTES;
