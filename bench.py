@@ -22,6 +22,7 @@ bytes over ranks divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -249,6 +250,148 @@ class Suite:
 
 
 SEQS = ["bicgk", "gemver", "gesummv", "atax", "axpydot", "waxpby"]
+
+
+# ---------------------------------------------------------------- cuBLAS context
+
+class CublasChain:
+    """The paper's comparison system on this GPU: each canonical script as
+    the chain of cuBLAS calls a BLAS user writes (Section 5 compares the
+    fused kernels with such CUBLAS chains), called through ctypes on the
+    cuBLAS that torch loaded.  Context only, never part of the library.
+
+    A row-major m x n matrix with lda = n is cuBLAS's column-major n x m
+    matrix C = A^T, so A p is gemv(T) on C and A^T r is gemv(N) on C, and
+    B += u v^T is ger(v, u) on C.  Scalars live on the device (pointer mode
+    device), so no call waits for the host."""
+    OP_N, OP_T = 0, 1
+
+    def __init__(self, suite, st):
+        d = torch.device("cuda", torch.cuda.current_device())
+        torch.mv(torch.ones(2, 2, device=d), torch.ones(2, device=d))  # torch loads its cuBLAS
+        path = None
+        with open("/proc/self/maps") as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 6 and os.path.basename(parts[-1]).startswith("libcublas.so"):
+                    path = parts[-1]
+                    break
+        self.library = os.path.basename(path) if path else "libcublas.so"
+        lib = ctypes.CDLL(path or "libcublas.so")
+        P, I = ctypes.c_void_p, ctypes.c_int
+
+        def fn(name, *argtypes):
+            f = getattr(lib, name)
+            f.argtypes = list(argtypes)
+            f.restype = ctypes.c_int
+            return f
+
+        self._create = fn("cublasCreate_v2", ctypes.POINTER(P))
+        self._destroy = fn("cublasDestroy_v2", P)
+        self._stream = fn("cublasSetStream_v2", P, P)
+        self._pmode = fn("cublasSetPointerMode_v2", P, I)
+        self._gemv = fn("cublasSgemv_v2", P, I, I, I, P, P, I, P, I, P, P, I)
+        self._ger = fn("cublasSger_v2", P, I, I, P, P, I, P, I, P, I)
+        self._copy = fn("cublasScopy_v2", P, I, P, I, P, I)
+        self._axpy = fn("cublasSaxpy_v2", P, I, P, P, I, P, I)
+        self._scal = fn("cublasSscal_v2", P, I, P, P, I)
+        self._dot = fn("cublasSdot_v2", P, I, P, I, P, I, P)
+        self.h = P()
+        self._ok(self._create(ctypes.byref(self.h)), "cublasCreate")
+        self._ok(self._stream(self.h, P(st.cuda_stream)), "cublasSetStream")
+        self._ok(self._pmode(self.h, 1), "cublasSetPointerMode")
+        self.sc = torch.tensor([1.0, 0.0, ALPHA, BETA, -ALPHA], device=d)
+        self.suite = suite
+        self.out = {}
+        for seq in SEQS:
+            if hasattr(suite, seq):
+                self.out[seq] = [torch.empty_like(t) for t in suite.outputs(seq)]
+        self.tmp = {seq: torch.empty_like(getattr(suite, seq)["t"]) for seq in ("atax",) if hasattr(suite, seq)}
+
+    @staticmethod
+    def _ok(rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} returned cuBLAS status {rc}")
+
+    def _s(self, i):
+        return self.sc.data_ptr() + 4 * i
+
+    def run(self, seq):
+        """Issue the chain of `seq` on the handle's stream."""
+        one, zero, al, be, nal = (self._s(i) for i in range(5))
+        b = getattr(self.suite, seq)
+        o = [t.data_ptr() for t in self.out[seq]]
+        h, ok = self.h, self._ok
+        if seq == "bicgk":
+            m, n = b["A"].shape
+            ok(self._gemv(h, self.OP_T, n, m, one, b["A"].data_ptr(), n, b["p"].data_ptr(), 1, zero, o[0], 1), "gemv")
+            ok(self._gemv(h, self.OP_N, n, m, one, b["A"].data_ptr(), n, b["r"].data_ptr(), 1, zero, o[1], 1), "gemv")
+        elif seq == "gemver":
+            n = b["A"].shape[0]
+            B, x, w = o
+            ok(self._copy(h, n * n, b["A"].data_ptr(), 1, B, 1), "copy")
+            ok(self._ger(h, n, n, one, b["v1"].data_ptr(), 1, b["u1"].data_ptr(), 1, B, n), "ger")
+            ok(self._ger(h, n, n, one, b["v2"].data_ptr(), 1, b["u2"].data_ptr(), 1, B, n), "ger")
+            ok(self._copy(h, n, b["z"].data_ptr(), 1, x, 1), "copy")
+            ok(self._gemv(h, self.OP_N, n, n, be, B, n, b["y"].data_ptr(), 1, one, x, 1), "gemv")
+            ok(self._gemv(h, self.OP_T, n, n, al, B, n, x, 1, zero, w, 1), "gemv")
+        elif seq == "gesummv":
+            n = b["A"].shape[0]
+            ok(self._gemv(h, self.OP_T, n, n, al, b["A"].data_ptr(), n, b["x"].data_ptr(), 1, zero, o[0], 1), "gemv")
+            ok(self._gemv(h, self.OP_T, n, n, be, b["B"].data_ptr(), n, b["x"].data_ptr(), 1, one, o[0], 1), "gemv")
+        elif seq == "atax":
+            m, n = b["A"].shape
+            t = self.tmp["atax"].data_ptr()
+            ok(self._gemv(h, self.OP_T, n, m, one, b["A"].data_ptr(), n, b["x"].data_ptr(), 1, zero, t, 1), "gemv")
+            ok(self._gemv(h, self.OP_N, n, m, one, b["A"].data_ptr(), n, t, 1, zero, o[0], 1), "gemv")
+        elif seq == "axpydot":
+            n = b["w"].numel()
+            z, r = o
+            ok(self._copy(h, n, b["w"].data_ptr(), 1, z, 1), "copy")
+            ok(self._axpy(h, n, nal, b["v"].data_ptr(), 1, z, 1), "axpy")
+            ok(self._dot(h, n, z, 1, b["u"].data_ptr(), 1, r), "dot")
+        elif seq == "waxpby":
+            n = b["x"].numel()
+            w = o[0]
+            ok(self._copy(h, n, b["y"].data_ptr(), 1, w, 1), "copy")
+            ok(self._scal(h, n, be, w, 1), "scal")
+            ok(self._axpy(h, n, al, b["x"].data_ptr(), 1, w, 1), "axpy")
+
+    def outputs(self, seq):
+        return self.out[seq]
+
+    def close(self):
+        if self.h:
+            self._destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+
+CUBLAS_CALLS = dict(bicgk="gemv(T), gemv(N)", gemver="copy, ger, ger, copy, gemv(N), gemv(T)",
+                    gesummv="gemv(T), gemv(T)", atax="gemv(T), gemv(N)", axpydot="copy, axpy, dot",
+                    waxpby="copy, scal, axpy")
+
+
+def cublas_section(suite, st, steps, warmup, seqs, fused_ms):
+    """Each sequence as a cuBLAS chain on the same inputs and GPU: mean ms
+    (back-to-back calls between one event pair), the fused kernel's speedup
+    over it, and how far its results are from the fused ones (normwise)."""
+    try:
+        cb = CublasChain(suite, st)
+    except (OSError, AttributeError, RuntimeError) as e:
+        return {"unavailable": f"cuBLAS not callable here: {e}"}
+    out = {"library": cb.library, "note": "context: the paper's comparison system (CUBLAS chains) on this GPU"}
+    try:
+        for seq in seqs:
+            ms = time_calls(lambda _st, q=seq: cb.run(q), steps, warmup, st)
+            torch.cuda.synchronize()
+            suite.fused(seq, st)
+            torch.cuda.synchronize()
+            diff = max(rel_diff(a, b) for a, b in zip(cb.outputs(seq), suite.outputs(seq)))
+            out[seq] = {"calls": CUBLAS_CALLS[seq], "ms": ms, "gbs_algorithmic": algorithmic_bytes(seq, suite.sizes[seq]) / (ms * 1e-3) / 1e9,
+                        "fused_speedup": ms / fused_ms[seq], "max_rel_diff_vs_fused": diff}
+    finally:
+        cb.close()
+    return out
 
 
 # ---------------------------------------------------------------- helpers
@@ -694,6 +837,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--no-cublas", action="store_true", help="skip the cuBLAS-chain context section")
     ap.add_argument("--seqs", default=",".join(SEQS), help="comma-separated subset of the suite")
     ap.add_argument("--bicgk", type=int, default=0, help="square BiCGK size override (profiling)")
     ap.add_argument("--mat-tuning", default="", help="warps,vec,unroll,groups,stages for matrix passes")
@@ -767,6 +911,8 @@ def main():
         unf_total, unf_per = time_suite(suite, "unfused", args.steps, args.warmup, st, seqs)
 
     extra = {}
+    if not args.no_cublas:
+        extra["cublas_chain"] = cublas_section(suite, st, args.steps, args.warmup, seqs, per)
     if not args.small and args.bicgk == 0 and seqs == SEQS:
         del suite
         torch.cuda.empty_cache()
