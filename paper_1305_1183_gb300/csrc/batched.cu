@@ -7,10 +7,11 @@
 // warps side by side; the block's 8 / cw warp rows take turns over the
 // band's 32-row blocks, so narrow matrices do not leave warps on masked
 // columns.  Blocks pull tiles from an atomic queue; in a tile, row dots are
-// kept as per-lane partials of 8 rows, reduced across the cw warps of a warp
-// row (a named barrier per warp row), and column sums are added across the
-// warp rows in row order at the end of the tile; the tile writes its
-// instance's row partial (per strip) and column partial (per band).  The
+// kept as per-lane partials of 8 rows and written out per warp (one partial
+// per 128 columns, so the warps of a warp row never wait for each other), and
+// column sums are added across the warp rows in row order at the end of the
+// tile; the tile writes its instance's row partials (per 128 columns) and
+// column partial (per band).  The
 // last tile of an instance to finish (a per-instance counter) adds the
 // partials in strip / band order and writes the outputs (Section 3.2.2,
 // option (ii)), so each instance's result does not depend on which block ran
@@ -128,7 +129,6 @@ __global__ void __launch_bounds__(BNW * 32, 3)
   __shared__ int s_last;
   // the current and the next tile's record, read field by field (keeps registers free)
   __shared__ BRec s_rec[2];
-  __shared__ float red[2][NR][BNW][32];
   __shared__ float csum[KIND == 0 ? BNW : 1][128];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -162,17 +162,14 @@ __global__ void __launch_bounds__(BNW * 32, 3)
       acc[e] = 0.f;
     }
     const int64_t nblk = (r1 - r0 + 31) >> 5;
-    const int64_t iters = (nblk + rw - 1) / rw;  // the same for every warp (barriers below)
-    for (int64_t it = 0; it < iters; ++it) {
-      const int64_t k = it * rw + wrow;
-      const bool blk_ok = k < nblk;  // warp-uniform
+    for (int64_t k = wrow; k < nblk; k += rw) {  // this warp row's 32-row blocks
       const int64_t row0 = r0 + k * 32;
-      const bool lane_ok = blk_ok && row0 + lane < r1;
+      const bool lane_ok = row0 + lane < r1;
       const float rv = (KIND == 0 && lane_ok) ? __ldg(d.r + row0 + lane) : 0.f;
       float rowdot[NR];
 #pragma unroll
       for (int g = 0; g < NR; ++g) rowdot[g] = 0.f;
-      if (blk_ok) {
+      {
 #pragma unroll 1
         for (int h = 0; h < 4; ++h) {
           float dacc[NR][8];
@@ -220,23 +217,13 @@ __global__ void __launch_bounds__(BNW * 32, 3)
           }
         }
       }
-      // row dots across the cw warps of this warp row, in fixed warp order
-      if (cw == 1) {
-        if (lane_ok)
+      // each warp's row dots over its 128 columns go out as their own
+      // partial (no exchange between the warps of a warp row); the instance's
+      // last tile adds them in column order
+      if (lane_ok)
 #pragma unroll
-          for (int g = 0; g < NR; ++g)
-            rowpart[d.rowpart_off + ((int64_t)g * d.nstrips + rc.strip) * m + row0 + lane] = rowdot[g];
-      } else {
-        const int buf = (int)(it & 1);
-#pragma unroll
-        for (int g = 0; g < NR; ++g) red[buf][g][warp][lane] = rowdot[g];
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + wrow), "r"(cw * 32) : "memory");
-        if (wcol < NR && lane_ok) {
-          float sum = 0.f;
-          for (int w = 0; w < cw; ++w) sum += red[buf][wcol][wrow * cw + w][lane];
-          rowpart[d.rowpart_off + ((int64_t)wcol * d.nstrips + rc.strip) * m + row0 + lane] = sum;
-        }
-      }
+        for (int g = 0; g < NR; ++g)
+          rowpart[d.rowpart_off + (((int64_t)g * d.nstrips + rc.strip) * cw + wcol) * m + row0 + lane] = rowdot[g];
     }
     if (KIND == 0) {
       // column sums of the strip: the rw warp rows added in row order
@@ -278,7 +265,7 @@ __global__ void __launch_bounds__(BNW * 32, 3)
         float v[NR];
 #pragma unroll
         for (int g = 0; g < NR; ++g)
-          v[g] = ordered_sum(rowpart + d.rowpart_off + (int64_t)g * d.nstrips * m + i, m, d.nstrips);
+          v[g] = ordered_sum(rowpart + d.rowpart_off + (int64_t)g * d.nstrips * d.cw * m + i, m, d.nstrips * d.cw);
         if (KIND == 0) d.y[i] = v[0];
         else d.y[i] = __fadd_rn(__fmul_rn(d.alpha, v[0]), __fmul_rn(d.beta, v[NR - 1]));
       }
@@ -363,7 +350,7 @@ kf_status kf_batched_create(kf_seq seq, const kf_batch_desc* descs, int count, i
     d.ntiles = d.nstrips * d.nbands;
     d.rowpart_off = b->rowpart_floats;
     d.colpart_off = b->colpart_floats;
-    b->rowpart_floats += (int64_t)nr * d.nstrips * u.m;
+    b->rowpart_floats += (int64_t)nr * d.nstrips * d.cw * u.m;
     if (b->kind == 0) b->colpart_floats += (int64_t)d.nbands * u.n;
     b->desc.push_back(d);
     for (int bd = 0; bd < d.nbands; ++bd)
