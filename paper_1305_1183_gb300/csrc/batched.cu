@@ -7,21 +7,15 @@
 // warps side by side; the block's 8 / cw warp rows take turns over the
 // band's 32-row blocks, so narrow matrices do not leave warps on masked
 // columns.  Blocks pull tiles from an atomic queue; in a tile, row dots are
-// kept as per-lane partials of 8 rows and written out per warp (one partial
-// per 128 columns, so the warps of a warp row never wait for each other), and
-// column sums are added across the warp rows in row order at the end of the
-// tile; the tile writes its instance's row partials (per 128 columns) and
-// column partial (per band).  The
+// kept as per-lane partials of 8 rows, reduced across the cw warps of a warp
+// row (a named barrier per warp row), and column sums are added across the
+// warp rows in row order at the end of the tile; the tile writes its
+// instance's row partial (per strip) and column partial (per band).  The
 // last tile of an instance to finish (a per-instance counter) adds the
 // partials in strip / band order and writes the outputs (Section 3.2.2,
 // option (ii)), so each instance's result does not depend on which block ran
 // which tile, and equals the same instance run alone.  The queue and the
 // counters reset themselves, so the launch can be replayed from a CUDA graph.
-//
-// A tile's record carries its instance's descriptor (one 128-byte read per
-// tile), and a block reserves its next tile while the current one streams:
-// between two tiles a block waits for one instance-counter atomic and one
-// record read, not for a chain of queue atomic, tile read and descriptor read.
 //
 // Loads are element-interleaved (lane l of a warp reads columns l, l+32,
 // l+64, l+96 of its 128-column slice), so every load instruction covers 128
@@ -61,41 +55,7 @@ struct BTile {
   int inst, band, strip, pad;
 };
 
-// One tile as the kernel reads it: the instance's descriptor and the tile.
-struct alignas(16) BRec {
-  BDesc d;
-  int inst, band, strip, pad;
-};
-static_assert(sizeof(BDesc) == 112 && sizeof(BRec) == 128, "record layout");
-
 constexpr int BNW = 8;             // warps per block (side by side)
-
-// Copy one 128-byte tile record into shared memory (one thread, eight
-// independent 16-byte loads).
-__device__ __forceinline__ void copy_rec(BRec* dst, const BRec* src) {
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  float4* d4 = reinterpret_cast<float4*>(dst);
-  float4 v[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __ldcg(s4 + i);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) d4[i] = v[i];
-}
-
-// p[0] + p[stride] + ... + p[(cnt - 1) stride], added left to right; the
-// loads are issued eight at a time ahead of the adds.
-__device__ __forceinline__ float ordered_sum(const float* p, int64_t stride, int cnt) {
-  float sum = 0.f;
-  for (int k0 = 0; k0 < cnt; k0 += 8) {
-    float v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = k0 + k < cnt ? __ldcg(p + (int64_t)(k0 + k) * stride) : 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (k0 + k < cnt) sum += v[k];
-  }
-  return sum;
-}
 
 __device__ __forceinline__ float reduce8(float (&d)[8], int lane) {
 #pragma unroll
@@ -120,39 +80,39 @@ __device__ __forceinline__ float reduce8(float (&d)[8], int lane) {
 // rows taking turns over the band's 32-row blocks; 3 blocks per SM.
 template <int KIND>
 __global__ void __launch_bounds__(BNW * 32, 3)
-    batched_kernel(const BRec* __restrict__ R, int ntiles, int band_rows, float* __restrict__ rowpart,
-                   float* __restrict__ colpart, unsigned* __restrict__ inst_count, unsigned* __restrict__ queue) {
+    batched_kernel(const BDesc* __restrict__ D, const BTile* __restrict__ T, int ntiles, int band_rows,
+                   float* __restrict__ rowpart, float* __restrict__ colpart, unsigned* __restrict__ inst_count,
+                   unsigned* __restrict__ queue) {
   constexpr int NM = KIND == 0 ? 1 : 2;   // matrices
   constexpr int NR = KIND == 0 ? 1 : 2;   // row results
   constexpr int BU = KIND == 0 ? 8 : 4;   // rows loaded together (the same bytes in flight for one matrix as for two)
-  __shared__ int s_next;
+  __shared__ int s_tile;
   __shared__ int s_last;
-  // the current and the next tile's record, read field by field (keeps registers free)
-  __shared__ BRec s_rec[2];
+  __shared__ BDesc s_desc;  // the tile's instance, read field by field (keeps registers free)
+  __shared__ float red[2][NR][BNW][32];
   __shared__ float csum[KIND == 0 ? BNW : 1][128];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  if (threadIdx.x == 0) {
-    const int tt = (int)atomicAdd(&queue[0], 1u);
-    s_next = tt;
-    if (tt < ntiles) copy_rec(&s_rec[0], R + tt);
-  }
-  __syncthreads();
-  int buf = 0;
-  for (int t = s_next; t < ntiles; buf ^= 1) {
-    // reserve the tile after this one now; its number is read when this one ends
-    unsigned nxt = 0u;
-    if (threadIdx.x == 0) nxt = atomicAdd(&queue[0], 1u);
-    const BRec& rc = s_rec[buf];
-    const BDesc& d = rc.d;
+  for (;;) {
+    __syncthreads();  // previous tile's shared-memory use is over
+    if (threadIdx.x == 0) {
+      const int tt = (int)atomicAdd(&queue[0], 1u);
+      s_tile = tt;
+      if (tt < ntiles) s_desc = D[T[tt].inst];
+    }
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const BTile tl = T[t];
+    const BDesc& d = s_desc;
     const int64_t m = d.m, n = d.n;
     // cw warps side by side cover the strip (cw * 128 columns); the block's
     // rw = 8 / cw warp rows take turns over the band's 32-row blocks
     const int cw = d.cw, rw = BNW / cw;
     const int wcol = warp % cw, wrow = warp / cw;
-    const int64_t r0 = (int64_t)rc.band * band_rows;
+    const int64_t r0 = (int64_t)tl.band * band_rows;
     const int64_t r1 = min(m, r0 + band_rows);
-    const int64_t wc = (int64_t)rc.strip * cw * 128 + wcol * 128;  // this warp's slice
+    const int64_t wc = (int64_t)tl.strip * cw * 128 + wcol * 128;  // this warp's slice
 
     float xv[4], acc[4];
 #pragma unroll
@@ -162,14 +122,17 @@ __global__ void __launch_bounds__(BNW * 32, 3)
       acc[e] = 0.f;
     }
     const int64_t nblk = (r1 - r0 + 31) >> 5;
-    for (int64_t k = wrow; k < nblk; k += rw) {  // this warp row's 32-row blocks
+    const int64_t iters = (nblk + rw - 1) / rw;  // the same for every warp (barriers below)
+    for (int64_t it = 0; it < iters; ++it) {
+      const int64_t k = it * rw + wrow;
+      const bool blk_ok = k < nblk;  // warp-uniform
       const int64_t row0 = r0 + k * 32;
-      const bool lane_ok = row0 + lane < r1;
+      const bool lane_ok = blk_ok && row0 + lane < r1;
       const float rv = (KIND == 0 && lane_ok) ? __ldg(d.r + row0 + lane) : 0.f;
       float rowdot[NR];
 #pragma unroll
       for (int g = 0; g < NR; ++g) rowdot[g] = 0.f;
-      {
+      if (blk_ok) {
 #pragma unroll 1
         for (int h = 0; h < 4; ++h) {
           float dacc[NR][8];
@@ -217,13 +180,23 @@ __global__ void __launch_bounds__(BNW * 32, 3)
           }
         }
       }
-      // each warp's row dots over its 128 columns go out as their own
-      // partial (no exchange between the warps of a warp row); the instance's
-      // last tile adds them in column order
-      if (lane_ok)
+      // row dots across the cw warps of this warp row, in fixed warp order
+      if (cw == 1) {
+        if (lane_ok)
 #pragma unroll
-        for (int g = 0; g < NR; ++g)
-          rowpart[d.rowpart_off + (((int64_t)g * d.nstrips + rc.strip) * cw + wcol) * m + row0 + lane] = rowdot[g];
+          for (int g = 0; g < NR; ++g)
+            rowpart[d.rowpart_off + ((int64_t)g * d.nstrips + tl.strip) * m + row0 + lane] = rowdot[g];
+      } else {
+        const int buf = (int)(it & 1);
+#pragma unroll
+        for (int g = 0; g < NR; ++g) red[buf][g][warp][lane] = rowdot[g];
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + wrow), "r"(cw * 32) : "memory");
+        if (wcol < NR && lane_ok) {
+          float sum = 0.f;
+          for (int w = 0; w < cw; ++w) sum += red[buf][wcol][wrow * cw + w][lane];
+          rowpart[d.rowpart_off + ((int64_t)wcol * d.nstrips + tl.strip) * m + row0 + lane] = sum;
+        }
+      }
     }
     if (KIND == 0) {
       // column sums of the strip: the rw warp rows added in row order
@@ -231,7 +204,7 @@ __global__ void __launch_bounds__(BNW * 32, 3)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int64_t c = wc + e * 32 + lane;
-          if (c < n) colpart[d.colpart_off + (int64_t)rc.band * n + c] = acc[e];
+          if (c < n) colpart[d.colpart_off + (int64_t)tl.band * n + c] = acc[e];
         }
       } else {
 #pragma unroll
@@ -243,39 +216,39 @@ __global__ void __launch_bounds__(BNW * 32, 3)
             float sum = 0.f;
             for (int q = 0; q < rw; ++q) sum += csum[q * cw + wcol][e * 32 + lane];
             const int64_t c = wc + e * 32 + lane;
-            if (c < n) colpart[d.colpart_off + (int64_t)rc.band * n + c] = sum;
+            if (c < n) colpart[d.colpart_off + (int64_t)tl.band * n + c] = sum;
           }
         }
       }
     }
-    // last tile of the instance finishes it; the next tile's record is read
-    // meanwhile into the other buffer (its last reader, the tile before this
-    // one, is past the barrier below)
+    // last tile of the instance finishes it
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-      s_last = atomicAdd(&inst_count[rc.inst], 1u) == (unsigned)d.ntiles - 1u;
-      s_next = (int)nxt;
-      if ((int)nxt < ntiles) copy_rec(&s_rec[buf ^ 1], R + nxt);
-    }
+    if (threadIdx.x == 0) s_last = atomicAdd(&inst_count[tl.inst], 1u) == (unsigned)d.ntiles - 1u;
     __syncthreads();
     if (s_last) {
       __threadfence();
       for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
         float v[NR];
 #pragma unroll
-        for (int g = 0; g < NR; ++g)
-          v[g] = ordered_sum(rowpart + d.rowpart_off + (int64_t)g * d.nstrips * d.cw * m + i, m, d.nstrips * d.cw);
+        for (int g = 0; g < NR; ++g) {
+          float sum = 0.f;
+          for (int st = 0; st < d.nstrips; ++st)
+            sum += __ldcg(rowpart + d.rowpart_off + ((int64_t)g * d.nstrips + st) * m + i);
+          v[g] = sum;
+        }
         if (KIND == 0) d.y[i] = v[0];
         else d.y[i] = __fadd_rn(__fmul_rn(d.alpha, v[0]), __fmul_rn(d.beta, v[NR - 1]));
       }
       if (KIND == 0) {
-        for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
-          d.s[j] = ordered_sum(colpart + d.colpart_off + j, n, d.nbands);
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+          float sum = 0.f;
+          for (int bnd = 0; bnd < d.nbands; ++bnd) sum += __ldcg(colpart + d.colpart_off + (int64_t)bnd * n + j);
+          d.s[j] = sum;
+        }
       }
-      if (threadIdx.x == 0) inst_count[rc.inst] = 0u;
+      if (threadIdx.x == 0) inst_count[tl.inst] = 0u;
     }
-    t = s_next;
   }
   // the last block out resets the queue for the next launch
   if (threadIdx.x == 0) {
@@ -299,9 +272,8 @@ struct kf_batched {
   int band_rows = 128;
   std::vector<kf::BDesc> desc;
   std::vector<kf::BTile> tiles;
-  std::vector<kf::BRec> recs;  // tiles in queue order with their descriptors (what the kernel reads)
   int64_t rowpart_floats = 0, colpart_floats = 0;
-  size_t off_queue = 0, off_counts = 0, off_recs = 0, off_row = 0, off_col = 0, total = 0;
+  size_t off_queue = 0, off_counts = 0, off_desc = 0, off_tiles = 0, off_row = 0, off_col = 0, total = 0;
   double bytes = 0.0;  // algorithmic bytes of one launch
 };
 
@@ -350,7 +322,7 @@ kf_status kf_batched_create(kf_seq seq, const kf_batch_desc* descs, int count, i
     d.ntiles = d.nstrips * d.nbands;
     d.rowpart_off = b->rowpart_floats;
     d.colpart_off = b->colpart_floats;
-    b->rowpart_floats += (int64_t)nr * d.nstrips * d.cw * u.m;
+    b->rowpart_floats += (int64_t)nr * d.nstrips * u.m;
     if (b->kind == 0) b->colpart_floats += (int64_t)d.nbands * u.n;
     b->desc.push_back(d);
     for (int bd = 0; bd < d.nbands; ++bd)
@@ -366,12 +338,11 @@ kf_status kf_batched_create(kf_seq seq, const kf_batch_desc* descs, int count, i
     return rows * cols;
   };
   std::stable_sort(b->tiles.begin(), b->tiles.end(), [&](const BTile& x, const BTile& y) { return tsize(x) > tsize(y); });
-  b->recs.reserve(b->tiles.size());
-  for (const BTile& t : b->tiles) b->recs.push_back(BRec{b->desc[t.inst], t.inst, t.band, t.strip, 0});
   size_t o = WS_HEADER;
   b->off_queue = o; o += 256;
   b->off_counts = o; o += a256((size_t)count * 4);
-  b->off_recs = o; o += a256(b->recs.size() * sizeof(BRec));
+  b->off_desc = o; o += a256(b->desc.size() * sizeof(BDesc));
+  b->off_tiles = o; o += a256(b->tiles.size() * sizeof(BTile));
   b->off_row = o; o += a256((size_t)b->rowpart_floats * 4);
   b->off_col = o; o += a256((size_t)b->colpart_floats * 4);
   b->total = o;
@@ -401,9 +372,11 @@ kf_status kf_batched_upload(const kf_batched* b, void* ws, size_t ws_bytes, void
   }
   char* w = static_cast<char*>(ws);
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemsetAsync(w, 0, b->off_recs, st);  // header, queue, instance counters
-  if (e == cudaSuccess && !b->recs.empty())
-    e = cudaMemcpyAsync(w + b->off_recs, b->recs.data(), b->recs.size() * sizeof(BRec), cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemsetAsync(w, 0, b->off_desc, st);  // header, queue, instance counters
+  if (e == cudaSuccess && !b->desc.empty())
+    e = cudaMemcpyAsync(w + b->off_desc, b->desc.data(), b->desc.size() * sizeof(BDesc), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !b->tiles.empty())
+    e = cudaMemcpyAsync(w + b->off_tiles, b->tiles.data(), b->tiles.size() * sizeof(BTile), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables may change after return
   if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return KF_ERR_CUDA; }
   return KF_OK;
@@ -424,14 +397,15 @@ kf_status kf_batched_launch(const kf_batched* b, void* ws, size_t ws_bytes, void
     occ[b->kind] = o;
   }
   const int grid = (int)std::min<int64_t>((int64_t)device_sm_count() * occ[b->kind], (int64_t)b->tiles.size());
-  const BRec* R = reinterpret_cast<const BRec*>(w + b->off_recs);
+  const BDesc* D = reinterpret_cast<const BDesc*>(w + b->off_desc);
+  const BTile* T = reinterpret_cast<const BTile*>(w + b->off_tiles);
   int nt = (int)b->tiles.size();
   int br = b->band_rows;
   float* rp = reinterpret_cast<float*>(w + b->off_row);
   float* cp = reinterpret_cast<float*>(w + b->off_col);
   unsigned* cnt = reinterpret_cast<unsigned*>(w + b->off_counts);
   unsigned* q = reinterpret_cast<unsigned*>(w + b->off_queue);
-  void* args[] = {(void*)&R, (void*)&nt, (void*)&br, (void*)&rp, (void*)&cp, (void*)&cnt, (void*)&q};
+  void* args[] = {(void*)&D, (void*)&T, (void*)&nt, (void*)&br, (void*)&rp, (void*)&cp, (void*)&cnt, (void*)&q};
   cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(BNW * 32), args, 0, (cudaStream_t)stream);
   if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return KF_ERR_CUDA; }
   return KF_OK;
