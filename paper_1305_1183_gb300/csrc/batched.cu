@@ -57,6 +57,22 @@ struct BTile {
 
 constexpr int BNW = 8;             // warps per block (side by side)
 
+// p[0] + p[stride] + ... + p[(cnt - 1) stride], added left to right; the
+// loads are issued eight at a time ahead of the adds (the column sums over
+// up to 64 bands; the row sums over one or two strips keep a plain loop).
+__device__ __forceinline__ float ordered_sum(const float* p, int64_t stride, int cnt) {
+  float sum = 0.f;
+  for (int k0 = 0; k0 < cnt; k0 += 8) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = k0 + k < cnt ? __ldcg(p + (int64_t)(k0 + k) * stride) : 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k0 + k < cnt) sum += v[k];
+  }
+  return sum;
+}
+
 __device__ __forceinline__ float reduce8(float (&d)[8], int lane) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) d[i] += __shfl_xor_sync(FULL_MASK, d[i], 16);
@@ -241,11 +257,8 @@ __global__ void __launch_bounds__(BNW * 32, 3)
         else d.y[i] = __fadd_rn(__fmul_rn(d.alpha, v[0]), __fmul_rn(d.beta, v[NR - 1]));
       }
       if (KIND == 0) {
-        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-          float sum = 0.f;
-          for (int bnd = 0; bnd < d.nbands; ++bnd) sum += __ldcg(colpart + d.colpart_off + (int64_t)bnd * n + j);
-          d.s[j] = sum;
-        }
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+          d.s[j] = ordered_sum(colpart + d.colpart_off + j, n, d.nbands);
       }
       if (threadIdx.x == 0) inst_count[tl.inst] = 0u;
     }
