@@ -244,17 +244,36 @@ __global__ void __launch_bounds__(BNW * 32, 3)
     __syncthreads();
     if (s_last) {
       __threadfence();
-      for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-        float v[NR];
+      // four rows per thread at a time (their strip partials load together),
+      // each row's partials added in strip order
+      for (int64_t i0 = threadIdx.x; i0 < m; i0 += 4 * (int64_t)blockDim.x) {
+        float v[4][NR];
 #pragma unroll
-        for (int g = 0; g < NR; ++g) {
-          float sum = 0.f;
-          for (int st = 0; st < d.nstrips; ++st)
-            sum += __ldcg(rowpart + d.rowpart_off + ((int64_t)g * d.nstrips + st) * m + i);
-          v[g] = sum;
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int g = 0; g < NR; ++g) v[q][g] = 0.f;
+        for (int st = 0; st < d.nstrips; ++st) {
+          float x[4][NR];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t i = i0 + q * (int64_t)blockDim.x;
+#pragma unroll
+            for (int g = 0; g < NR; ++g)
+              x[q][g] = i < m ? __ldcg(rowpart + d.rowpart_off + ((int64_t)g * d.nstrips + st) * m + i) : 0.f;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int g = 0; g < NR; ++g) v[q][g] += x[q][g];
         }
-        if (KIND == 0) d.y[i] = v[0];
-        else d.y[i] = __fadd_rn(__fmul_rn(d.alpha, v[0]), __fmul_rn(d.beta, v[NR - 1]));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t i = i0 + q * (int64_t)blockDim.x;
+          if (i < m) {
+            if (KIND == 0) d.y[i] = v[q][0];
+            else d.y[i] = __fadd_rn(__fmul_rn(d.alpha, v[q][0]), __fmul_rn(d.beta, v[q][NR - 1]));
+          }
+        }
       }
       if (KIND == 0) {
         for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
