@@ -57,22 +57,6 @@ struct BTile {
 
 constexpr int BNW = 8;             // warps per block (side by side)
 
-// p[0] + p[stride] + ... + p[(cnt - 1) stride], added left to right; the
-// loads are issued eight at a time ahead of the adds (the column sums over
-// up to 64 bands; the row sums over one or two strips keep a plain loop).
-__device__ __forceinline__ float ordered_sum(const float* p, int64_t stride, int cnt) {
-  float sum = 0.f;
-  for (int k0 = 0; k0 < cnt; k0 += 8) {
-    float v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = k0 + k < cnt ? __ldcg(p + (int64_t)(k0 + k) * stride) : 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (k0 + k < cnt) sum += v[k];
-  }
-  return sum;
-}
-
 __device__ __forceinline__ float reduce8(float (&d)[8], int lane) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) d[i] += __shfl_xor_sync(FULL_MASK, d[i], 16);
@@ -276,8 +260,30 @@ __global__ void __launch_bounds__(BNW * 32, 3)
         }
       }
       if (KIND == 0) {
-        for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
-          d.s[j] = ordered_sum(colpart + d.colpart_off + j, n, d.nbands);
+        // two columns per thread at a time, each column's band partials
+        // loaded eight at a time and added in band order
+        for (int64_t j = threadIdx.x; j < n; j += 2 * (int64_t)blockDim.x) {
+          const int64_t j2 = j + blockDim.x;
+          const float* p0 = colpart + d.colpart_off + j;
+          float s0 = 0.f, s1 = 0.f;
+          for (int k0 = 0; k0 < d.nbands; k0 += 8) {
+            float v0[8], v1[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const bool ok = k0 + k < d.nbands;
+              v0[k] = ok ? __ldcg(p0 + (int64_t)(k0 + k) * n) : 0.f;
+              v1[k] = ok && j2 < n ? __ldcg(p0 + (int64_t)(k0 + k) * n + blockDim.x) : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (k0 + k < d.nbands) {
+                s0 += v0[k];
+                s1 += v1[k];
+              }
+          }
+          d.s[j] = s0;
+          if (j2 < n) d.s[j2] = s1;
+        }
       }
       if (threadIdx.x == 0) inst_count[tl.inst] = 0u;
     }
