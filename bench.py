@@ -10,8 +10,10 @@ Reported value: algorithmic bytes of the suite (bytes each sequence must move
 at least once: matrices read/written once, vectors once) / device time, in
 GB/s.  Beside it: per-sequence GB/s and fraction of the measured HBM copy
 bandwidth, the unfused per-call kernel chain on the same GPU and its speedup,
-the dominant kernel's roofline, an end-to-end number through host buffers,
-and the FP64 CPU oracle's throughput on a bounded sample.
+the same sequences as cuBLAS call chains (context: the paper's comparison
+system), the dominant kernel's roofline, an end-to-end number through host
+buffers, the row-scaled BF16 / E4M3 forms, the batched form, and the FP64
+CPU oracle's throughput on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU runs (torchrun) are independent replicas: the suite does not shard
