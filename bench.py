@@ -850,6 +850,8 @@ def main():
     ap.add_argument("--only", default="", choices=["", "batched", "precision"],
                     help="run only this section and print its JSON (profiling)")
     ap.add_argument("--batched-count", type=int, default=4096, help="instances per batched launch")
+    ap.add_argument("--precision-n", type=int, default=16384,
+                    help="matrix order of the precision section when run alone with --only precision (profiling)")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
 
@@ -888,7 +890,7 @@ def main():
         d = torch.device("cuda", local)
         st = torch.cuda.Stream()
         sec = (batched_section(kf, d, st, args.steps, args.warmup, count=args.batched_count)
-               if args.only == "batched" else precision_section(kf, d, st, args.steps, args.warmup))
+               if args.only == "batched" else precision_section(kf, d, st, args.steps, args.warmup, n=args.precision_n))
         if rank == 0:
             print(json.dumps({args.only: sec}), flush=True)
         return
