@@ -234,10 +234,26 @@ __device__ __forceinline__ void quant_store_row(void* B, int64_t ldb, int64_t ro
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     uint32_t code[CH];
+    if constexpr (FMT == FMT_E4M3) {
+      // two values per conversion each way (the paired E4M3 forms round
+      // each element exactly as the single ones do)
 #pragma unroll
-    for (int e = 0; e < CH; ++e) {
-      code[e] = encode1<FMT>(__fmul_rn(a[v * CH + e], isB));
-      a[v * CH + e] = __fmul_rn(sB, decode1<FMT>(code[e]));
+      for (int e = 0; e < CH; e += 2) {
+        const float2 t = make_float2(__fmul_rn(a[v * CH + e], isB), __fmul_rn(a[v * CH + e + 1], isB));
+        const uint32_t pr = (uint32_t)__nv_cvt_float2_to_fp8x2(t, __NV_SATFINITE, __NV_E4M3);
+        code[e] = pr & 0xFFu;
+        code[e + 1] = (pr >> 8) & 0xFFu;
+        float lo, hi;
+        e4m3x2_to_f32(pr, lo, hi);
+        a[v * CH + e] = __fmul_rn(sB, lo);
+        a[v * CH + e + 1] = __fmul_rn(sB, hi);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < CH; ++e) {
+        code[e] = encode1<FMT>(__fmul_rn(a[v * CH + e], isB));
+        a[v * CH + e] = __fmul_rn(sB, decode1<FMT>(code[e]));
+      }
     }
     if (!row_ok) continue;
     if constexpr (VEC) {
