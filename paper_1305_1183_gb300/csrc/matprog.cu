@@ -297,22 +297,20 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   if (occ < 1) { *why = "kernel does not fit on an SM with this tuning"; return -10; }
 
   // Geometry: strips by the instance's strip width, groups to fill one wave.
-  // A group takes whole 8-row units (32-row blocks would leave up to a
-  // quarter of the wave idle: 256 row blocks over 76 groups round to 4 each).
   const int64_t strips = P.n > 0 ? (P.n + sw - 1) / sw : 1;
-  const int64_t nr8 = (P.m + 7) / 8;
+  const int64_t nrb = (P.m + 31) / 32;
   const int64_t slots = (int64_t)device_sm_count() * occ;
   int64_t G;
   if (t.groups > 0) G = t.groups;
   else G = std::max<int64_t>(1, slots / std::max<int64_t>(1, strips));
-  G = std::min<int64_t>(G, std::max<int64_t>(1, nr8));
+  G = std::min<int64_t>(G, std::max<int64_t>(1, nrb));
   G = std::min<int64_t>(G, MAT_MAXGROUPS);
-  const int64_t upg = nr8 > 0 ? (nr8 + G - 1) / G : 0;  // 8-row units per group
-  G = nr8 > 0 ? (nr8 + upg - 1) / upg : 1;
+  int64_t bpg = nrb > 0 ? (nrb + G - 1) / G : 0;
+  G = nrb > 0 ? (nrb + bpg - 1) / bpg : 1;
   if (strips > 0x7fffffffLL) { *why = "matrix too wide"; return -2; }
   P.n_strips = (int)strips;
   P.n_groups = (int)G;
-  P.rows_per_group = 8 * upg;
+  P.blocks_per_group = bpg;
   P.stages = stages;
   dim3 grid((unsigned)strips, (unsigned)G);
   void* args[] = {&P};

@@ -433,15 +433,10 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   const int64_t wcol0 = col0 + (int64_t)min(warp, NW - 1) * SWW;
   const int nops = P.nops;
 
-  // The group's rows [r_lo, r_hi) are whole 8-row units; the block walks the
-  // 32-row blocks that overlap them and masks the rows outside (a 32-row
-  // block at a group boundary is shared, each group taking its own rows).
-  const int64_t r_lo = min(m, (int64_t)group * P.rows_per_group);
-  const int64_t r_hi = min(m, r_lo + P.rows_per_group);
-  const int64_t rb_begin = r_lo >> 5;
-  const int64_t rb_end = r_hi > r_lo ? (r_hi + 31) >> 5 : rb_begin;
-  const int64_t nbatch = (rb_end - rb_begin) * NB;
-  auto in_rows = [&](int64_t row) { return row >= r_lo && row < r_hi; };
+  const int64_t nrb = (m + 31) >> 5;
+  const int64_t rb_begin = (int64_t)group * P.blocks_per_group;
+  const int64_t rb_end = min(nrb, rb_begin + P.blocks_per_group);
+  const int64_t nbatch = (rb_end > rb_begin ? rb_end - rb_begin : 0) * NB;
 
   const int S = STAGED ? P.stages : 1;
   const bool ring = STAGED && (col0 + SW <= n);  // block-uniform
@@ -478,11 +473,11 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
         unsigned bytes = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (in_rows(rowb + u)) bytes += NMAT * SEG;
+          if (rowb + u < m) bytes += NMAT * SEG;
         mbar_expect_tx(&full[s], bytes);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          if (in_rows(rowb + u)) {
+          if (rowb + u < m) {
 #pragma unroll
             for (int t = 0; t < NMAT; ++t) {
               const char* src = static_cast<const char*>(P.A[t]) + ((rowb + u) * P.lda[t] + col0) * BYTES;
@@ -532,7 +527,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
         const char* stage = ringp + (size_t)s * BATCH + (size_t)warp * SEGW;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const bool row_ok = !dead && in_rows(row0 + r + u);
+          const bool row_ok = !dead && (row0 + r + u < m);
 #pragma unroll
           for (int t = 0; t < NMAT; ++t)
 #pragma unroll
@@ -559,8 +554,8 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
           const int64_t row = row0 + r + u;
 #pragma unroll
           for (int t = 0; t < NMAT; ++t) {
-            if constexpr (RAW) load_row_raw<FMT, V>(P.A[t], P.lda[t], row, in_rows(row), wcol0, n, lane, a[t][u]);
-            else load_row<FMT, V, VEC>(P.A[t], P.lda[t], row, in_rows(row), wcol0, n, lane, a[t][u]);
+            if constexpr (RAW) load_row_raw<FMT, V>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u]);
+            else load_row<FMT, V, VEC>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u]);
           }
         }
       }
@@ -569,7 +564,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
     int64_t j = 0;  // batch counter (every consumer warp visits every batch)
     for (int64_t rb = rb_begin; rb < rb_end; ++rb) {
       const int64_t row0 = rb << 5;
-      const bool lane_row_ok = in_rows(row0 + lane);
+      const bool lane_row_ok = row0 + lane < m;
       float rv[NOPS];  // per-lane row scalar (GER u, GEMVT y) for row row0+lane
 #pragma unroll
       for (int k = 0; k < NOPS; ++k) {
@@ -684,7 +679,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
                 if constexpr (QOUT) {
                   if (k == LASTGER) {
                     const int64_t row = row0 + rr;
-                    quant_store_row<FMT, V, VEC>(P.Bout[0], P.ldb[0], row, in_rows(row), wcol0, n, lane, ar[0],
+                    quant_store_row<FMT, V, VEC>(P.Bout[0], P.ldb[0], row, row < m, wcol0, n, lane, ar[0],
                                                  __shfl_sync(FULL_MASK, sbrow, rr),
                                                  __shfl_sync(FULL_MASK, isbrow, rr));
                   }
@@ -692,7 +687,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
               }
             }
             const int64_t row = row0 + rr;
-            if (!QOUT && in_rows(row)) {
+            if (!QOUT && row < m) {
 #pragma unroll
               for (int t = 0; t < NMAT; ++t)
                 if (P.Bout[t] != nullptr)
@@ -800,8 +795,8 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   if (s_last[1]) {
     __threadfence();
     // Row results of this group: sum the strips' partials in strip order.
-    const int64_t r0 = r_lo;
-    const int64_t r1 = r_hi;
+    const int64_t r0 = rb_begin << 5;
+    const int64_t r1 = min(m, rb_end << 5);
     const bool v4 = (m & 3) == 0;
     const int step = v4 ? 4 : 1;
     for (int64_t i = r0 + threadIdx.x * step; i < r1; i += (int64_t)blockDim.x * step) {
