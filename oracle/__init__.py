@@ -25,60 +25,75 @@ _SRC = os.path.join(_HERE, "kf_oracle.c")
 _lib = None
 
 
+SOURCE = _SRC
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile one oracle C source into a shared library (gcc, -O2, strict IEEE)."""
+    subprocess.run(
+        ["gcc", "-O2", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+         "-std=c11", "-o", out, src, "-lm"],
+        check=True,
+    )
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile kf_oracle.c into a shared library (gcc, -O2, strict IEEE)."""
+    """Compile kf_oracle.c into the package's shared library when it is stale."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.run(
-            ["gcc", "-O2", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
-             "-std=c11", "-o", tmp, _SRC, "-lm"],
-            check=True,
-        )
+        compile_source(_SRC, tmp)
         os.replace(tmp, _SO)
     return _SO
 
 
 def lib():
+    """The loaded oracle library (built on first use)."""
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_SO)
-        d = ctypes.POINTER(ctypes.c_double)
-        i64 = ctypes.c_int64
-        dbl = ctypes.c_double
-        vp = ctypes.c_void_p
-        fp = ctypes.POINTER(ctypes.c_float)
-        L.kfo_gemv.argtypes = [i64, i64, d, i64, d, dbl, dbl, d, d]
-        L.kfo_gemvt.argtypes = [i64, i64, d, i64, d, dbl, dbl, d, d]
-        L.kfo_ger.argtypes = [i64, i64, d, i64, dbl, d, d, d, i64]
-        L.kfo_madd.argtypes = [i64, i64, d, d, d]
-        L.kfo_axpby.argtypes = [i64, dbl, d, dbl, d, d]
-        L.kfo_vadd3.argtypes = [i64, d, d, d, d]
-        L.kfo_dot.argtypes = [i64, d, d]
-        L.kfo_dot.restype = dbl
-        L.kfo_bicgk.argtypes = [i64, i64, d, i64, d, d, d, d]
-        L.kfo_gemver.argtypes = [i64, d, i64, d, d, d, d, d, d, dbl, dbl, d, d, d]
-        L.kfo_gesummv.argtypes = [i64, i64, d, d, i64, d, dbl, dbl, d]
-        L.kfo_atax.argtypes = [i64, i64, d, i64, d, d, d]
-        L.kfo_axpydot.argtypes = [i64, d, d, d, dbl, d]
-        L.kfo_axpydot.restype = dbl
-        L.kfo_waxpby.argtypes = [i64, dbl, d, dbl, d, d]
-        L.kfo_abs_gemv.argtypes = [i64, i64, d, i64, d, d]
-        L.kfo_abs_gemvt.argtypes = [i64, i64, d, i64, d, d]
-        L.kfo_quantize_rows.argtypes = [i64, i64, fp, i64, ctypes.c_int, vp, fp]
-        L.kfo_dequantize_rows.argtypes = [i64, i64, vp, ctypes.c_int, fp, d]
-        L.kfo_gemver_rowscaled_store.argtypes = [i64, vp, ctypes.c_int, fp, fp, fp, fp, fp, vp, fp]
-        L.kfo_bf16_value.argtypes = [ctypes.c_uint16]
-        L.kfo_bf16_value.restype = dbl
-        L.kfo_e4m3_value.argtypes = [ctypes.c_uint8]
-        L.kfo_e4m3_value.restype = dbl
-        L.kfo_bf16_code.argtypes = [ctypes.c_float]
-        L.kfo_bf16_code.restype = ctypes.c_uint16
-        L.kfo_e4m3_code.argtypes = [ctypes.c_float]
-        L.kfo_e4m3_code.restype = ctypes.c_uint8
-        _lib = L
+        _lib = load(_SO)
     return _lib
+
+
+def load(path: str):
+    """Load a compiled oracle library from ``path`` and declare its signatures."""
+    L = ctypes.CDLL(path)
+    d = ctypes.POINTER(ctypes.c_double)
+    i64 = ctypes.c_int64
+    dbl = ctypes.c_double
+    vp = ctypes.c_void_p
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.kfo_gemv.argtypes = [i64, i64, d, i64, d, dbl, dbl, d, d]
+    L.kfo_gemvt.argtypes = [i64, i64, d, i64, d, dbl, dbl, d, d]
+    L.kfo_ger.argtypes = [i64, i64, d, i64, dbl, d, d, d, i64]
+    L.kfo_madd.argtypes = [i64, i64, d, d, d]
+    L.kfo_axpby.argtypes = [i64, dbl, d, dbl, d, d]
+    L.kfo_vadd3.argtypes = [i64, d, d, d, d]
+    L.kfo_dot.argtypes = [i64, d, d]
+    L.kfo_dot.restype = dbl
+    L.kfo_bicgk.argtypes = [i64, i64, d, i64, d, d, d, d]
+    L.kfo_gemver.argtypes = [i64, d, i64, d, d, d, d, d, d, dbl, dbl, d, d, d]
+    L.kfo_gesummv.argtypes = [i64, i64, d, d, i64, d, dbl, dbl, d]
+    L.kfo_atax.argtypes = [i64, i64, d, i64, d, d, d]
+    L.kfo_axpydot.argtypes = [i64, d, d, d, dbl, d]
+    L.kfo_axpydot.restype = dbl
+    L.kfo_waxpby.argtypes = [i64, dbl, d, dbl, d, d]
+    L.kfo_abs_gemv.argtypes = [i64, i64, d, i64, d, d]
+    L.kfo_abs_gemvt.argtypes = [i64, i64, d, i64, d, d]
+    L.kfo_quantize_rows.argtypes = [i64, i64, fp, i64, ctypes.c_int, vp, fp]
+    L.kfo_dequantize_rows.argtypes = [i64, i64, vp, ctypes.c_int, fp, d]
+    L.kfo_gemver_rowscaled_store.argtypes = [i64, vp, ctypes.c_int, fp, fp, fp, fp, fp, vp, fp]
+    L.kfo_bf16_value.argtypes = [ctypes.c_uint16]
+    L.kfo_bf16_value.restype = dbl
+    L.kfo_e4m3_value.argtypes = [ctypes.c_uint8]
+    L.kfo_e4m3_value.restype = dbl
+    L.kfo_bf16_code.argtypes = [ctypes.c_float]
+    L.kfo_bf16_code.restype = ctypes.c_uint16
+    L.kfo_e4m3_code.argtypes = [ctypes.c_float]
+    L.kfo_e4m3_code.restype = ctypes.c_uint8
+    return L
 
 
 def _d(a) -> np.ndarray:

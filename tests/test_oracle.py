@@ -198,6 +198,74 @@ def test_waxpby_cases():
     assert np.array_equal(w, y)
 
 
+# ------------------------------------------------------------------ elementaries
+
+def test_gemv_gemvt_scalars_and_accumulators():
+    """One-hot A = E_kl on a 3 x 5 matrix: GEMV gives a x_l e_k + b y0 and
+    GEMV^T gives a y_k e_l + b x0; alpha and beta each scale one term."""
+    m, n = 3, 5
+    x, y = U((n,), 3), U((m,), 4)
+    y0, x0 = U((m,), 9), U((n,), 10)
+    for k, l in [(0, 4), (2, 1)]:
+        A = np.zeros((m, n)); A[k, l] = 1.0
+        ye = 1.2 * y0; ye[k] += 1.5 * x[l]
+        np.testing.assert_allclose(oracle.gemv(A, x, 1.5, 1.2, y0), ye, rtol=1e-15, atol=0)
+        xe = 1.2 * x0; xe[l] += 1.5 * y[k]
+        np.testing.assert_allclose(oracle.gemvt(A, y, 1.5, 1.2, x0), xe, rtol=1e-15, atol=0)
+    assert np.array_equal(oracle.gemv(np.zeros((m, n)), x, 1.5, 1.0, y0), y0)
+    assert np.array_equal(oracle.gemvt(np.zeros((m, n)), y, 1.5, 1.0, x0), x0)
+
+
+def test_ger_one_hot_and_alpha():
+    """A = 0, u = e_k, v = e_l on a 3 x 5 matrix: B = alpha E_kl."""
+    m, n = 3, 5
+    e_m, e_n = np.eye(m), np.eye(n)
+    for k, l in [(0, 4), (2, 1)]:
+        B = oracle.ger(np.zeros((m, n)), e_m[k], e_n[l], alpha=-0.75)
+        Be = np.zeros((m, n)); Be[k, l] = -0.75
+        assert np.array_equal(B, Be)
+    A = U((m, n), 1)
+    assert np.array_equal(oracle.ger(A, U((m,), 5), np.zeros(n), alpha=2.0), A)
+
+
+def test_madd_vadd_dot_special_cases():
+    m, n = 4, 6
+    A = U((m, n), 1)
+    assert np.array_equal(oracle.madd(A, -A), np.zeros((m, n)))
+    E = np.zeros((m, n)); E[3, 2] = 1.0
+    C = oracle.madd(np.zeros((m, n)), E)
+    assert np.array_equal(C, E)
+    k = 9
+    x, y, z = U((k,), 3), U((k,), 4), U((k,), 9)
+    assert np.array_equal(oracle.vadd3(x, -x, z), z)
+    e = np.eye(k)
+    assert np.array_equal(oracle.vadd3(e[0], 2 * e[1], 4 * e[2]), e[0] + 2 * e[1] + 4 * e[2])
+    assert oracle.dot(e[0], x) == x[0] and oracle.dot(x, e[k - 1]) == x[k - 1]
+    xi = synth.integers((k,), 0, 3).numpy().astype(np.float64)
+    assert oracle.dot(xi, np.ones(k)) == sum(int(v) for v in xi)
+
+
+def test_script_elementary_ops():
+    """SCAL, VADD, MADD, GER and GEMV with an accumulator through the script
+    interpreter, each against a closed form."""
+    n = 6
+    x = synth.integers((n,), 0, 3).numpy().astype(np.float64)
+    y = synth.integers((n,), 0, 4).numpy().astype(np.float64)
+    e = np.eye(n)
+    E = oscript.run([("SCAL", ["t"], ["x"], [0.5]),
+                     ("VADD", ["v"], ["x", "y", "t"], []),
+                     ("GER", ["G"], ["Z", "e0", "e5"], [3.0]),
+                     ("MADD", ["H"], ["G", "G"], []),
+                     ("GEMV", ["g"], ["H", "x", "y"], [0.5, 2.0])],
+                    {"x": x, "y": y, "Z": np.zeros((n, n)), "e0": e[0], "e5": e[5]})
+    assert np.array_equal(E["t"], 0.5 * x)
+    assert np.array_equal(E["v"], 1.5 * x + y)
+    Ge = np.zeros((n, n)); Ge[0, 5] = 3.0
+    assert np.array_equal(E["G"], Ge) and np.array_equal(E["H"], 2 * Ge)
+    ge = 2.0 * y; ge[0] += 0.5 * 6.0 * x[5]
+    assert np.array_equal(E["g"], ge)
+
+
 # ------------------------------------------------------------------ scripts
 
 def test_script_matches_sequences():
