@@ -800,6 +800,22 @@ def cpu_baseline(sizes, budget_s=12.0, frac_rows=16):
 
 # ---------------------------------------------------------------- main
 
+def slowest_rank_ms(ms: float, dist, device) -> float:
+    """The longest timed region over all ranks.  Replicas run side by side,
+    so the job ends when its slowest rank does."""
+    if dist is None:
+        return ms
+    t = torch.tensor([ms], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(world: int, step_bytes: int, ms_per_step: float) -> float:
+    """Whole-job throughput in GB/s: each of ``world`` replicas moves
+    ``step_bytes`` per step, and a step lasts ``ms_per_step``."""
+    return world * step_bytes / (ms_per_step * 1e-3) / 1e9
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -933,13 +949,11 @@ def main():
         e2e_steps = max(1, min(args.steps, 5))
 
     step_bytes = sum(algorithmic_bytes(s, sizes[s]) for s in seqs)
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    ms_step = t_max / args.steps
-    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    dev = torch.device("cuda", local)
+    ms_step = slowest_rank_ms(total_ms, dist, dev) / args.steps
+    value = job_gbs(world, step_bytes, ms_step)
+    if not args.no_e2e:
+        e2e_ms = slowest_rank_ms(e2e_ms, dist, dev)
     peak, peak_kind = hbm_peak()
 
     seqinfo = {}
@@ -988,7 +1002,7 @@ def main():
         "gpu_launches": args.steps * sum(Suite.FUSED_LAUNCHES[s] for s in seqs),
     }
     if not args.no_e2e:
-        line["e2e"] = {"value": world * step_bytes / (e2e_ms / e2e_steps * 1e-3) / 1e9, "unit": "GB/s",
+        line["e2e"] = {"value": job_gbs(world, step_bytes, e2e_ms / e2e_steps), "unit": "GB/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": e2e_ms / e2e_steps}
     line.update(extra)
