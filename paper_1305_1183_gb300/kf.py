@@ -20,6 +20,9 @@ KF_F32, KF_BF16_ROWSCALE, KF_FP8E4M3_ROWSCALE = 0, 1, 2
 (KF_SEQ_BICGK, KF_SEQ_GEMVER, KF_SEQ_GESUMMV, KF_SEQ_ATAX, KF_SEQ_AXPYDOT, KF_SEQ_WAXPBY,
  KF_SEQ_GEMV, KF_SEQ_GEMVT, KF_SEQ_DOT) = range(9)
 
+(KF_ERR_INVALID_ARG, KF_ERR_SHAPE, KF_ERR_DTYPE, KF_ERR_ALIGN, KF_ERR_CYCLE, KF_ERR_UNDEFINED_VAR, KF_ERR_CUDA,
+ KF_ERR_NO_MEM, KF_ERR_DEVICE_TIMEOUT, KF_ERR_UNSUPPORTED, KF_ERR_WORKSPACE) = range(-1, -12, -1)
+
 STATUS_NAMES = {
     -1: "KF_ERR_INVALID_ARG", -2: "KF_ERR_SHAPE", -3: "KF_ERR_DTYPE", -4: "KF_ERR_ALIGN",
     -5: "KF_ERR_CYCLE", -6: "KF_ERR_UNDEFINED_VAR", -7: "KF_ERR_CUDA", -8: "KF_ERR_NO_MEM",

@@ -56,3 +56,17 @@ def test_validation_without_gpu(kf):
     assert L.kf_workspace_size(42, 1, 1, 0, ctypes.byref(b)) == -1
     assert L.kf_axpydot(10, None, None, None, 1.0, None, None, None, 0, None) == -1
     assert L.kf_ger(4, 4, 1024, 4, 1.0, 16, 16, 1024, 8, None) == -2                   # in place, ldb != lda
+
+
+def test_binding_constants_match_the_header(kf):
+    """Status codes and sequence ids in the Python binding equal the
+    header's, name for name."""
+    src = open(os.path.join(ROOT, "include", "kf.h")).read()
+    codes = dict(re.findall(r"#define\s+(KF_(?:OK|ERR_\w+))\s+\(?(-?\d+)\)?", src))
+    assert len(codes) >= 12, codes
+    for name, v in codes.items():
+        assert getattr(kf, name) == int(v), name
+    seqs = re.findall(r"\b(KF_SEQ_\w+)\s*=\s*(\d+)", src)
+    assert len(seqs) >= 9
+    for name, v in seqs:
+        assert getattr(kf, name) == int(v), name
