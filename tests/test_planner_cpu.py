@@ -194,3 +194,61 @@ def test_enumeration_cap(kf):
     s.output("v7")
     c, t = s.count_plans(cap=10)
     assert c == 10 and t
+
+
+def _groupings(kf, s):
+    """The kernels (lists of call indices) of every enumerated plan."""
+    c, _ = s.count_plans()
+    return [[k["calls"] for k in s.plan(kf.KF_PLAN_INDEX, index=i).describe()["kernels"]] for i in range(c)]
+
+
+def test_fusion_refused_across_lengths_and_shapes(kf):
+    """Vector calls of different lengths, and GEMVs on matrices of different
+    shapes, never share a kernel (Section 3.2: fused calls iterate over the
+    same index space)."""
+    s = kf.Script()
+    s.vector("x", 100); s.vector("y", 100); s.vector("a", 50); s.vector("b", 50)
+    s.input("x", "a"); s.output("y", "b")
+    s.call("SCAL", ["y"], ["x"], [2.0]); s.call("SCAL", ["b"], ["a"], [2.0])
+    assert _groupings(kf, s) == [[[0], [1]]]
+    s = kf.Script()
+    s.matrix("A", 64, 32); s.matrix("B", 48, 32)
+    s.vector("x", 32); s.vector("y", 64); s.vector("z", 48)
+    s.input("A", "B", "x"); s.output("y", "z")
+    s.call("GEMV", ["y"], ["A", "x"]); s.call("GEMV", ["z"], ["B", "x"])
+    assert _groupings(kf, s) == [[[0], [1]]]
+
+
+def test_at_most_two_matrices_per_kernel(kf):
+    """GEMVs of three matrices sharing x: every pair may fuse (GESUMMV's
+    shape), the three together may not."""
+    s = kf.Script()
+    for M in "ABC":
+        s.matrix(M, 32, 32)
+    for v in ("x", "y1", "y2", "y3"):
+        s.vector(v, 32)
+    s.input("A", "B", "C", "x"); s.output("y1", "y2", "y3")
+    for i, M in enumerate("ABC"):
+        s.call("GEMV", [f"y{i + 1}"], [M, "x"])
+    g = _groupings(kf, s)
+    assert all(len(k) <= 2 for plan in g for k in plan)
+    pairs = {tuple(k) for plan in g for k in plan if len(k) == 2}
+    assert pairs == {(0, 1), (0, 2), (1, 2)}
+
+
+def test_epilogue_never_mixes_row_and_column_results(kf):
+    """u = q + s with q = A p (row-indexed) and s = A^T r (column-indexed):
+    the map may join the kernel of one of them once the other is complete,
+    never the kernel that produces both."""
+    s = kf.Script()
+    s.matrix("A", 32, 32)
+    for v in ("p", "r", "q", "s", "u"):
+        s.vector(v, 32)
+    s.input("A", "p", "r"); s.output("u")
+    s.call("GEMV", ["q"], ["A", "p"]); s.call("GEMVT", ["s"], ["A", "r"])
+    s.call("AXPBY", ["u"], ["q", "s"], [1.0, 1.0])
+    g = _groupings(kf, s)
+    assert not any(sorted(k) == [0, 1, 2] for plan in g for k in plan)
+    assert any([0, 1] in plan for plan in g)            # the BiCGK core still fuses
+    assert any(sorted(k) == [0, 2] for plan in g for k in plan)
+    assert any(sorted(k) == [1, 2] for plan in g for k in plan)
