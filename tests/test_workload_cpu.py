@@ -1,0 +1,106 @@
+"""The learned planner's workload and its host-side selection logic (no GPU).
+
+Random scripts of 6-10 elementary calls (AXPY, SCAL, DOT, GEMV, GEMVT, GER)
+over shared vectors and matrices, n = 2^k with k in [10, 14], are the
+training and test data of the plan cost model.  These tests check the
+generator's stated rule on the full 500-script set, that the planner accepts
+every generated script, and the subset of plans timed per training script.
+"""
+
+from collections import Counter
+
+import numpy as np
+import pytest
+
+from synth import scripts as sscripts
+
+OPS = {"AXPBY", "SCAL", "DOT", "GEMV", "GEMVT", "GER"}
+
+
+@pytest.fixture(scope="module")
+def learn():
+    from paper_1305_1183_gb300 import _build
+    _build.build()
+    from paper_1305_1183_gb300 import learn as L
+    return L
+
+
+def _shape_ok(sd, name, kind):
+    return sd["vars"][name][0] == kind
+
+
+def test_random_scripts_follow_the_generation_rule():
+    n = 64
+    ops = Counter()
+    shared = 0
+    for i in range(500):
+        sd = sscripts.random_script(0, i, n)
+        calls = sd["calls"]
+        assert 6 <= len(calls) <= 10
+        for op, outs, ins, sc in calls:
+            assert op in OPS
+            ops[op] += 1
+            if op in ("GEMV", "GEMVT"):
+                assert _shape_ok(sd, ins[0], "m") and _shape_ok(sd, ins[1], "v") and _shape_ok(sd, outs[0], "v")
+                assert outs[0] != ins[1]                       # never overwrites its own input
+            elif op == "GER":
+                assert _shape_ok(sd, ins[0], "m") and _shape_ok(sd, outs[0], "m")
+            elif op == "DOT":
+                assert _shape_ok(sd, outs[0], "s")
+            else:
+                assert all(_shape_ok(sd, v, "v") for v in ins + outs)
+            assert all(-1.0 <= a < 1.0 or a in (0.0, 1.0) for a in sc)
+        reads = Counter(v for _, _, ins, _ in calls for v in ins)
+        shared += any(c >= 2 for c in reads.values())
+        assert all(spec[1] == n for spec in sd["vars"].values() if spec[0] in "vm")
+        assert set(sd["outputs"]) == {c[1][0] for c in calls}
+    # every op of the vocabulary is drawn about one time in six
+    total = sum(ops.values())
+    for op in OPS:
+        assert 0.12 < ops[op] / total < 0.22, (op, ops[op] / total)
+    # operands are shared: nearly every script reads some variable twice
+    assert shared >= 450
+
+
+def test_every_generated_script_is_accepted_by_the_planner(learn):
+    for i in range(100):
+        sd = sscripts.random_script(0, i, 1024)
+        s = learn.to_script(sd)
+        s.validate()
+        count, _ = s.count_plans(cap=64)
+        assert count >= 1
+
+
+def test_script_sizes_are_powers_of_two_in_range(learn):
+    sizes = Counter(learn.script_size(0, i, 10, 14) for i in range(500))
+    assert set(sizes) == {1 << k for k in range(10, 15)}
+    assert min(sizes.values()) >= 60                   # each of the five about 100 times
+
+
+def test_training_subset(learn):
+    """Up to per_script plans: all of them when there are that few, else the
+    best-predicted half, the fewest-kernel plan, the unfused plan and a
+    seeded sample of the rest; deterministic for a seed."""
+    pred = np.array([5.0, 1.0, 3.0, 2.0, 4.0])
+    nk = np.array([2, 3, 1, 4, 2])
+    assert learn.training_subset(0, 0, pred, nk, 4, per_script=8) == [0, 1, 2, 3, 4]
+    count, per = 300, 40
+    pred = np.linspace(1.0, 2.0, count)[::-1].copy()   # the last plans are predicted best
+    nk = np.full(count, 3)
+    nk[7] = 1                                          # fewest kernels
+    nk[11] = 6                                         # the unfused plan (one kernel per call)
+    sub = learn.training_subset(0, 5, pred, nk, 6, per_script=per)
+    assert len(sub) == per and len(set(sub)) == per and sub == sorted(sub)
+    assert set(range(count - per // 2, count)) <= set(sub)
+    assert 7 in sub and 11 in sub
+    assert sub == learn.training_subset(0, 5, pred, nk, 6, per_script=per)
+    assert sub != learn.training_subset(1, 5, pred, nk, 6, per_script=per)
+
+
+def test_summary_of_ratios(learn):
+    rows = [{"r": 1.0}, {"r": 1.04}, {"r": 1.21}, {"r": 1.0}]
+    s = learn.summary(rows, "r")
+    assert s["within_5pct"] == 0.75
+    assert s["worst"] == 1.21
+    assert s["mean_ratio"] == pytest.approx(1.0625, abs=1e-4)
+    assert s["geomean_ratio"] == pytest.approx(float(np.exp(np.mean(np.log([1.0, 1.04, 1.21, 1.0])))), abs=1e-4)
