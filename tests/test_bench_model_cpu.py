@@ -1,0 +1,73 @@
+"""The byte model behind every GB/s the bench reports (no GPU).
+
+bench.py counts the bytes a sequence must move at least once (each matrix
+and vector crossing HBM once), and the bytes of its one-kernel-per-call
+chain.  The planner counts the bytes of each plan from the script on its
+own.  The two models must agree at the benchmarked sizes.  The counts must
+also equal the closed forms of the byte table (A read once: 4mn bytes plus
+the vectors).
+"""
+
+import pytest
+
+import bench
+from test_planner_cpu import atax, axpydot, bicgk, gemver, gesummv, waxpby
+
+BUILDERS = {
+    "bicgk": lambda kf: bicgk(kf, 16384, 16384),
+    "gemver": lambda kf: gemver(kf, 8192),
+    "gesummv": lambda kf: gesummv(kf, 8192),
+    "atax": lambda kf: atax(kf, 8192),
+    "axpydot": lambda kf: axpydot(kf, 1 << 26),
+    "waxpby": lambda kf: waxpby(kf, 1 << 26),
+}
+
+
+@pytest.fixture(scope="module")
+def kf():
+    from paper_1305_1183_gb300 import _build, kf as K
+    _build.build()
+    K.lib()
+    return K
+
+
+def test_closed_forms_at_the_benchmarked_sizes():
+    F = bench.FULL
+    n = 8192
+    assert bench.algorithmic_bytes("bicgk", F["bicgk"]) == 4 * 16384 * 16384 + 8 * (2 * 16384)
+    assert bench.algorithmic_bytes("gemver", F["gemver"]) == 12 * n * n + 36 * n
+    assert bench.algorithmic_bytes("gesummv", F["gesummv"]) == 8 * n * n + 8 * n
+    assert bench.algorithmic_bytes("atax", F["atax"]) == 4 * n * n + 8 * n
+    assert bench.algorithmic_bytes("axpydot", F["axpydot"]) == 16 * (1 << 26) + 4
+    assert bench.algorithmic_bytes("waxpby", F["waxpby"]) == 12 * (1 << 26)
+    # the matrix passes are matrix bound: vectors add under 0.1 %
+    for s in ("bicgk", "gemver", "gesummv", "atax"):
+        b = bench.algorithmic_bytes(s, F[s])
+        mat = {"bicgk": 4 * 16384 ** 2, "gemver": 12 * n * n, "gesummv": 8 * n * n, "atax": 4 * n * n}[s]
+        assert 0 <= b - mat < 1e-3 * mat
+
+
+@pytest.mark.parametrize("seq,ideal", [("bicgk", 2.0), ("gemver", 2.0), ("gesummv", 1.0), ("atax", 2.0),
+                                       ("axpydot", 1.25), ("waxpby", 5 / 3)])
+def test_ideal_speedups(seq, ideal):
+    s = bench.FULL[seq]
+    assert bench.unfused_bytes(seq, s) / bench.algorithmic_bytes(seq, s) == pytest.approx(ideal, rel=2e-3)
+
+
+@pytest.mark.parametrize("seq", sorted(BUILDERS))
+def test_planner_byte_counts_agree_with_the_bench(kf, seq):
+    """The planner's fused and unfused plans move the bench's bytes (the
+    plan description prints six significant digits).  ATAX is the exception
+    for the fused count: a script {t = A x; y = A^T t} gets the paper's two
+    kernels, since a GEMV result is not consumed in its own kernel, while
+    the bench times the dedicated single-pass kf_atax (A read once)."""
+    s = BUILDERS[seq](kf)
+    size = bench.FULL[seq]
+    fused = s.plan(kf.KF_PLAN_ANALYTIC).describe()["bytes"]
+    unfused = s.plan(kf.KF_PLAN_UNFUSED).describe()["bytes"]
+    assert unfused == pytest.approx(bench.unfused_bytes(seq, size), rel=1e-4)
+    if seq == "atax":
+        assert fused == pytest.approx(bench.unfused_bytes(seq, size), rel=1e-4)
+        assert bench.algorithmic_bytes(seq, size) == pytest.approx(fused / 2, rel=1e-3)
+    else:
+        assert fused == pytest.approx(bench.algorithmic_bytes(seq, size), rel=1e-4)
