@@ -252,3 +252,27 @@ def test_epilogue_never_mixes_row_and_column_results(kf):
     assert any([0, 1] in plan for plan in g)            # the BiCGK core still fuses
     assert any(sorted(k) == [0, 2] for plan in g for k in plan)
     assert any(sorted(k) == [1, 2] for plan in g for k in plan)
+
+
+def test_analytic_predictor_is_max_of_transfer_and_compute_plus_launch(kf):
+    """Per kernel: max(bytes / bandwidth, flops / FP32 rate) + launch cost
+    (Section 3.2's max(t_t, t_c), plus the per-kernel cost), summed over
+    kernels.  BiCGK 16384^2: 4mn flops (2 per multiply-add) at 80 TFLOP/s."""
+    m = n = 16384
+    try:
+        kf.kf_planner_set_model(1000.0, 3.0)            # 1 TB/s: transfer bound
+        s = bicgk(kf, m, n)
+        for mode in (kf.KF_PLAN_ANALYTIC, kf.KF_PLAN_UNFUSED):
+            p = s.plan(mode)
+            d = p.describe()
+            want = sum(k["bytes"] / 1e12 * 1e6 + 3.0 for k in d["kernels"])
+            assert p.predicted_us() == pytest.approx(want, rel=1e-5)
+        kf.kf_planner_set_model(1e9, 3.0)               # bandwidth out of the way: compute bound
+        p = bicgk(kf, m, n).plan(kf.KF_PLAN_ANALYTIC)
+        assert p.predicted_us() == pytest.approx(4.0 * m * n / 80e12 * 1e6 + 3.0, rel=1e-3)
+        with pytest.raises(kf.KFError):
+            kf.kf_planner_set_model(0.0, 3.0)
+        with pytest.raises(kf.KFError):
+            kf.kf_planner_set_model(1000.0, -1.0)
+    finally:
+        kf.kf_planner_set_model(6500.0, 2.0)            # the built-in model
