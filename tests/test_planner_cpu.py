@@ -276,3 +276,30 @@ def test_analytic_predictor_is_max_of_transfer_and_compute_plus_launch(kf):
             kf.kf_planner_set_model(1000.0, -1.0)
     finally:
         kf.kf_planner_set_model(6500.0, 2.0)            # the built-in model
+
+
+def test_plan_features_describe_the_plan(kf):
+    """The 16 features of the learned cost model match what the plan is:
+    kernel counts by kind, log2 of bytes (total, matrix, vector), log2 n,
+    calls per kernel, matrix ops per kernel, dependent finishing phases,
+    epilogue outputs, matrix stores, log2 of the analytic prediction."""
+    import math
+    n = 4096
+    s = gemver(kf, n)
+    fused, unf = s.plan(kf.KF_PLAN_ANALYTIC), s.plan(kf.KF_PLAN_UNFUSED)
+    for p in (fused, unf):
+        f, d = p.features(), p.describe()
+        assert f[0] == p.kernel_count() == f[1] + f[2]
+        assert f[3] == pytest.approx(math.log2(1 + d["bytes"]), abs=1e-4)
+        assert f[6] == pytest.approx(math.log2(n))
+        assert f[7] == pytest.approx(5 / p.kernel_count())          # GEMVER's 5 calls
+        assert f[13] == pytest.approx(math.log2(1 + p.predicted_us()), abs=1e-4)
+    f, fu = fused.features(), unf.features()
+    assert (f[1], f[2]) == (2, 0)                       # {GER, GER, GEMVT, AXPBY} and {GEMV}
+    assert f[8] == 3                                     # GER, GER, GEMVT in one pass
+    assert f[15] == 1 and fu[15] == 2                    # B stored once; twice by the GER chain
+    assert f[4] == pytest.approx(math.log2(1 + 2 * 4.0 * n * n), abs=1e-3)   # matrix reads: A, then B
+    assert f[5] == pytest.approx(math.log2(1 + fused.describe()["bytes"] - 2 * 4.0 * n * n), abs=1e-3)
+    assert fu[3] > f[3] + 0.9                            # the chain moves about twice the bytes
+    g = bicgk(kf, 2048, 2048).plan(kf.KF_PLAN_ANALYTIC).features()
+    assert (g[0], g[1], g[8], g[9], g[10]) == (1, 1, 2, 1, 1)   # row and column results: two finishes
