@@ -124,6 +124,34 @@ def collect(seed, indices, kmin, kmax, per_script, reps, cap=2000, device="cuda"
             np.array(sid, dtype=np.int64), meta)
 
 
+def timing_key(seed, indices, kmin, kmax, per_script, reps, device):
+    """What a plan-timing table was measured on.  A stored table is reused
+    only under the same key: timings belong to one device and one workload."""
+    if torch.cuda.is_available() and str(device).startswith("cuda"):
+        dev = torch.cuda.get_device_name(torch.device(device))
+    else:
+        dev = str(device)
+    return {"seed": int(seed), "indices": [int(i) for i in indices], "kmin": int(kmin), "kmax": int(kmax),
+            "per_script": int(per_script), "reps": int(reps), "device": dev}
+
+
+def save_timings(path, key, X, ms, pu, sid, meta):
+    """Write a plan-timing table (features, measured ms, analytic prediction,
+    script ids, per-script notes) with its key, as one .npz file at ``path``."""
+    with open(path, "wb") as fh:
+        np.savez(fh, X=X, ms=ms, pu=pu, sid=sid, meta=json.dumps(meta), key=json.dumps(key, sort_keys=True))
+
+
+def load_timings(path, key):
+    """The table stored at ``path`` if it was measured under ``key``, else None."""
+    if not path or not os.path.exists(path):
+        return None
+    with np.load(path, allow_pickle=False) as z:
+        if str(z["key"]) != json.dumps(key, sort_keys=True):
+            return None
+        return (z["X"].copy(), z["ms"].copy(), z["pu"].copy(), z["sid"].copy(), json.loads(str(z["meta"])))
+
+
 def he_uniform_params(d_in, seed, device):
     """He-uniform weights from the seeded generator, zero biases (kf_mlp layout)."""
     H = kf.MLP_HIDDEN
@@ -209,9 +237,19 @@ def summary(rows, key):
 
 
 def run(seed=0, scripts=500, ntrain=400, kmin=10, kmax=14, per_script=64, reps=5, epochs=3000, top_k=3,
-        analytic_weight=1.0, centre=True, margin=0.1, device="cuda", log=print):
+        analytic_weight=1.0, centre=True, margin=0.1, device="cuda", log=print, timings=""):
+    """Collect (or load from ``timings``) the training table, train, and
+    score the held-out scripts.  With a ``timings`` path, a table measured
+    under the same key is reused and a freshly collected one is saved."""
     t0 = time.time()
-    X, ms, pu, sid, meta = collect(seed, range(ntrain), kmin, kmax, per_script, reps, device=device)
+    key = timing_key(seed, range(ntrain), kmin, kmax, per_script, reps, device)
+    got = load_timings(timings, key)
+    if got is None:
+        X, ms, pu, sid, meta = collect(seed, range(ntrain), kmin, kmax, per_script, reps, device=device)
+        if timings:
+            save_timings(timings, key, X, ms, pu, sid, meta)
+    else:
+        X, ms, pu, sid, meta = got
     t1 = time.time()
     model, hist = train(X, ms, pu, sid if centre else None, analytic_weight, epochs=epochs, seed=seed,
                         device=device)
@@ -227,6 +265,7 @@ def run(seed=0, scripts=500, ntrain=400, kmin=10, kmax=14, per_script=64, reps=5
                    "centred_per_script": centre,
                    "features": kf.NFEATURES,
                    "hidden": kf.MLP_HIDDEN},
+        "train_timings": "loaded" if got is not None else "measured",
         "train_plans_timed": int(len(ms)), "test_plans_timed": int(plans.sum()),
         "test_plans_per_script": {"mean": float(plans.mean()), "max": int(plans.max())},
         "seconds": {"collect": round(t1 - t0, 1), "train": round(t2 - t1, 2), "evaluate": round(t3 - t2, 1)},
@@ -260,10 +299,13 @@ def main(argv=None):
     ap.add_argument("--margin", type=float, default=0.1, help="score margin (ln ms) of plans also re-timed")
     ap.add_argument("--out", default="")
     ap.add_argument("--save-model", default="")
+    ap.add_argument("--timings", default="",
+                    help="plan-timing table (.npz): reused if measured with the same seed, scripts, sizes, "
+                         "plans per script, repetitions and device; written after a fresh collection")
     a = ap.parse_args(argv)
     kf.lib()
     res, model = run(a.seed, a.scripts, a.train, a.kmin, a.kmax, a.per_script, a.reps, a.epochs, a.top_k,
-                     a.analytic_weight, centre=not a.no_centre, margin=a.margin)
+                     a.analytic_weight, centre=not a.no_centre, margin=a.margin, timings=a.timings)
     if a.out:
         with open(a.out, "w") as fh:
             json.dump(res, fh, indent=1)

@@ -104,3 +104,25 @@ def test_summary_of_ratios(learn):
     assert s["worst"] == 1.21
     assert s["mean_ratio"] == pytest.approx(1.0625, abs=1e-4)
     assert s["geomean_ratio"] == pytest.approx(float(np.exp(np.mean(np.log([1.0, 1.04, 1.21, 1.0])))), abs=1e-4)
+
+
+def test_timing_table_round_trip_and_key(learn, tmp_path):
+    """A stored plan-timing table comes back unchanged under its own key and
+    is refused under any other (another seed, size range or device)."""
+    key = learn.timing_key(0, range(4), 10, 14, 64, 5, "cpu")
+    X = np.arange(48, dtype=np.float64).reshape(3, 16)
+    ms, pu, sid = np.array([0.5, 0.25, 1.0]), np.array([400.0, 200.0, 900.0]), np.array([0, 0, 3])
+    meta = [{"index": 0, "n": 1024, "calls": 7, "plans": 12, "timed": 2}]
+    path = str(tmp_path / "timings.npz")
+    learn.save_timings(path, key, X, ms, pu, sid, meta)
+    got = learn.load_timings(path, key)
+    assert got is not None
+    for a, b in zip(got[:4], (X, ms, pu, sid)):
+        assert np.array_equal(a, b) and a.dtype == b.dtype
+    assert got[4] == meta
+    for other in (learn.timing_key(1, range(4), 10, 14, 64, 5, "cpu"),
+                  learn.timing_key(0, range(4), 10, 13, 64, 5, "cpu"),
+                  learn.timing_key(0, range(4), 10, 14, 64, 5, "another-device")):
+        assert learn.load_timings(path, other) is None
+    assert learn.load_timings(str(tmp_path / "none.npz"), key) is None
+    assert learn.load_timings("", key) is None
