@@ -303,3 +303,107 @@ def test_plan_features_describe_the_plan(kf):
     assert fu[3] > f[3] + 0.9                            # the chain moves about twice the bytes
     g = bicgk(kf, 2048, 2048).plan(kf.KF_PLAN_ANALYTIC).features()
     assert (g[0], g[1], g[8], g[9], g[10]) == (1, 1, 2, 1, 1)   # row and column results: two finishes
+
+
+def _random_valid_script(rng, n, m):
+    """A valid script over vectors of length n ("x") and m ("y") and m x n
+    matrices, every operand written or declared input before it is read."""
+    kinds, inputs, calls = {}, [], []
+
+    def new(kind):
+        nm = f"{kind}{len(kinds)}"
+        kinds[nm] = kind
+        return nm
+
+    def pick(kind):
+        pool = sorted(k for k, v in kinds.items() if v == kind)
+        if pool and rng.random() < 0.7:
+            return rng.choice(pool)
+        nm = new(kind)
+        inputs.append(nm)
+        return nm
+
+    for _ in range(rng.randint(1, 9)):
+        op = rng.choice(["AXPBY", "SCAL", "DOT", "VADD", "GEMV", "GEMVT", "GER"])
+        vk = rng.choice("xy")
+        a, b = rng.uniform(-1, 1), rng.uniform(-1, 1)
+        if op == "AXPBY":
+            ins = [pick(vk), pick(vk)]
+            out, sc = (ins[1] if rng.random() < 0.5 else pick(vk)), [a, b]
+        elif op == "SCAL":
+            ins = [pick(vk)]
+            out, sc = (ins[0] if rng.random() < 0.5 else pick(vk)), [a]
+        elif op == "VADD":
+            ins, out, sc = [pick(vk), pick(vk), pick(vk)], pick(vk), []
+        elif op == "DOT":
+            ins, out, sc = [pick(vk), pick(vk)], new("s"), []
+        elif op in ("GEMV", "GEMVT"):
+            src, dst = ("x", "y") if op == "GEMV" else ("y", "x")
+            ins = [pick("A"), pick(src)] + ([pick(dst)] if rng.random() < 0.3 else [])
+            out = pick(dst)
+            if out in ins[1:]:
+                out = new(dst)
+            sc = [a, b]
+        else:
+            ins = [pick("A"), pick("y"), pick("x")]
+            out, sc = (ins[0] if rng.random() < 0.6 else new("A")), [a]
+        calls.append((op, [out], ins, sc))
+    return kinds, sorted(set(inputs)), calls
+
+
+def test_random_scripts_every_plan_is_well_formed(kf):
+    """Every enumerated plan of 300 random valid scripts (sizes 1 to 64,
+    square and not) covers each call once, orders its kernels so that every
+    read-after-write, write-after-read and write-after-write dependency
+    points forward, and never feeds a GEMV / GEMVT result to a matrix op of
+    the kernel that computes it."""
+    import random
+    rng = random.Random(1305)
+    nplans = 0
+    for _ in range(300):
+        n = rng.choice([1, 2, 7, 33, 64])
+        m = rng.choice([n, 5])
+        kinds, inputs, calls = _random_valid_script(rng, n, m)
+        s = kf.Script()
+        for nm, kd in kinds.items():
+            if kd == "x":
+                s.vector(nm, n)
+            elif kd == "y":
+                s.vector(nm, m)
+            elif kd == "A":
+                s.matrix(nm, m, n)
+            else:
+                s.scalar(nm)
+        s.input(*inputs)
+        written = sorted({c[1][0] for c in calls})
+        s.output(*rng.sample(written, rng.randint(1, len(written))))
+        for op, outs, ins, sc in calls:
+            s.call(op, outs, ins, sc)
+        s.validate()
+        # dependencies: (earlier call, later call, reduction result consumed by a matrix op)
+        deps, last_w, readers = [], {}, {}
+        for j, (op, outs, ins, _) in enumerate(calls):
+            for pos, v in enumerate(ins):
+                if v in last_w:
+                    i = last_w[v]
+                    deep = calls[i][0] in ("GEMV", "GEMVT") and op in ("GEMV", "GEMVT", "GER") and pos > 0
+                    deps.append((i, j, deep))
+                readers.setdefault(v, []).append(j)
+            o = outs[0]
+            deps += [(i, j, False) for i in readers.get(o, []) if i != j]
+            if o in last_w:
+                deps.append((last_w[o], j, False))
+            last_w[o], readers[o] = j, []
+        count, _ = s.count_plans(cap=100)
+        assert count >= 1
+        for idx in range(count):
+            p = s.plan(kf.KF_PLAN_INDEX, index=idx, max_plans=100)
+            kernels = [k["calls"] for k in p.describe()["kernels"]]
+            assert sorted(c for k in kernels for c in k) == list(range(len(calls))), kernels
+            where = {c: ki for ki, k in enumerate(kernels) for c in k}
+            for i, j, deep in deps:
+                assert where[i] <= where[j], (calls, kernels, i, j)
+                assert not (deep and where[i] == where[j]), (calls, kernels, i, j)
+            assert p.predicted_us() > 0 and p.workspace_size() >= 0 and len(p.features()) == 16
+            nplans += 1
+    assert nplans > 1000
