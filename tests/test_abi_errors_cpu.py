@@ -1,0 +1,142 @@
+"""Each entry point returns the status its declaration in include/kf.h
+documents, for each kind of bad argument (no GPU).
+
+Every call below breaks at least one rule, so it returns from argument
+checking before any device work: stand-in addresses are never dereferenced.
+"""
+
+import ctypes
+
+import pytest
+
+P = 1 << 16                # stand-in device address (16-byte aligned, never dereferenced)
+Q = 1 << 20                # a second one
+F32, BF16, E4M3 = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1305_1183_gb300 import _build, kf
+    _build.build()
+    return kf.lib()
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_1305_1183_gb300 import kf
+    return kf
+
+
+def _ws_size(L, seq, m, n, fmt=F32):
+    b = ctypes.c_size_t(0)
+    assert L.kf_workspace_size(seq, m, n, fmt, ctypes.byref(b)) == 0
+    return b.value
+
+
+def test_gemver_errors(L, K):
+    n = 8
+    ok = dict(n=n, A=P, lda=n, u1=P, v1=P, u2=P, v2=P, y=P, z=P, alpha=1.5, beta=1.2, B=Q, ldb=n, x=P, w=P)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return L.kf_gemver(a["n"], a["A"], a["lda"], a["u1"], a["v1"], a["u2"], a["v2"], a["y"], a["z"],
+                           a["alpha"], a["beta"], a["B"], a["ldb"], a["x"], a["w"], None, 0, None)
+    assert call(n=-1) == K.KF_ERR_INVALID_ARG
+    assert call(A=None) == K.KF_ERR_INVALID_ARG
+    assert call(lda=n - 1) == K.KF_ERR_SHAPE
+    assert call(ldb=n - 1) == K.KF_ERR_SHAPE
+    for v in ("u1", "v1", "u2", "v2", "y", "z", "x", "w"):
+        assert call(**{v: None}) == K.KF_ERR_INVALID_ARG, v
+        assert v.encode() in L.kf_last_error()
+    assert call(B=P, lda=2 * n, ldb=n) == K.KF_ERR_SHAPE          # in place with ldb != lda
+    assert call() == K.KF_ERR_WORKSPACE                             # no workspace
+
+
+def test_gemver_q_errors(L, K):
+    n = 8
+
+    def call(fmt=BF16, sA=P, QB=Q, sB=P, ws=None, wsb=0, lda=n):
+        return L.kf_gemver_q(n, P, lda, fmt, sA, P, P, P, P, P, P, 1.5, 1.2, QB, n, sB, P, P, ws, wsb, None)
+    assert call(fmt=F32) == K.KF_ERR_DTYPE
+    assert call(fmt=7) == K.KF_ERR_DTYPE
+    assert call(sA=None) == K.KF_ERR_INVALID_ARG
+    assert call(sB=None) == K.KF_ERR_INVALID_ARG
+    assert call(QB=P) == K.KF_ERR_SHAPE                             # QB aliases QA
+    assert call(lda=n - 1) == K.KF_ERR_SHAPE
+    assert call(fmt=E4M3) == K.KF_ERR_WORKSPACE
+    assert call(fmt=E4M3, ws=Q, wsb=16) == K.KF_ERR_WORKSPACE        # below the header
+
+
+def test_gesummv_atax_errors(L, K):
+    m, n = 8, 12
+    g = lambda A=P, B=Q, lda=n, x=P, y=P, ws=None, wsb=0: L.kf_gesummv(  # noqa: E731
+        m, n, A, B, lda, x, 1.5, 1.2, y, ws, wsb, None)
+    assert g(B=None) == K.KF_ERR_INVALID_ARG
+    assert g(lda=n - 1) == K.KF_ERR_SHAPE
+    assert g(x=None) == K.KF_ERR_INVALID_ARG and g(y=None) == K.KF_ERR_INVALID_ARG
+    assert g() == K.KF_ERR_WORKSPACE
+    assert g(ws=Q, wsb=_ws_size(L, K.KF_SEQ_GESUMMV, m, n) - 1) == K.KF_ERR_WORKSPACE
+    a = lambda lda=n, x=P, y=Q, ws=None: L.kf_atax(m, n, P, lda, x, y, ws, 0, None)  # noqa: E731
+    assert a(x=None) == K.KF_ERR_INVALID_ARG and a(y=None) == K.KF_ERR_INVALID_ARG
+    assert a(lda=n - 1) == K.KF_ERR_SHAPE
+    assert a() == K.KF_ERR_WORKSPACE
+    assert a(x=P + 4) == K.KF_ERR_WORKSPACE                         # unaligned: two-pass form, same rule
+
+
+def test_bicgk_and_elementary_matrix_errors(L, K):
+    m, n = 8, 12
+    b = lambda fmt=F32, rs=None, ws=None, wsb=0: L.kf_bicgk(  # noqa: E731
+        m, n, P, n, fmt, rs, P, P, Q, Q, ws, wsb, None)
+    assert b(fmt=BF16) == K.KF_ERR_INVALID_ARG                      # row scales required
+    assert b() == K.KF_ERR_WORKSPACE
+    assert b(ws=Q, wsb=_ws_size(L, K.KF_SEQ_BICGK, m, n) - 1) == K.KF_ERR_WORKSPACE
+    gv = lambda fmt=F32, beta=0.0, y0=None, ws=None: L.kf_gemv(  # noqa: E731
+        m, n, P, n, fmt, None, 1.0, P, beta, y0, Q, ws, 0, None)
+    assert gv(fmt=5) == K.KF_ERR_DTYPE
+    assert gv(fmt=E4M3) == K.KF_ERR_INVALID_ARG
+    assert gv(beta=1.0) == K.KF_ERR_INVALID_ARG                     # y0 needed when beta != 0
+    assert gv() == K.KF_ERR_WORKSPACE
+    gt = lambda beta=0.0, x0=None, lda=n: L.kf_gemvt(  # noqa: E731
+        m, n, P, lda, F32, None, 1.0, P, beta, x0, Q, None, 0, None)
+    assert gt(beta=2.0) == K.KF_ERR_INVALID_ARG
+    assert gt(lda=n - 1) == K.KF_ERR_SHAPE
+    assert gt() == K.KF_ERR_WORKSPACE
+    gr = lambda u=P, v=P, B=Q, ldb=n: L.kf_ger(m, n, P, n, 1.0, u, v, B, ldb, None)  # noqa: E731
+    assert gr(u=None) == K.KF_ERR_INVALID_ARG and gr(v=None) == K.KF_ERR_INVALID_ARG
+    assert gr(B=None) == K.KF_ERR_INVALID_ARG
+    assert gr(ldb=n - 1) == K.KF_ERR_SHAPE
+    md = lambda A=P, lda=n, ldb=n, ldc=n: L.kf_madd(m, n, A, lda, Q, ldb, Q, ldc, None)  # noqa: E731
+    assert md(A=None) == K.KF_ERR_INVALID_ARG
+    assert md(lda=n - 1) == K.KF_ERR_SHAPE and md(ldb=n - 1) == K.KF_ERR_SHAPE and md(ldc=n - 1) == K.KF_ERR_SHAPE
+    qr = lambda fmt=BF16, Qp=Q, rs=P: L.kf_quantize_rows(m, n, P, n, fmt, Qp, rs, None)  # noqa: E731
+    assert qr(fmt=F32) == K.KF_ERR_DTYPE
+    assert qr(Qp=None) == K.KF_ERR_INVALID_ARG and qr(rs=None) == K.KF_ERR_INVALID_ARG
+
+
+def test_vector_errors(L, K):
+    n = 100
+    assert L.kf_waxpby(-1, 1.0, P, 1.0, P, Q, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_waxpby(n, 1.0, None, 1.0, P, Q, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_waxpby(n, 1.0, P, 1.0, P, None, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_axpydot(n, P, P, P, 1.5, Q, None, None, 0, None) == K.KF_ERR_INVALID_ARG       # null r
+    assert L.kf_axpydot(n, P, None, P, 1.5, Q, Q, None, 0, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_axpydot(n, P, P, P, 1.5, Q, Q, None, 0, None) == K.KF_ERR_WORKSPACE
+    assert L.kf_axpby(n, 1.0, P, 1.0, None, Q, None) == K.KF_ERR_INVALID_ARG                  # y with beta != 0
+    assert L.kf_axpby(-3, 1.0, P, 0.0, None, Q, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_scal(n, 2.0, None, Q, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_vadd3(n, P, P, None, Q, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_dot(n, P, P, None, Q, 4096, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_dot(n, P, P, Q, None, 0, None) == K.KF_ERR_WORKSPACE
+    assert L.kf_dot(n, P, P, Q, Q, 8, None) == K.KF_ERR_WORKSPACE
+
+
+def test_empty_problems_return_before_any_launch(L, K):
+    """Empty sizes are valid and need no pointers or workspace."""
+    assert L.kf_bicgk(0, 0, None, 0, F32, None, None, None, None, None, None, 0, None) == K.KF_OK
+    assert L.kf_gemver(0, None, 0, None, None, None, None, None, None, 1.0, 1.0, None, 0, None, None,
+                       None, 0, None) == K.KF_OK
+    assert L.kf_gesummv(0, 5, None, None, 5, P, 1.0, 1.0, None, None, 0, None) == K.KF_OK
+    assert L.kf_atax(5, 0, None, 0, None, None, None, 0, None) == K.KF_OK
+    assert L.kf_waxpby(0, 1.0, None, 1.0, None, None, None) == K.KF_OK
+    assert L.kf_ger(0, 4, None, 4, 1.0, None, P, None, 4, None) == K.KF_OK
+    assert L.kf_madd(3, 0, None, 0, None, 0, None, 0, None) == K.KF_OK
