@@ -329,7 +329,11 @@ kf_status kf_plan_enumerate_info(const kf_script* s, int cap, float* feats, doub
                                  int* count);
 /* JSON: kernels, their calls and bytes, prediction. */
 kf_status kf_plan_describe(const kf_plan* p, char* buf, size_t cap, size_t* needed);
-/* Enqueue the plan's kernels on `stream`. */
+/* Enqueue the plan's kernels on `stream`.  bindings[var_id] is the device
+ * address of each script variable (one device float for a scalar); ws holds
+ * at least kf_plan_workspace_size bytes.  Every kernel's bindings and
+ * workspace are checked before the first launch: on KF_ERR_INVALID_ARG (a
+ * variable not bound) or KF_ERR_WORKSPACE nothing has been enqueued. */
 kf_status kf_plan_execute(const kf_plan* p, void* const* bindings, int n_bindings, void* ws, size_t ws_bytes,
                           void* stream);
 /* Synchronous: run once, then time `reps` executions with CUDA events on

@@ -126,11 +126,44 @@ kf_status launch_kernel(const Kernel& K, void* const* bindings, int nb, void* ws
 }
 
 
+// The checks launch_kernel makes, without launching: every variable the
+// kernel uses is bound, and the workspace holds what the kernel needs (the
+// matrix-pass rule is matprog_bind_workspace's own, on a copy).
+kf_status check_kernel(const Kernel& K, void* const* bindings, int nb, void* ws, size_t ws_bytes) {
+  for (auto& b : K.bind)
+    if (b.second < 0 || b.second >= nb || bindings[b.second] == nullptr)
+      return err(KF_ERR_INVALID_ARG, "variable " + std::to_string(b.second) + " is not bound");
+  if (K.is_mat) {
+    MatProg P = K.mp;
+    char* wsm = ws ? static_cast<char*>(ws) + plan_vec_region() : nullptr;
+    const size_t wsm_bytes = ws_bytes > plan_vec_region() ? ws_bytes - plan_vec_region() : 0;
+    if (matprog_bind_workspace(P, wsm, wsm_bytes) != 0)
+      return err(KF_ERR_WORKSPACE, "workspace missing or smaller than kf_plan_workspace_size()");
+  } else if (K.vp.ndot > 0 && (ws == nullptr || ws_bytes < plan_vec_region())) {
+    return err(KF_ERR_WORKSPACE, "workspace missing or smaller than kf_plan_workspace_size()");
+  }
+  return KF_OK;
+}
+
+// Every kernel of a plan checked before the first launch, so that a call
+// with a missing binding or a short workspace launches nothing.
+kf_status check_plan(const Plan& P, void* const* bindings, int nb, void* ws, size_t ws_bytes) {
+  for (const Kernel& K : P.kernels) {
+    kf_status st = check_kernel(K, bindings, nb, ws, ws_bytes);
+    if (st != KF_OK) return st;
+  }
+  return KF_OK;
+}
+
 // Run once, then time `reps` executions with CUDA events; the median (ms).
 kf_status time_plan(const Plan& P, int nvars, void* const* bindings, int nb, void* ws, size_t ws_bytes, void* stream,
                     int reps, float* median_ms) {
   if (nb > 0 && bindings == nullptr) return err(KF_ERR_INVALID_ARG, "null bindings");
   if (nb < nvars) return err(KF_ERR_INVALID_ARG, "every script variable needs a binding");
+  {
+    kf_status chk = check_plan(P, bindings, nb, ws, ws_bytes);
+    if (chk != KF_OK) return chk;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const MatTune tune = current_matrix_tuning();
   auto run = [&]() -> kf_status {
@@ -376,6 +409,8 @@ kf_status kf_plan_execute(const kf_plan* p, void* const* bindings, int n_binding
                           void* stream) {
   if (p == nullptr || (n_bindings > 0 && bindings == nullptr)) return err(KF_ERR_INVALID_ARG, "null argument");
   if (n_bindings < p->nvars) return err(KF_ERR_INVALID_ARG, "every script variable needs a binding");
+  kf_status chk = check_plan(p->p, bindings, n_bindings, ws, ws_bytes);
+  if (chk != KF_OK) return chk;
   const MatTune tune = current_matrix_tuning();
   for (const Kernel& K : p->p.kernels) {
     kf_status st = launch_kernel(K, bindings, n_bindings, ws, ws_bytes, stream, tune);
@@ -401,6 +436,8 @@ kf_status kf_autotune_plan(const kf_plan* p, void* const* bindings, int n_bindin
                            void* stream, int reps, float* tuned_ms, float* auto_ms) {
   if (p == nullptr || reps <= 0 || (n_bindings > 0 && bindings == nullptr)) return err(KF_ERR_INVALID_ARG, "bad arguments");
   if (n_bindings < p->nvars) return err(KF_ERR_INVALID_ARG, "every script variable needs a binding");
+  kf_status chk = check_plan(p->p, bindings, n_bindings, ws, ws_bytes);
+  if (chk != KF_OK) return chk;
   float tsum = 0.f, asum = 0.f;
   for (const Kernel& K : p->p.kernels) {
     float bm = 0.f, am = 0.f;

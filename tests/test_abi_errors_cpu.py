@@ -140,3 +140,75 @@ def test_empty_problems_return_before_any_launch(L, K):
     assert L.kf_waxpby(0, 1.0, None, 1.0, None, None, None) == K.KF_OK
     assert L.kf_ger(0, 4, None, 4, 1.0, None, P, None, 4, None) == K.KF_OK
     assert L.kf_madd(3, 0, None, 0, None, 0, None, 0, None) == K.KF_OK
+
+
+def _exec(L, plan, binds, ws, ws_bytes):
+    arr = (ctypes.c_void_p * len(binds))(*binds)
+    return L.kf_plan_execute(plan.h, arr, len(binds), ws, ws_bytes, None)
+
+
+def test_plan_execute_checks_every_kernel_before_launching(L, K):
+    """A binding missing only from a later kernel, or a workspace that only a
+    later kernel needs, is refused before the first kernel launches."""
+    import torch
+    from test_planner_cpu import gemver
+    s = gemver(K, 40)
+    p = s.plan(K.KF_PLAN_ANALYTIC)
+    assert p.kernel_count() == 2                     # {GER, GER, GEMVT, AXPBY}, then {GEMV}
+    binds = [P] * len(s.ids)
+    binds[s.ids["w"]] = None                         # read only by the second kernel
+    assert _exec(L, p, binds, Q, p.workspace_size()) == K.KF_ERR_INVALID_ARG
+    assert b"not bound" in L.kf_last_error()
+    g = K.Script()                                   # GER (no workspace), then GEMV (needs one)
+    g.matrix("A", 32, 32); g.matrix("B", 32, 32)
+    for v in ("u", "v", "x", "y"):
+        g.vector(v, 32)
+    g.input("A", "u", "v", "x"); g.output("B", "y")
+    g.call("GER", ["B"], ["A", "u", "v"], [1.0])
+    g.call("GEMV", ["y"], ["B", "x"], [1.0, 0.0])
+    up = g.plan(K.KF_PLAN_UNFUSED)
+    assert up.kernel_count() == 2
+    binds = [P] * len(g.ids)
+    assert _exec(L, up, binds, None, 0) == K.KF_ERR_WORKSPACE
+    assert _exec(L, up, binds, Q, 1024) == K.KF_ERR_WORKSPACE        # below the matrix pass's region
+    if torch.cuda.is_available():
+        return                                       # below, the checks pass and a launch would follow
+    # with everything bound and the plan's workspace, every plan passes the
+    # checks (here the launch itself then fails: there is no device)
+    for sc in (s, g):
+        for i in range(sc.count_plans()[0]):
+            pl = sc.plan(K.KF_PLAN_INDEX, index=i)
+            st = _exec(L, pl, [P] * len(sc.ids), Q, pl.workspace_size())
+            assert st not in (K.KF_ERR_INVALID_ARG, K.KF_ERR_WORKSPACE), (i, st, L.kf_last_error())
+
+
+def test_plan_checks_accept_every_valid_plan(L, K):
+    """Every plan of 150 random valid scripts, fully bound and given its
+    reported workspace, passes the up-front checks (the launch that follows
+    fails here, with no device)."""
+    import random
+
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("the checks pass, so a launch on stand-in addresses would follow")
+    from test_planner_cpu import _random_valid_script
+    rng = random.Random(77)
+    checked = 0
+    for _ in range(150):
+        n = rng.choice([1, 7, 64])
+        m = rng.choice([n, 5])
+        kinds, inputs, calls = _random_valid_script(rng, n, m)
+        s = K.Script()
+        for nm, kd in kinds.items():
+            (s.vector(nm, n) if kd == "x" else s.vector(nm, m) if kd == "y" else
+             s.matrix(nm, m, n) if kd == "A" else s.scalar(nm))
+        s.input(*inputs)
+        s.output(*sorted({c[1][0] for c in calls}))
+        for op, outs, ins, sc in calls:
+            s.call(op, outs, ins, sc)
+        for i in range(min(s.count_plans(cap=50)[0], 50)):
+            pl = s.plan(K.KF_PLAN_INDEX, index=i, max_plans=50)
+            st = _exec(L, pl, [P] * len(s.ids), Q, pl.workspace_size())
+            assert st not in (K.KF_ERR_INVALID_ARG, K.KF_ERR_WORKSPACE), (calls, i, L.kf_last_error())
+            checked += 1
+    assert checked > 500
