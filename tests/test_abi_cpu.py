@@ -70,3 +70,31 @@ def test_binding_constants_match_the_header(kf):
     assert len(seqs) >= 9
     for name, v in seqs:
         assert getattr(kf, name) == int(v), name
+
+
+def test_header_is_plain_c_and_links(kf, tmp_path):
+    """include/kf.h compiles as strict C99 (no C++ or torch types), and a C
+    program that takes the address of every declared function links
+    against the library and runs (kf_version needs no device)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    names = declared_functions()
+    src = tmp_path / "use_all.c"
+    src.write_text('#include "kf.h"\n#include <stdio.h>\nint main(void) {\n'
+                   "  typedef void (*fnp)(void);\n  const fnp fns[] = {\n"
+                   + "".join(f"    (fnp)&{n},\n" for n in names)
+                   + '  };\n  printf("%s|%d\\n", kf_version(), (int)(sizeof(fns) / sizeof(fns[0])));\n'
+                   "  return 0;\n}\n")
+    libdir = os.path.dirname(kf.library_path())
+    exe = tmp_path / "use_all"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I" + os.path.join(ROOT, "include"), str(src), "-L" + libdir, "-lkf",
+                        "-Wl,-rpath," + libdir, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    version, count = out.stdout.strip().split("|")
+    assert version == kf.kf_version() and int(count) == len(names)
