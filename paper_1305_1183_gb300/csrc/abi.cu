@@ -306,9 +306,6 @@ kf_status kf_gemver_q(int64_t n, const void* QA, int64_t lda, kf_dtype fmt, cons
   REQ(ws != nullptr && ws_bytes >= WS_HEADER, KF_ERR_WORKSPACE, "workspace required");
   // max |v1|, max |v2| for the row-scale bound, in the workspace header
   float* norms = reinterpret_cast<float*>(static_cast<char*>(ws) + WS_AUX);
-  const float* vs[2] = {v1, v2};
-  const char* why = nullptr;
-  CHK(from_launch(launch_colnorms(vs, 2, n, norms, stream, &why), why));
   // Pass 1: B = Ahat + u1 v1^T + u2 v2^T stored as codes + row scales,
   // x = beta Bhat^T y + z.
   MatProg P = new_prog(n, n);
@@ -321,6 +318,15 @@ kf_status kf_gemver_q(int64_t n, const void* QA, int64_t lda, kf_dtype fmt, cons
   P.nrow_res = 1; P.ncol_res = 1;
   P.ncol_out = 1; P.col_out[0] = epi1(x, beta);
   epi_add_ext(P.col_out[0], z, 1.f);
+  {
+    // the passes' workspace rule, checked before the norm pre-pass is enqueued
+    MatProg chk = P;
+    if (matprog_bind_workspace(chk, ws, ws_bytes) != 0)
+      return fail(KF_ERR_WORKSPACE, "workspace missing or smaller than kf_workspace_size()");
+  }
+  const float* vs[2] = {v1, v2};
+  const char* why = nullptr;
+  CHK(from_launch(launch_colnorms(vs, 2, n, norms, stream, &why), why));
   CHK(run_mat(P, ws, ws_bytes, stream));
   // Pass 2: w = alpha Bhat x.
   MatProg Q = new_prog(n, n);

@@ -65,6 +65,10 @@ def test_gemver_q_errors(L, K):
     assert call(lda=n - 1) == K.KF_ERR_SHAPE
     assert call(fmt=E4M3) == K.KF_ERR_WORKSPACE
     assert call(fmt=E4M3, ws=Q, wsb=16) == K.KF_ERR_WORKSPACE        # below the header
+    # above the header but short of the passes' partial sums: refused before
+    # the norm pre-pass is enqueued
+    assert call(fmt=E4M3, ws=Q, wsb=4096) == K.KF_ERR_WORKSPACE
+    assert b"kf_workspace_size" in L.kf_last_error()
 
 
 def test_gesummv_atax_errors(L, K):
