@@ -547,3 +547,21 @@ def test_hand_worked_examples():
     close(z, c["z"]); close(r, c["r"])
     c = g["waxpby"]
     close(oracle.waxpby(c["alpha"], c["x"], c["beta"], c["y"]), c["w"])
+
+
+def test_hand_worked_quantisation():
+    """The quantiser reproduces row codes worked by hand from the BF16 and
+    E4M3 format definitions (tests/golden/hand_examples.txt)."""
+    g = _golden()
+    for name, fmt in (("quantize_e4m3", oracle.FMT_E4M3), ("quantize_e4m3_rounding", oracle.FMT_E4M3),
+                      ("quantize_bf16", oracle.FMT_BF16)):
+        c = g[name]
+        A = np.atleast_2d(c["A"]).astype(np.float32)
+        codes, scale = oracle.quantize_rows(A, fmt)
+        assert np.array_equal(codes.astype(np.int64), np.atleast_2d(c["codes"]).astype(np.int64)), name
+        if "s" in c:
+            assert scale[0] == np.float32(c["s"]), name
+    _, scale = oracle.quantize_rows(np.atleast_2d(g["quantize_e4m3_rounding"]["A"]).astype(np.float32),
+                                    oracle.FMT_E4M3)
+    assert scale[0] == np.float32(1) / np.float32(448) and scale[1] == 1.0
+
