@@ -565,3 +565,17 @@ def test_hand_worked_quantisation():
                                     oracle.FMT_E4M3)
     assert scale[0] == np.float32(1) / np.float32(448) and scale[1] == 1.0
 
+
+def test_hand_worked_rowscaled_gemver_storage():
+    """The row-scaled GEMVER storage rule reproduces codes and scales worked
+    by hand (tests/golden/hand_examples.txt): sB_i = bound_i / QMAX and the
+    codes of B = Ahat + u1 v1^T + u2 v2^T."""
+    c = _golden()["gemver_rowscaled_e4m3"]
+    QA = c["QA"].astype(np.uint8)
+    vec = {k: c[k] for k in ("u1", "v1", "u2", "v2")}
+    QB, sB, _, _, _ = oracle.gemver_rowscaled(QA, c["sA"], oracle.FMT_E4M3, vec["u1"], vec["v1"], vec["u2"],
+                                              vec["v2"], np.ones(2), np.zeros(2), 1.5, 1.2)
+    assert np.array_equal(QB.astype(np.int64), c["QB"].astype(np.int64))
+    for i in range(2):
+        assert sB[i] == np.float32(c["bound"][i]) / np.float32(448)
+
