@@ -112,7 +112,7 @@ C_MUTANTS = [
      [P("test_waxpby_cases")]),
     ("bf16_truncates", "static uint16_t f32_to_bf16_rne(",
      "u += 0x7FFFu + lsb;", "u += 0u * lsb;",
-     [P("test_bf16_codes_match_round_to_nearest_even")]),
+     [P("test_bf16_codes_match_round_to_nearest_even"), P("test_hand_worked_quantisation")]),
     ("bf16_ties_away_from_zero", "static uint16_t f32_to_bf16_rne(",
      "u += 0x7FFFu + lsb;", "u += 0x8000u + 0u * lsb;",
      [P("test_bf16_codes_match_round_to_nearest_even")]),
@@ -130,21 +130,25 @@ C_MUTANTS = [
      [P("test_e4m3_format_definition"), P("test_e4m3_matches_torch_in_range")]),
     ("row_scale_ignores_qmax", "void kfo_quantize_rows(",
      "const float qmax = (fmt == 2) ? 448.0f : 1.0f;", "const float qmax = 1.0f;",
-     [P("test_quantize_error_bound", E4M3, 2 ** -4), P("test_quantize_exact_rows_are_lossless", E4M3)]),
+     [P("test_quantize_error_bound", E4M3, 2 ** -4), P("test_quantize_exact_rows_are_lossless", E4M3),
+      P("test_hand_worked_quantisation")]),
     ("row_scale_from_the_first_element", "void kfo_quantize_rows(",
      "if (a > amax) amax = a;", "if (j == 0) amax = a;",
-     [P("test_quantize_error_bound", BF16, 2 ** -8), P("test_quantize_error_bound", E4M3, 2 ** -4)]),
+     [P("test_quantize_error_bound", BF16, 2 ** -8), P("test_quantize_error_bound", E4M3, 2 ** -4),
+      P("test_hand_worked_quantisation")]),
     ("dequantize_with_row_0_scale", "void kfo_dequantize_rows(",
      "Ahat[i * n + j] = (double)scale[i] * q;", "Ahat[i * n + j] = (double)scale[0] * q;",
      [P("test_quantize_error_bound", BF16, 2 ** -8), P("test_quantize_error_bound", E4M3, 2 ** -4)]),
     ("stored_gemver_bound_drops_u2", "void kfo_gemver_rowscaled_store(",
      "bound = bound + fabsf(u2[i]) * n2;", "bound = bound + 0.0f * n2;",
      [P("test_gemver_rowscaled_storage_bound", BF16, 2.0 ** -8, 2.0 ** -126, 64.0),
-      P("test_gemver_rowscaled_storage_bound", E4M3, 2.0 ** -4, 2.0 ** -6, 64.0)]),
+      P("test_gemver_rowscaled_storage_bound", E4M3, 2.0 ** -4, 2.0 ** -6, 64.0),
+      P("test_hand_worked_rowscaled_gemver_storage")]),
     ("stored_gemver_updates_mixed", "void kfo_gemver_rowscaled_store(",
      "fmaf(u2[i], v2[j], fmaf(u1[i], v1[j], a))", "fmaf(u1[i], v2[j], fmaf(u2[i], v1[j], a))",
      [P("test_gemver_rowscaled_storage_bound", BF16, 2.0 ** -8, 2.0 ** -126, 1.0),
-      P("test_gemver_rowscaled_storage_bound", E4M3, 2.0 ** -4, 2.0 ** -6, 1.0)]),
+      P("test_gemver_rowscaled_storage_bound", E4M3, 2.0 ** -4, 2.0 ** -6, 1.0),
+      P("test_hand_worked_rowscaled_gemver_storage")]),
 ]
 
 # Python oracles: (id, module, old, new, pins); ``old`` must occur once in the module.
