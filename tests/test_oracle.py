@@ -508,6 +508,24 @@ def test_generator_grid_range_and_subsets():
     assert abs(float(ls.mean()) - (np.log(32) + np.log(2048)) / 2) < 0.1
 
 
+def test_generator_is_splitmix64():
+    """Element i of a tensor is output i of a SplitMix64 stream seeded with
+    the tensor's key: the stream seeded with 0 gives the published first
+    outputs, and the int64 tensor path equals the integer path."""
+    published = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    state = [synth._s64((synth.GAMMA * (i + 1)) & synth.MASK64) for i in range(4)]
+    got = synth._mix_t(torch.tensor(state, dtype=torch.int64))
+    assert [int(v) & synth.MASK64 for v in got] == published
+    assert [synth._mix_int((synth.GAMMA * (i + 1)) & synth.MASK64) for i in range(4)] == published
+    k = synth.key(7, synth.TID["A"])
+    idx = torch.tensor([0, 1, 2, 12345])
+    b = synth.bits(7, synth.TID["A"], idx)
+    for j, i in enumerate(idx.tolist()):
+        want = synth._mix_int((k + (i + 1) * synth.GAMMA) & synth.MASK64)
+        assert int(b[j]) & synth.MASK64 == want
+        assert float(synth.uniform_at(7, synth.TID["A"], idx)[j]) == (want >> 40) * 2.0 ** -23 - 1.0
+
+
 # ------------------------------------------------------------------ hand-worked examples
 
 def _golden():
