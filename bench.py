@@ -86,8 +86,8 @@ def unfused_bytes(seq: str, size) -> int:
         m, n = size
         return f * (2 * m * n + 2 * (m + n))
     if seq == "gemver":
-        n = size
-        return f * (6 * n * n + 14 * n)
+        n = size                                     # GER, GER in place, GEMVT, AXPBY, GEMV
+        return f * (6 * n * n + 11 * n)
     if seq == "gesummv":
         n = size
         return f * (2 * n * n + 7 * n)
@@ -95,7 +95,7 @@ def unfused_bytes(seq: str, size) -> int:
         m, n = size
         return f * (2 * m * n + 2 * n + 2 * m)
     if seq == "axpydot":
-        return f * (5 * size)
+        return f * (5 * size + 1)                    # AXPBY (w, v in; z out), DOT (z, u in; r out)
     if seq == "waxpby":
         return f * 5 * size
     raise KeyError(seq)

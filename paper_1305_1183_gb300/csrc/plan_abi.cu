@@ -384,6 +384,7 @@ kf_status kf_plan_features(const kf_script* s, const kf_plan* p, float* out, int
 kf_status kf_plan_describe(const kf_plan* p, char* buf, size_t cap, size_t* needed) {
   if (p == nullptr) return err(KF_ERR_INVALID_ARG, "null plan");
   std::ostringstream o;
+  o.precision(17);  // byte counts and predictions round-trip exactly
   o << "{\"predicted_us\":" << p->p.predicted_us << ",\"bytes\":" << p->p.bytes << ",\"kernels\":[";
   for (size_t i = 0; i < p->p.kernels.size(); ++i) {
     const Kernel& K = p->p.kernels[i];
