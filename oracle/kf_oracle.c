@@ -213,13 +213,13 @@ static uint8_t f32_to_e4m3_rne_sat(float xf) {
         return (uint8_t)(sign | (uint8_t)k);
     }
     int e;
-    double fr = frexp(x, &e);          /* x = fr * 2^e, fr in [0.5, 1) */
+    (void)frexp(x, &e);                /* x = fr * 2^e, fr in [0.5, 1) */
     int E = e - 1;                     /* x = 1.f * 2^E, E in [-6, 8] */
     double quantum = ldexp(1.0, E - 3);
     double q = rint(x / quantum) * quantum;
     if (q >= 448.0) return (uint8_t)(sign | 0x7E);
     /* q may have rounded up to 2^(E+1): re-derive exponent and mantissa */
-    fr = frexp(q, &e);
+    (void)frexp(q, &e);
     E = e - 1;
     int mant = (int)rint((q / ldexp(1.0, E) - 1.0) * 8.0);   /* 0..7 */
     int ebits = E + 7;
