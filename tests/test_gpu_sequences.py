@@ -10,7 +10,7 @@ import torch
 
 import oracle
 from gpu_util import ALPHA, BETA, I, U, built, dev, host  # noqa: F401
-from tolerance import EPS32, check_map, check_reduce
+from tolerance import check_map, check_reduce
 
 pytestmark = pytest.mark.gpu
 

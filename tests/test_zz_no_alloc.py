@@ -12,8 +12,6 @@ second call catches state left over from the first (the array keeps it).
 The file is named so that pytest collects it last.
 """
 
-import ctypes
-
 import numpy as np
 import pytest
 import torch
