@@ -216,3 +216,27 @@ def test_plan_checks_accept_every_valid_plan(L, K):
             assert st not in (K.KF_ERR_INVALID_ARG, K.KF_ERR_WORKSPACE), (calls, i, L.kf_last_error())
             checked += 1
     assert checked > 500
+
+
+def test_last_error_is_per_thread(L, K):
+    """Each thread reads the message of its own last failed call."""
+    import threading
+    results = {}
+    barrier = threading.Barrier(2)
+
+    def worker(name, call, expect):
+        barrier.wait()
+        for _ in range(200):
+            assert call() != K.KF_OK
+            msg = L.kf_last_error()
+            if expect not in msg:
+                results[name] = msg
+                return
+        results[name] = "ok"
+
+    a = threading.Thread(target=worker, args=("a", lambda: L.kf_waxpby(-1, 1.0, P, 1.0, P, Q, None),
+                                               b"negative size"))
+    b = threading.Thread(target=worker, args=("b", lambda: L.kf_waxpby(8, 1.0, None, 1.0, P, Q, None),
+                                               b"null vector x"))
+    a.start(); b.start(); a.join(); b.join()
+    assert results == {"a": "ok", "b": "ok"}, results
