@@ -240,3 +240,26 @@ def test_last_error_is_per_thread(L, K):
                                                b"null vector x"))
     a.start(); b.start(); a.join(); b.join()
     assert results == {"a": "ok", "b": "ok"}, results
+
+
+def test_mlp_entry_point_errors(L, K):
+    """The cost model's network: 64 hidden units, 1..32 inputs; parameter
+    count H d + H + H H + H + H + 1; bad sizes, missing operands and a short
+    workspace are refused before any launch."""
+    c = ctypes.c_int(0)
+    assert L.kf_mlp_param_count(16, 64, ctypes.byref(c)) == K.KF_OK
+    assert c.value == 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+    for d, h in ((16, 32), (0, 64), (33, 64)):
+        assert L.kf_mlp_param_count(d, h, ctypes.byref(c)) == K.KF_ERR_INVALID_ARG
+    b = ctypes.c_size_t(0)
+    assert L.kf_mlp_workspace_size(16, 64, -1, ctypes.byref(b)) == K.KF_ERR_INVALID_ARG
+    assert L.kf_mlp_workspace_size(16, 64, 1000, ctypes.byref(b)) == K.KF_OK and b.value > 0
+    assert L.kf_mlp_forward(P, 16, 64, P, 10, None, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_mlp_forward(P, 16, 64, P, 0, None, None) == K.KF_OK            # empty batch
+    assert L.kf_mlp_loss_grad(P, 16, 64, P, P, 0, Q, None, None, 0, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_mlp_loss_grad(P, 16, 64, P, P, 10, None, None, None, 0, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_mlp_loss_grad(P, 16, 64, P, P, 10, Q, None, None, 0, None) == K.KF_ERR_WORKSPACE
+    assert L.kf_mlp_loss_grad(P, 16, 64, P, P, 10, Q, None, Q, b.value // 1000, None) == K.KF_ERR_WORKSPACE
+    assert L.kf_mlp_adam(P, P, Q, Q, 100, 0, 1e-3, 0.9, 0.999, 1e-8, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_mlp_adam(P, P, Q, Q, 0, 1, 1e-3, 0.9, 0.999, 1e-8, None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_mlp_adam(P, None, Q, Q, 100, 1, 1e-3, 0.9, 0.999, 1e-8, None) == K.KF_ERR_INVALID_ARG
