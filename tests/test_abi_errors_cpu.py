@@ -263,3 +263,52 @@ def test_mlp_entry_point_errors(L, K):
     assert L.kf_mlp_adam(P, P, Q, Q, 100, 0, 1e-3, 0.9, 0.999, 1e-8, None) == K.KF_ERR_INVALID_ARG
     assert L.kf_mlp_adam(P, P, Q, Q, 0, 1, 1e-3, 0.9, 0.999, 1e-8, None) == K.KF_ERR_INVALID_ARG
     assert L.kf_mlp_adam(P, None, Q, Q, 100, 1, 1e-3, 0.9, 0.999, 1e-8, None) == K.KF_ERR_INVALID_ARG
+
+
+def test_script_and_plan_api_errors(L, K):
+    """Bad variable ids and operand counts are refused when the script is
+    validated (KF_ERR_SHAPE); null handles are KF_ERR_INVALID_ARG; a short
+    description buffer gets a truncated, terminated string and the size
+    needed."""
+    def script():
+        h = ctypes.c_void_p()
+        assert L.kf_script_create(ctypes.byref(h)) == K.KF_OK
+        i = ctypes.c_int()
+        for nm in (b"x", b"y"):
+            assert L.kf_script_vector(h, nm, 8, ctypes.byref(i)) == K.KF_OK
+        assert L.kf_script_input(h, 0) == K.KF_OK
+        return h
+
+    for outs, ins, msg in (([99], [0, 1], b"out of range"), ([1], [-3, 0], b"out of range"),
+                           ([1], [0], b"AXPBY"), ([1], [0, 0, 0, 0], b"AXPBY"), ([], [0, 1], b"exactly one output")):
+        h = script()
+        o = (ctypes.c_int * max(1, len(outs)))(*outs)
+        n = (ctypes.c_int * len(ins))(*ins)
+        assert L.kf_script_call(h, K.KF_OP_AXPBY, o, len(outs), n, len(ins), None, 0) == K.KF_OK
+        assert L.kf_script_validate(h) == K.KF_ERR_SHAPE
+        assert msg in L.kf_last_error(), (outs, ins, L.kf_last_error())
+        L.kf_script_destroy(h)
+    h = script()
+    i = ctypes.c_int()
+    assert L.kf_script_call(h, 7, (ctypes.c_int * 1)(1), 1, (ctypes.c_int * 2)(0, 1), 2, None, 0) \
+        == K.KF_ERR_INVALID_ARG                                              # unknown op
+    assert L.kf_script_call(h, K.KF_OP_AXPBY, (ctypes.c_int * 1)(1), 1, (ctypes.c_int * 2)(0, 1), 2,
+                            (ctypes.c_double * 3)(1, 2, 3), 3) == K.KF_ERR_INVALID_ARG   # three scalars
+    assert L.kf_script_vector(h, b"z", -1, ctypes.byref(i)) == K.KF_ERR_INVALID_ARG
+    assert L.kf_script_input(h, 42) == K.KF_ERR_INVALID_ARG
+    assert L.kf_script_output(h, -1) == K.KF_ERR_INVALID_ARG
+    L.kf_script_destroy(h)
+    assert L.kf_script_vector(None, b"x", 8, ctypes.byref(i)) == K.KF_ERR_INVALID_ARG
+    assert L.kf_script_validate(None) == K.KF_ERR_INVALID_ARG
+    need = ctypes.c_size_t(0)
+    assert L.kf_plan_describe(None, None, 0, ctypes.byref(need)) == K.KF_ERR_INVALID_ARG
+    assert L.kf_plan_execute(None, None, 0, None, 0, None) == K.KF_ERR_INVALID_ARG
+    from test_planner_cpu import bicgk
+    p = bicgk(K).plan(K.KF_PLAN_ANALYTIC)
+    assert L.kf_plan_describe(p.h, None, 0, ctypes.byref(need)) == K.KF_OK and need.value > 20
+    buf = ctypes.create_string_buffer(b"#" * 16, 16)
+    assert L.kf_plan_describe(p.h, buf, 16, ctypes.byref(need)) == K.KF_OK
+    assert len(buf.value) == 15 and buf.raw[15] == 0
+    full = ctypes.create_string_buffer(need.value)
+    assert L.kf_plan_describe(p.h, full, need.value, ctypes.byref(need)) == K.KF_OK
+    assert full.value.startswith(buf.value) and len(full.value) == need.value - 1
