@@ -98,3 +98,27 @@ def test_header_is_plain_c_and_links(kf, tmp_path):
     assert out.returncode == 0, out.stderr
     version, count = out.stdout.strip().split("|")
     assert version == kf.kf_version() and int(count) == len(names)
+
+
+def test_readme_c_example_compiles_and_links(kf, tmp_path):
+    """The C example in README.md builds against the header, the CUDA
+    runtime and the library (it runs only on a GPU)."""
+    import re
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if gcc is None or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("no C compiler or CUDA headers")
+    block = re.search(r"```c\n(.*?)```", open(os.path.join(ROOT, "README.md")).read(), flags=re.S)
+    assert block, "README has no C example"
+    src = tmp_path / "example.c"
+    src.write_text(block.group(1) + "\nint main(void) { return 0; }\n")
+    libdir = os.path.dirname(kf.library_path())
+    cudalib = next((d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"))
+                    if os.path.exists(d)), None)
+    cmd = [gcc, "-std=c99", "-Wall", "-Werror", "-I" + os.path.join(ROOT, "include"),
+           "-I" + os.path.join(cuda, "include"), str(src), "-L" + libdir, "-lkf", "-L" + cudalib, "-lcudart",
+           "-o", str(tmp_path / "example")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
