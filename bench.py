@@ -582,6 +582,21 @@ def time_calls(fn, steps, warmup, st):
     return a.elapsed_time(b) / steps
 
 
+def read_probe_section(kf, suite, sizes, steps, warmup, st):
+    """A read-only probe: the library's own dot product over two of the
+    suite's long vectors (each read once, one float written), the call the
+    unfused AXPYDOT chain makes, timed on its own like the sequences.  A
+    failure is reported in the result; the other measurements stand."""
+    pb = suite.axpydot
+    n = sizes["axpydot"]
+    try:
+        ms = time_calls(lambda s: kf.kf_dot(pb["w"], pb["v"], pb["r"], pb["ws"], stream=s), steps, warmup, st)
+        return {"gbs": (8 * n + 4) / (ms * 1e-3) / 1e9, "ms": ms, "bytes_per_launch": 8 * n + 4,
+                "kernel": f"vecprog via kf_dot: x . y over two vectors of {n} floats (reads only)"}
+    except Exception as e:
+        return {"error": str(e)[:200]}
+
+
 def rel_diff(a, b):
     """max |a - b| / max |b| (normwise difference of a result from the FP32 path's)."""
     return float((a.double() - b.double()).abs().max() / b.double().abs().max().clamp_min(1e-300))
@@ -930,6 +945,8 @@ def main():
     if not args.no_unfused:
         unf_total, unf_per = time_suite(suite, "unfused", args.steps, args.warmup, st, seqs)
 
+    read_probe = read_probe_section(kf, suite, sizes, args.steps, args.warmup, st) if "axpydot" in seqs else None
+
     extra = {}
     if not args.no_cublas:
         extra["cublas_chain"] = cublas_section(suite, st, args.steps, args.warmup, seqs, per)
@@ -977,6 +994,9 @@ def main():
             "kernel": "matprog_kernel (BiCGK q=Ap, s=A^T r, one pass over A)",
             "algorithmic_bytes_per_launch": dom_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    if read_probe is not None and "gbs" in read_probe:
+        roof["read_probe_gbs"] = read_probe["gbs"]
+        roof["frac_of_read_probe"] = achieved / read_probe["gbs"]
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -1001,6 +1021,8 @@ def main():
         "clocks": clk,
         "gpu_launches": args.steps * sum(Suite.FUSED_LAUNCHES[s] for s in seqs),
     }
+    if read_probe is not None:
+        line["read_probe"] = read_probe
     if not args.no_e2e:
         line["e2e"] = {"value": job_gbs(world, step_bytes, e2e_ms / e2e_steps), "unit": "GB/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -71,3 +71,34 @@ def test_planner_byte_counts_agree_with_the_bench(kf, seq):
         assert bench.algorithmic_bytes(seq, size) == pytest.approx(fused / 2, rel=1e-3)
     else:
         assert fused == bench.algorithmic_bytes(seq, size)
+
+
+def test_read_probe_section(monkeypatch):
+    """The read-only probe times kf_dot over the AXPYDOT vectors and reports
+    (8n + 4) bytes per launch; an error becomes an entry, not a crash."""
+    calls = []
+
+    class FakeKF:
+        @staticmethod
+        def kf_dot(x, y, out, ws, stream=None):
+            calls.append((x, y, out, ws, stream))
+
+    def fake_time(fn, steps, warmup, st):
+        fn(st)
+        return 0.25                                     # ms
+
+    class FakeSuite:
+        axpydot = {"w": "W", "v": "V", "r": "R", "ws": "WS", "u": "U", "z": "Z"}
+
+    monkeypatch.setattr(bench, "time_calls", fake_time)
+    n = 1 << 26
+    r = bench.read_probe_section(FakeKF, FakeSuite, {"axpydot": n}, 5, 3, "ST")
+    assert calls == [("W", "V", "R", "WS", "ST")]
+    assert r["bytes_per_launch"] == 8 * n + 4 and r["ms"] == 0.25
+    assert r["gbs"] == pytest.approx((8 * n + 4) / 0.25e-3 / 1e9)
+
+    def failing_time(fn, steps, warmup, st):
+        raise RuntimeError("no device")
+
+    monkeypatch.setattr(bench, "time_calls", failing_time)
+    assert bench.read_probe_section(FakeKF, FakeSuite, {"axpydot": n}, 5, 3, "ST") == {"error": "no device"}
