@@ -11,8 +11,9 @@ at least once: matrices read/written once, vectors once) / device time, in
 GB/s.  Beside it: per-sequence GB/s and fraction of the measured HBM copy
 bandwidth, the unfused per-call kernel chain on the same GPU and its speedup,
 the same sequences as cuBLAS call chains (context: the paper's comparison
-system), the dominant kernel's roofline, an end-to-end number through host
-buffers, the row-scaled BF16 / E4M3 forms, the batched form, and the FP64
+system), the dominant kernel's roofline (against the measured copy, and
+against a read-only probe of the library's own dot product), an end-to-end
+number through host buffers, the row-scaled BF16 / E4M3 forms, the batched form, and the FP64
 CPU oracle's throughput on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
