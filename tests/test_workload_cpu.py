@@ -126,3 +126,35 @@ def test_timing_table_round_trip_and_key(learn, tmp_path):
         assert learn.load_timings(path, other) is None
     assert learn.load_timings(str(tmp_path / "none.npz"), key) is None
     assert learn.load_timings("", key) is None
+
+
+def test_run_resumes_from_a_stored_timing_table(learn, tmp_path, monkeypatch):
+    """With a timings path, the first run collects and stores the training
+    table and a second run with the same key loads it instead of timing
+    plans again (the GPU stages are replaced by fakes here)."""
+    collected = []
+
+    def fake_collect(seed, indices, kmin, kmax, per_script, reps, cap=2000, device="cuda"):
+        collected.append(list(indices))
+        X = np.arange(32, dtype=np.float64).reshape(2, 16)
+        return X, np.array([0.5, 0.7]), np.array([400.0, 600.0]), np.array([0, 1]), [{"index": 0}]
+
+    seen = []
+
+    def fake_train(X, ms, pu, sid, analytic_weight, epochs=0, seed=0, device="cpu"):
+        seen.append((X.copy(), ms.copy()))
+        return None, [(1, 0.5)]
+
+    row = {"plans": 3, "timed_topk": 3, "timed_margin": 5}
+    row.update({k: 1.0 for k in ("mlp", "mlp_topk", "mlp_top2k", "mlp_margin", "analytic", "greedy", "unfused")})
+    monkeypatch.setattr(learn, "collect", fake_collect)
+    monkeypatch.setattr(learn, "train", fake_train)
+    monkeypatch.setattr(learn, "evaluate", lambda *a, **k: [dict(row)])
+    path = str(tmp_path / "t.npz")
+    out1, _ = learn.run(seed=3, scripts=4, ntrain=2, device="cpu", log=None, timings=path)
+    out2, _ = learn.run(seed=3, scripts=4, ntrain=2, device="cpu", log=None, timings=path)
+    assert (out1["train_timings"], out2["train_timings"]) == ("measured", "loaded")
+    assert collected == [[0, 1]]
+    assert np.array_equal(seen[0][0], seen[1][0]) and np.array_equal(seen[0][1], seen[1][1])
+    out3, _ = learn.run(seed=4, scripts=4, ntrain=2, device="cpu", log=None, timings=path)
+    assert out3["train_timings"] == "measured" and len(collected) == 2     # another seed: timed again
