@@ -103,6 +103,32 @@ kf_status kf_workspace_init(void* ws, size_t bytes, void* stream);
  * an earlier call on this workspace ran out, KF_OK otherwise. */
 kf_status kf_workspace_status(void* ws, void* stream);
 
+/* Bound of every kernel wait on data (not in the paper: its kernels wait on
+ * nothing but kernel boundaries).  The staged matrix pass and ATAX wait for
+ * bulk asynchronous copies on mbarriers; each such wait gives up after
+ * limit_ns (default 1 s), after which the block records the timeout in the
+ * workspace's error word (kf_workspace_status reports KF_ERR_DEVICE_TIMEOUT),
+ * lets the copies already in flight land within the default bound, and
+ * returns, so the context stays usable.  Process-wide; applies to launches
+ * enqueued after the call.  Range KF_WAIT_LIMIT_MIN_NS..KF_WAIT_LIMIT_MAX_NS,
+ * else KF_ERR_INVALID_ARG.  A limit shorter than a copy's latency makes
+ * waits run out on healthy copies (wrong results, reported by the status). */
+#define KF_WAIT_LIMIT_MIN_NS ((uint64_t)1000)
+#define KF_WAIT_LIMIT_MAX_NS ((uint64_t)60000000000ull)
+kf_status kf_set_wait_limit_ns(uint64_t limit_ns);
+kf_status kf_get_wait_limit_ns(uint64_t* limit_ns);
+
+/* Probe of the timeout path shared by every bounded wait (a diagnostic, not
+ * in the paper): one thread of one block waits, bounded by limit_ns, on an
+ * mbarrier phase that nothing completes, so the wait runs out; the kernel
+ * then sets the error word at the start of `ws` (>= 256 bytes) and returns.
+ * kf_workspace_status(ws) afterwards reports KF_ERR_DEVICE_TIMEOUT.
+ * waited_ns (device pointer or NULL) receives the nanoseconds the wait took
+ * by the global timer.  Enqueued on `stream`; no fault, trap or unbounded
+ * wait is involved. */
+kf_status kf_wait_probe(uint64_t limit_ns, void* ws, size_t ws_bytes, unsigned long long* waited_ns,
+                        void* stream);
+
 /* ------------------------------------------------------------------------
  * Fused sequences (Table 1 of Section 4.1).  Each is one pass of the fused
  * kernels the planner emits for the canonical script of the sequence.
@@ -517,8 +543,8 @@ kf_status kf_mlp_adam(float* params, const float* grad, float* m, float* v, int 
  * Some callers cannot call cudaMalloc or any allocating routine where they
  * need BiCGK (a framework that forbids allocation while it records work, a
  * host whose device memory belongs to another allocator, a C program with
- * no device allocator).  kf_bicgk_noalloc computes exactly what kf_bicgk
- * computes for FP32 A (q = A p, s = A^T r, one read of A) but takes no
+ * no device allocator).  kf_bicgk_noalloc computes what kf_bicgk computes
+ * for FP32 A (q = A p, s = A^T r, one read of A) but takes no
  * workspace: its scratch is a fixed array of KF_BICGK_NOALLOC_SCRATCH_BYTES
  * in the library's device image, present on every GPU that loads the
  * library until the process exits.  It allocates nothing.
@@ -528,6 +554,13 @@ kf_status kf_mlp_adam(float* params, const float* grad, float* m, float* v, int 
  *     array's device address and caches it; make that first call before any
  *     stream capture.
  *   - Each call clears the array's counters on `stream` before its launch.
+ *   - The kernel shape is the one kf_bicgk takes without a search (a tuning
+ *     fixed by kf_set_matrix_tuning, else the tuning cache's entry, else the
+ *     built-in shape), always in its direct-load form: the bulk-copy ring
+ *     depth of a fixed tuning is ignored, so the launch has no bounded wait
+ *     and no device error word to report.  This call never runs the
+ *     first-use tuning search (kf_set_autotune); results may differ from
+ *     kf_bicgk's in rounding when the two take different kernel shapes.
  *   - All calls on a device share the array: calls that overlap on the GPU
  *     (unordered streams, concurrent threads) race.  Order them on one
  *     stream.

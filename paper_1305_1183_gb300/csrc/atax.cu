@@ -39,7 +39,7 @@ template <int NT, int VA, int RP>
 __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const float* __restrict__ A, int64_t lda, int64_t m,
                                                         int64_t n, const float* __restrict__ x,
                                                         float* __restrict__ ypart, int stages,
-                                                        int64_t rowcap, unsigned* err) {
+                                                        int64_t rowcap, unsigned* err, uint64_t wait_ns) {
   extern __shared__ float4 ring4[];
   float* ring = reinterpret_cast<float*>(ring4);
   __shared__ __align__(8) uint64_t full[ATAX_MAXSTAGES];
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
       const int64_t row = j + rp;
       const bool valid = row < nrows;
       const int s = (int)(row % stages);
-      const bool got = valid ? mbar_wait_bounded(&full[s], (unsigned)((row / stages) & 1)) : true;
+      const bool got = valid ? mbar_wait_bounded(&full[s], (unsigned)((row / stages) & 1), wait_ns) : true;
       ok = ok && got;
       float d0 = 0.f, d1 = 0.f;
       const float4* rowp = reinterpret_cast<const float4*>(ring + s * rowcap);
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
       if (tid == 0) {
         atomicOr(err, KF_DEVERR_TIMEOUT);
         for (int64_t q = j; q < nrows && q < j + stages; ++q)
-          (void)mbar_wait_bounded(&full[q % stages], (unsigned)((q / stages) & 1));
+          (void)mbar_wait_bounded(&full[q % stages], (unsigned)((q / stages) & 1), WAIT_DRAIN_NS);
       }
       __syncthreads();
       return;
@@ -254,8 +254,9 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
   if (ws_bytes < 256 + (size_t)grid * n * sizeof(float)) { *why = "workspace too small"; return -11; }
 
   int nparts = (int)grid;
+  uint64_t wait_ns = wait_limit_ns();
   void* args[] = {(void*)&A, (void*)&lda, (void*)&m, (void*)&n, (void*)&x, (void*)&ypart,
-                  (void*)&stages, (void*)&rowcap, (void*)&err};
+                  (void*)&stages, (void*)&rowcap, (void*)&err, (void*)&wait_ns};
   cudaError_t e = launch_pdl(fn, dim3((unsigned)grid), dim3(512), args, smem, stream);
   if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
 

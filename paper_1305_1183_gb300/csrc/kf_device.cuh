@@ -50,7 +50,14 @@ __device__ __forceinline__ uint64_t global_ns() {
 // One-dimensional bulk asynchronous copies (global -> shared) whose
 // completion is counted in bytes on an mbarrier, and bounded waits on it.
 
-constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;  // every device wait gives up after 1 s
+// Every device wait gives up after a limit: by default 1 s
+// (kf_set_wait_limit_ns changes it for the waits on data, passed to the
+// kernels in their launch parameters).  The waits that let copies already in
+// flight land before a block that gave up exits always use the default, so
+// a short limit never lets a block exit with a copy into its shared memory
+// still pending.
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
+constexpr uint64_t WAIT_DRAIN_NS = 1000000000ull;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -84,12 +91,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Wait for a phase with a wall-clock bound; false if the bound ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+// Wait for a phase with a wall-clock bound of limit_ns; false if the bound
+// ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return true;
 }

@@ -86,6 +86,7 @@ struct MatProg {
   float* colpart;                // [ncol_res][n_groups][n]
   unsigned* counters;            // [n_strips + n_groups], zero between launches
   unsigned* errword;             // device error word (bounded waits that ran out)
+  uint64_t wait_ns;              // bound of every wait on data (set by launch_matprog)
 };
 
 struct VecProg {
@@ -120,6 +121,12 @@ struct VecTune {
 
 // Status codes mirror kf.h.
 int launch_matprog(MatProg& P, const MatTune& t, void* stream, const char** why);
+// The tuning an automatic launch would take without running a search: the
+// fixed tuning when its warps field is set, else the tuning cache's entry for
+// P's op signature and size class, else the built-in tuning.
+MatTune matprog_tuning_nosearch(const MatProg& P, const MatTune& fixed);
+// The matrix tuning fixed by kf_set_matrix_tuning (warps = 0: automatic).
+MatTune current_matrix_tuning();
 // cudaLaunchKernelExC with programmatic stream serialization (the kernel
 // must begin with pdl_enter()).
 cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, void* stream);
@@ -132,5 +139,8 @@ int matprog_bind_workspace(MatProg& P, void* ws, size_t bytes);
 void matprog_geometry(MatProg& P, const MatTune& t, int sm_count, int* threads, size_t* smem);
 
 int device_sm_count();
+
+// Bound of the kernels' waits on data (kf_set_wait_limit_ns; 1 s by default).
+uint64_t wait_limit_ns();
 
 }  // namespace kf

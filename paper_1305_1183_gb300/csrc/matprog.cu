@@ -206,6 +206,27 @@ cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, void** args, size_
 
 int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* best_ms, float* auto_ms);
 
+// Built-in tuning (no cache entry, no search): row-scaled formats keep packed
+// chunks with 8 rows in flight; FP32 BiCGK 8 rows in flight at 3 blocks per
+// SM (measured 4 % faster at 16384^2); the other FP32 passes 4 rows at 4
+// blocks per SM.
+MatTune default_tuning(int fmt, int sig) {
+  if (fmt != FMT_F32 || sig == mp::SIG_BICGK) return MatTune{8, 1, 8, 0, 0};
+  return MatTune{8, 1, 4, 0, 0};
+}
+
+// The tuning an automatic launch of P takes without running a search: the
+// fixed tuning if one is given, else the tuning cache's entry, else the
+// built-in one.
+MatTune matprog_tuning_nosearch(const MatProg& P, const MatTune& fixed) {
+  if (fixed.warps != 0) return fixed;
+  int sig = 0, shape_nops = 0, shape_ng = 0, ngemv = 0;
+  op_shape(P, &sig, &shape_nops, &shape_ng, &ngemv);
+  MatTune t{};
+  if (tune_cache_get_mat(mat_cache_key(P, sig, shape_nops, shape_ng), &t)) return t;
+  return default_tuning(P.fmt, sig);
+}
+
 // Tuning on first use (kf_set_autotune): timed runs per candidate, 0 = off.
 std::atomic<int> g_autotune_reps{0};
 thread_local bool g_in_search = false;
@@ -247,13 +268,7 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
         tuned = autotune_matprog(P, stream, g_autotune_reps.load(), &bt, &bm, nullptr) == 0;
         if (tuned) t = bt;
       }
-      if (!tuned) {
-        // row-scaled formats: packed chunks, 8 rows in flight; FP32 BiCGK:
-        // 8 rows in flight at 3 blocks per SM (measured 4 % faster at
-        // 16384^2), the other FP32 passes 4 rows at 4 blocks per SM
-        if (P.fmt != FMT_F32 || sig == mp::SIG_BICGK) t = MatTune{8, 1, 8, 0, 0};
-        else t = MatTune{8, 1, 4, 0, 0};
-      }
+      if (!tuned) t = default_tuning(P.fmt, sig);
     }
   }
   bool staged = vec && t.stages > 0;
@@ -310,6 +325,7 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   if (strips > 0x7fffffffLL) { *why = "matrix too wide"; return -2; }
   P.n_strips = (int)strips;
   P.n_groups = (int)G;
+  P.wait_ns = wait_limit_ns();
   P.blocks_per_group = bpg;
   P.stages = stages;
   dim3 grid((unsigned)strips, (unsigned)G);
@@ -379,7 +395,7 @@ int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* b
   // the current choice: the cache's entry, else the built-in default
   MatTune cur{};
   if (!tune_cache_get_mat(mat_cache_key(P, sig, shape_nops, shape_ng), &cur))
-    cur = (P.fmt != FMT_F32 || sig == mp::SIG_BICGK) ? MatTune{8, 1, 8, 0, 0} : MatTune{8, 1, 4, 0, 0};
+    cur = default_tuning(P.fmt, sig);
   // warm the GPU (clocks, caches, TLB) with the current choice, then time it
   float am = 1e30f;
   {

@@ -28,9 +28,10 @@
 // engine; one copy per row and matrix) into a ring of shared-memory stages,
 // `stages` batches of U rows ahead; a "full" mbarrier per stage counts the
 // bytes, an "empty" mbarrier per stage counts the consumer warps that have
-// read it.  Every wait is bounded (1 s): on a timeout the block records the
-// error word, stops waiting, lets its in-flight copies land (bounded) and
-// still takes part in the completion counters.
+// read it.  Every wait is bounded (P.wait_ns, 1 s by default): on a timeout
+// the block records the error word, stops waiting, lets its in-flight copies
+// land (bounded by the default 1 s) and still takes part in the completion
+// counters.
 //
 // GEMV is not a dense contraction, so there is nothing for the tensor cores
 // here; the bound is HBM bandwidth.
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
         const int s = (int)(jj % S);
         if (jj >= S) {
           bool ok = false;
-          if (!*(volatile int*)&s_abort) ok = mbar_wait_bounded(&empty[s], (unsigned)(((jj / S) - 1) & 1));
+          if (!*(volatile int*)&s_abort) ok = mbar_wait_bounded(&empty[s], (unsigned)(((jj / S) - 1) & 1), P.wait_ns);
           if (!ok) {
             *(volatile int*)&s_abort = 1;
             if (P.errword != nullptr) atomicOr(P.errword, KF_DEVERR_TIMEOUT);
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
       if (*(volatile int*)&s_abort) {
         // let the copies that may still be in flight land before exiting
         for (int64_t q = issued - S < 0 ? 0 : issued - S; q < issued; ++q)
-          (void)mbar_wait_bounded(&full[q % S], (unsigned)((q / S) & 1));
+          (void)mbar_wait_bounded(&full[q % S], (unsigned)((q / S) & 1), WAIT_DRAIN_NS);
       }
     }
     __syncwarp();  // reconverge the producer warp before the block barrier below
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
       if (ring) {
         const int s = (int)(jj % S);
         bool ok = false;
-        if (!dead && !*(volatile int*)&s_abort) ok = mbar_wait_bounded(&full[s], (unsigned)((jj / S) & 1));
+        if (!dead && !*(volatile int*)&s_abort) ok = mbar_wait_bounded(&full[s], (unsigned)((jj / S) & 1), P.wait_ns);
         ok = __all_sync(FULL_MASK, ok);
         if (!ok && !dead) {
           dead = true;

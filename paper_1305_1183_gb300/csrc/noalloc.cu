@@ -18,9 +18,16 @@
 //   * the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress, with that device current) and caches it; make
 //     that first call before any stream capture;
-//   * every call clears the array's header and counters on `stream` before
+//   * every call clears the array's completion counters on `stream` before
 //     the launch (cudaMemsetAsync), since the array keeps the last call's
 //     contents;
+//   * the matrix pass always takes its direct-load form here (16-byte loads
+//     into registers, no bulk-copy ring), which waits on nothing, so no
+//     bounded wait can run out and there is no device error word to report;
+//   * the kernel shape is the one kf_bicgk would take without a search: a
+//     tuning fixed by kf_set_matrix_tuning (its ring depth ignored), else the
+//     tuning cache's entry, else the built-in shape; this call never runs
+//     the first-use tuning search;
 //   * every call on a device shares the one array, so calls whose execution
 //     overlaps on the GPU (different streams without ordering, concurrent
 //     host threads) race and give wrong results; order them on one stream.
@@ -115,15 +122,18 @@ extern "C" kf_status kf_bicgk_noalloc(int64_t m, int64_t n, const float* A, int6
     set_error_message("scratch binding failed");
     return KF_ERR_WORKSPACE;
   }
-  // The array keeps the previous call's contents: clear the error word and
-  // the completion counters (everything before the partial sums).
-  const size_t clear = static_cast<size_t>(reinterpret_cast<char*>(P.rowpart) - static_cast<char*>(ws));
-  cudaError_t e = cudaMemsetAsync(ws, 0, clear, (cudaStream_t)stream);
+  // The array keeps the previous call's contents: clear the completion
+  // counters (they sit between the header and the partial sums, which every
+  // launch overwrites before reading).
+  const size_t clear = static_cast<size_t>(reinterpret_cast<char*>(P.rowpart) - reinterpret_cast<char*>(P.counters));
+  cudaError_t e = cudaMemsetAsync(P.counters, 0, clear, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     set_error_message(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     return KF_ERR_CUDA;
   }
-  MatTune t{0, 0, 0, 0, 0};
+  // kf_bicgk's kernel shape without a search, in its direct-load form
+  MatTune t = matprog_tuning_nosearch(P, current_matrix_tuning());
+  t.stages = 0;
   const char* why = nullptr;
   const int rc = launch_matprog(P, t, stream, &why);
   if (rc != 0) {

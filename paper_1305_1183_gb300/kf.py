@@ -69,6 +69,9 @@ _SIGS = {
     "kf_quantize_rows": ([i64, i64, vp, i64, ci, vp, vp, vp], ci),
     "kf_set_matrix_tuning": ([ci, ci, ci, ci, ci], ci),
     "kf_bicgk_noalloc": ([i64, i64, vp, i64, vp, vp, vp, vp, vp], ci),
+    "kf_set_wait_limit_ns": ([ctypes.c_uint64], ci),
+    "kf_get_wait_limit_ns": ([ctypes.POINTER(ctypes.c_uint64)], ci),
+    "kf_wait_probe": ([ctypes.c_uint64, vp, sz, vp, vp], ci),
     "kf_batched_create": ([ci, vp, ci, ci, ctypes.POINTER(vp)], ci),
     "kf_batched_destroy": ([vp], None),
     "kf_batched_workspace_size": ([vp, ctypes.POINTER(sz)], ci),
@@ -170,6 +173,32 @@ def _nb(t):
     return 0 if t is None else t.numel() * t.element_size()
 
 
+_CODE_DTYPES = {KF_F32: (torch.float32,), KF_BF16_ROWSCALE: (torch.int16, torch.bfloat16),
+                KF_FP8E4M3_ROWSCALE: (torch.uint8, torch.int8)}
+
+
+def _mat(A, fmt=KF_F32, name="A"):
+    """A matrix operand: the storage format's element type, unit column
+    stride (rows may be strided), on a CUDA device."""
+    if A is None:
+        return
+    if A.dtype not in _CODE_DTYPES[fmt]:
+        raise TypeError(f"{name}: dtype {A.dtype} does not hold storage format {fmt}")
+    if A.dim() != 2 or (A.shape[1] > 1 and A.stride(1) != 1):
+        raise ValueError(f"{name}: a 2-D tensor with unit column stride is required")
+    if not A.is_cuda:
+        raise ValueError(f"{name}: a CUDA tensor is required")
+
+
+def _vec(*ts):
+    """Vector operands: contiguous float32 CUDA tensors (None passes)."""
+    for t in ts:
+        if t is None or isinstance(t, int):
+            continue
+        if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+            raise TypeError("vector operands must be contiguous float32 CUDA tensors")
+
+
 # ------------------------------------------------------------------ utilities
 
 def kf_version() -> str:
@@ -211,6 +240,8 @@ def kf_get_matrix_tuning():
 # ------------------------------------------------------------------ sequences
 
 def kf_bicgk(A, p, r, q, s, ws, fmt=KF_F32, row_scale=None, lda=None, n=None, stream=None):
+    _mat(A, fmt)
+    _vec(p, r, q, s, row_scale)
     m = A.shape[0]
     n = A.shape[1] if n is None else n
     if fmt == KF_F32:
@@ -222,6 +253,9 @@ def kf_bicgk(A, p, r, q, s, ws, fmt=KF_F32, row_scale=None, lda=None, n=None, st
 
 
 def kf_gemver(A, u1, v1, u2, v2, y, z, alpha, beta, B, x, w, ws, stream=None):
+    _mat(A)
+    _mat(B, name="B")
+    _vec(u1, v1, u2, v2, y, z, x, w)
     n = A.shape[0]
     _ck(lib().kf_gemver(n, _p(A), A.stride(0), _p(u1), _p(v1), _p(u2), _p(v2), _p(y), _p(z),
                         alpha, beta, _p(B), B.stride(0), _p(x), _p(w), _p(ws), _nb(ws), _st(stream)))
@@ -230,12 +264,18 @@ def kf_gemver(A, u1, v1, u2, v2, y, z, alpha, beta, B, x, w, ws, stream=None):
 def kf_gemver_q(QA, fmt, sA, u1, v1, u2, v2, y, z, alpha, beta, QB, sB, x, w, ws, stream=None):
     """GEMVER on row-scaled codes (int16 BF16 or uint8 E4M3 tensors, n x n);
     writes codes QB and scales sB of B, x and w."""
+    _mat(QA, fmt, "QA")
+    _mat(QB, fmt, "QB")
+    _vec(sA, u1, v1, u2, v2, y, z, sB, x, w)
     n = QA.shape[0]
     _ck(lib().kf_gemver_q(n, _p(QA), QA.stride(0), fmt, _p(sA), _p(u1), _p(v1), _p(u2), _p(v2), _p(y), _p(z),
                           alpha, beta, _p(QB), QB.stride(0), _p(sB), _p(x), _p(w), _p(ws), _nb(ws), _st(stream)))
 
 
 def kf_gesummv(A, B, x, alpha, beta, y, ws, stream=None):
+    _mat(A)
+    _mat(B, name="B")
+    _vec(x, y)
     m, n = A.shape
     assert A.stride(0) == B.stride(0)
     _ck(lib().kf_gesummv(m, n, _p(A), _p(B), A.stride(0), _p(x), alpha, beta, _p(y),
@@ -243,6 +283,8 @@ def kf_gesummv(A, B, x, alpha, beta, y, ws, stream=None):
 
 
 def kf_atax(A, x, y, ws, stream=None):
+    _mat(A)
+    _vec(x, y)
     m, n = A.shape
     _ck(lib().kf_atax(m, n, _p(A), A.stride(0), _p(x), _p(y), _p(ws), _nb(ws), _st(stream)))
 
@@ -260,6 +302,8 @@ def kf_waxpby(alpha, x, beta, y, w, stream=None):
 
 def kf_gemv(A, x, y, ws, alpha=1.0, beta=0.0, y0=None, fmt=KF_F32, row_scale=None, n=None,
             stream=None):
+    _mat(A, fmt)
+    _vec(x, y, y0, row_scale)
     m = A.shape[0]
     n = A.shape[1] if n is None else n
     lda = A.stride(0) if fmt == KF_F32 else n
@@ -269,6 +313,8 @@ def kf_gemv(A, x, y, ws, alpha=1.0, beta=0.0, y0=None, fmt=KF_F32, row_scale=Non
 
 def kf_gemvt(A, y, x, ws, alpha=1.0, beta=0.0, x0=None, fmt=KF_F32, row_scale=None, n=None,
              stream=None):
+    _mat(A, fmt)
+    _vec(y, x, x0, row_scale)
     m = A.shape[0]
     n = A.shape[1] if n is None else n
     lda = A.stride(0) if fmt == KF_F32 else n
@@ -277,6 +323,9 @@ def kf_gemvt(A, y, x, ws, alpha=1.0, beta=0.0, x0=None, fmt=KF_F32, row_scale=No
 
 
 def kf_ger(A, u, v, B, alpha=1.0, stream=None):
+    _mat(A)
+    _mat(B, name="B")
+    _vec(u, v)
     m, n = A.shape
     _ck(lib().kf_ger(m, n, _p(A), A.stride(0), alpha, _p(u), _p(v), _p(B), B.stride(0), _st(stream)))
 
@@ -308,6 +357,23 @@ def kf_quantize_rows(A, fmt, Q, row_scale, stream=None):
     _ck(lib().kf_quantize_rows(m, n, _p(A), A.stride(0), fmt, _p(Q), _p(row_scale), _st(stream)))
 
 
+# ------------------------------------------------------------------ bounded waits
+
+def kf_set_wait_limit_ns(limit_ns: int):
+    _ck(lib().kf_set_wait_limit_ns(int(limit_ns)))
+
+
+def kf_get_wait_limit_ns() -> int:
+    v = ctypes.c_uint64(0)
+    _ck(lib().kf_get_wait_limit_ns(ctypes.byref(v)))
+    return v.value
+
+
+def kf_wait_probe(limit_ns, ws, waited=None, stream=None):
+    """Enqueue a wait that runs out after limit_ns (see include/kf.h)."""
+    _ck(lib().kf_wait_probe(int(limit_ns), _p(ws), _nb(ws), _p(waited), _st(stream)))
+
+
 # ------------------------------------------------------------------ no workspace
 
 KF_BICGK_NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -316,6 +382,8 @@ KF_BICGK_NOALLOC_SCRATCH_BYTES = 8 << 20
 def kf_bicgk_noalloc(A, p, r, q, s, stream=None):
     """BiCGK with the library's fixed device scratch instead of a workspace
     (for callers that cannot allocate); see include/kf.h."""
+    _mat(A)
+    _vec(p, r, q, s)
     m, n = A.shape
     _ck(lib().kf_bicgk_noalloc(m, n, _p(A), A.stride(0), _p(p), _p(r), _p(q), _p(s), _st(stream)))
 

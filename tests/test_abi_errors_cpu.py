@@ -312,3 +312,19 @@ def test_script_and_plan_api_errors(L, K):
     full = ctypes.create_string_buffer(need.value)
     assert L.kf_plan_describe(p.h, full, need.value, ctypes.byref(need)) == K.KF_OK
     assert full.value.startswith(buf.value) and len(full.value) == need.value - 1
+
+
+def test_wait_limit_and_probe_errors(L, K):
+    """The wait limit is range checked and unchanged by a refused value; the
+    probe needs a workspace for its error word and a limit in range."""
+    old = K.kf_get_wait_limit_ns()
+    assert old == 1_000_000_000
+    assert L.kf_set_wait_limit_ns(999) == K.KF_ERR_INVALID_ARG
+    assert L.kf_set_wait_limit_ns(60_000_000_001) == K.KF_ERR_INVALID_ARG
+    assert K.kf_get_wait_limit_ns() == old
+    assert L.kf_get_wait_limit_ns(None) == K.KF_ERR_INVALID_ARG
+    assert L.kf_set_wait_limit_ns(1000) == 0 and K.kf_get_wait_limit_ns() == 1000
+    assert L.kf_set_wait_limit_ns(old) == 0
+    assert L.kf_wait_probe(5000, None, 0, None, None) == K.KF_ERR_WORKSPACE
+    assert L.kf_wait_probe(5000, P, 255, None, None) == K.KF_ERR_WORKSPACE
+    assert L.kf_wait_probe(10, P, 256, None, None) == K.KF_ERR_INVALID_ARG

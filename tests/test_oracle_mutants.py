@@ -143,12 +143,16 @@ C_MUTANTS = [
      "bound = bound + fabsf(u2[i]) * n2;", "bound = bound + 0.0f * n2;",
      [P("test_gemver_rowscaled_storage_bound", BF16, 2.0 ** -8, 2.0 ** -126, 64.0),
       P("test_gemver_rowscaled_storage_bound", E4M3, 2.0 ** -4, 2.0 ** -6, 64.0),
-      P("test_hand_worked_rowscaled_gemver_storage")]),
+      P("test_hand_worked_rowscaled_gemver_storage"),
+      P("test_gemver_rowscaled_cost_against_the_amax_rule", BF16),
+      P("test_gemver_rowscaled_cost_against_the_amax_rule", E4M3)]),
     ("stored_gemver_updates_mixed", "void kfo_gemver_rowscaled_store(",
      "fmaf(u2[i], v2[j], fmaf(u1[i], v1[j], a))", "fmaf(u1[i], v2[j], fmaf(u2[i], v1[j], a))",
      [P("test_gemver_rowscaled_storage_bound", BF16, 2.0 ** -8, 2.0 ** -126, 1.0),
       P("test_gemver_rowscaled_storage_bound", E4M3, 2.0 ** -4, 2.0 ** -6, 1.0),
-      P("test_hand_worked_rowscaled_gemver_storage")]),
+      P("test_hand_worked_rowscaled_gemver_storage"),
+      P("test_gemver_rowscaled_cost_against_the_amax_rule", BF16),
+      P("test_gemver_rowscaled_cost_against_the_amax_rule", E4M3)]),
 ]
 
 # Python oracles: (id, module, old, new, pins); ``old`` must occur once in the module.
