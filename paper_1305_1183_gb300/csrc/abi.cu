@@ -16,9 +16,6 @@ namespace kf {
 
 bool atax_single_pass_ok(int64_t m, int64_t n, int64_t lda, const void* A, const void* x, const void* y);
 size_t atax_workspace_bytes(int64_t n);
-int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y,
-                       void* ws, size_t ws_bytes, int stages_req, int ctas_per_sm, void* stream,
-                       const char** why, int rows_per_round);
 int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, void* ws,
                       size_t ws_bytes, void* stream, const char** why);
 int launch_madd_strided(int64_t m, int64_t n, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,

@@ -32,10 +32,38 @@ constexpr int ATAX_MAXSTAGES = 8;
 
 namespace {
 
+// Distributed shared memory of a thread-block cluster.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_id_x() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float4 ld_cluster_f4(const void* local, unsigned rank) {
+  unsigned remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_addr(local)), "r"(rank));
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(remote)
+               : "memory");
+  return v;
+}
+
 // RP rows per round: their dots share one block barrier.  With RP = 2 the
 // vector x is read through L1 instead of being held in registers, which
-// pays for the second row's values.
-template <int NT, int VA, int RP>
+// pays for the second row's values.  CL > 1: the grid is made of clusters of
+// CL blocks, whose column partials are added inside the cluster through
+// distributed shared memory (block rank r adds slice r of the columns over
+// ranks 0..CL-1 in order) before one partial per cluster is stored.
+template <int NT, int VA, int RP, int CL>
 __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const float* __restrict__ A, int64_t lda, int64_t m,
                                                         int64_t n, const float* __restrict__ x,
                                                         float* __restrict__ ypart, int stages,
@@ -107,14 +135,16 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
       if (lane == 0) red[round & 1][rp][warp] = d;
     }
     if (__syncthreads_or(!ok)) {
-      // A copy never completed: report, let the other copies land (bounded), stop.
+      // A copy never completed: report, let the other copies land (bounded),
+      // stop reading rows (the cluster's blocks still meet at its barriers).
       if (tid == 0) {
         atomicOr(err, KF_DEVERR_TIMEOUT);
         for (int64_t q = j; q < nrows && q < j + stages; ++q)
           (void)mbar_wait_bounded(&full[q % stages], (unsigned)((q / stages) & 1), WAIT_DRAIN_NS);
       }
       __syncthreads();
-      return;
+      if constexpr (CL == 1) return;
+      break;
     }
     // Every thread has its rows' values in registers: the stages can be refilled.
     if (tid == 0) {
@@ -143,11 +173,38 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
       }
     }
   }
-  float4* yp = reinterpret_cast<float4*>(ypart + (int64_t)blockIdx.x * n);
+  if constexpr (CL == 1) {
+    float4* yp = reinterpret_cast<float4*>(ypart + (int64_t)blockIdx.x * n);
 #pragma unroll
-  for (int k = 0; k < VA; ++k) {
-    const int64_t c4 = (int64_t)k * NT + tid;
-    if (c4 < n4) yp[c4] = yacc[k];
+    for (int k = 0; k < VA; ++k) {
+      const int64_t c4 = (int64_t)k * NT + tid;
+      if (c4 < n4) yp[c4] = yacc[k];
+    }
+  } else {
+    // Every copy into the ring has landed and been read: the ring now holds
+    // this block's column partial (n floats), which the cluster reduces.
+    __syncthreads();
+    float4* mine = reinterpret_cast<float4*>(ring);
+#pragma unroll
+    for (int k = 0; k < VA; ++k) {
+      const int64_t c4 = (int64_t)k * NT + tid;
+      if (c4 < n4) mine[c4] = yacc[k];
+    }
+    cluster_sync_all();
+    const unsigned rank = cluster_rank();
+    const int64_t per = (n4 + CL - 1) / CL;
+    const int64_t s0 = (int64_t)rank * per, s1 = min(n4, s0 + per);
+    float4* yp = reinterpret_cast<float4*>(ypart + (int64_t)cluster_id_x() * n);
+    for (int64_t c4 = s0 + tid; c4 < s1; c4 += NT) {
+      float4 acc = ld_cluster_f4(mine + c4, 0);
+#pragma unroll
+      for (int c = 1; c < CL; ++c) {
+        const float4 v = ld_cluster_f4(mine + c4, (unsigned)c);
+        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+      }
+      yp[c4] = acc;
+    }
+    cluster_sync_all();  // no block leaves while another still reads its shared memory
   }
 }
 
@@ -196,9 +253,14 @@ __global__ void __launch_bounds__(FIN_COLS * FIN_SLICES) atax_finish_kernel(cons
   }
 }
 
+constexpr int ATAX_CLUSTER = 8;
+
 template <int VA>
-const void* atax_fn(int rp) {
-  return rp == 2 ? (const void*)&atax_rows_kernel<512, VA, 2> : (const void*)&atax_rows_kernel<512, VA, 1>;
+const void* atax_fn(int rp, bool cluster) {
+  if (cluster)
+    return rp == 2 ? (const void*)&atax_rows_kernel<512, VA, 2, ATAX_CLUSTER>
+                   : (const void*)&atax_rows_kernel<512, VA, 1, ATAX_CLUSTER>;
+  return rp == 2 ? (const void*)&atax_rows_kernel<512, VA, 2, 1> : (const void*)&atax_rows_kernel<512, VA, 1, 1>;
 }
 
 }  // namespace
@@ -216,7 +278,7 @@ size_t atax_workspace_bytes(int64_t n) {
 
 int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y,
                        void* ws, size_t ws_bytes, int stages_req, int ctas_per_sm, void* stream,
-                       const char** why, int rows_per_round) {
+                       const char** why, int rows_per_round, bool cluster) {
   const int VA = (int)((n / 4 + 511) / 512);
   const int va = VA <= 1 ? 1 : (VA <= 2 ? 2 : (VA <= 4 ? 4 : 8));
   const int64_t rowcap = (n + 31) / 32 * 32;  // 128-byte aligned stages
@@ -229,7 +291,13 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
   stages = std::min(stages, ATAX_MAXSTAGES);
   // two rows per barrier need both rows' stages in the ring at once
   const int rp = rows_per_round == 2 && va <= 4 && stages >= 2 ? 2 : 1;
-  const void* fn = va == 1 ? atax_fn<1>(rp) : va == 2 ? atax_fn<2>(rp) : va == 4 ? atax_fn<4>(rp) : atax_fn<8>(rp);
+  // clusters of ATAX_CLUSTER blocks add their column partials on chip when
+  // the grid has at least two clusters' worth of rows
+  const bool use_cluster = cluster && m >= 2 * ATAX_CLUSTER;
+  const void* fn = va == 1 ? atax_fn<1>(rp, use_cluster)
+                 : va == 2 ? atax_fn<2>(rp, use_cluster)
+                 : va == 4 ? atax_fn<4>(rp, use_cluster)
+                           : atax_fn<8>(rp, use_cluster);
   const size_t smem = (size_t)stages * rowbytes;
   {
     int dev = 0, optin = 0;
@@ -249,15 +317,55 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
   int64_t grid = (int64_t)device_sm_count() * occ;
   grid = std::min<int64_t>(grid, m);
   grid = std::min<int64_t>(grid, (int64_t)device_sm_count() * 4);
+  if (use_cluster) {
+    // whole clusters, all resident at once (a cluster's blocks share a GPC)
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3((unsigned)(grid / ATAX_CLUSTER * ATAX_CLUSTER));
+    q.blockDim = dim3(512);
+    q.dynamicSmemBytes = smem;
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = ATAX_CLUSTER;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, fn, &q) != cudaSuccess || clusters < 1) {
+      (void)cudaGetLastError();
+      *why = "cluster launch does not fit";
+      return -10;
+    }
+    grid = std::min<int64_t>(grid / ATAX_CLUSTER, clusters) * ATAX_CLUSTER;
+  }
   unsigned* err = reinterpret_cast<unsigned*>(ws);
   float* ypart = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
   if (ws_bytes < 256 + (size_t)grid * n * sizeof(float)) { *why = "workspace too small"; return -11; }
 
-  int nparts = (int)grid;
+  int nparts = (int)(use_cluster ? grid / ATAX_CLUSTER : grid);
   uint64_t wait_ns = wait_limit_ns();
   void* args[] = {(void*)&A, (void*)&lda, (void*)&m, (void*)&n, (void*)&x, (void*)&ypart,
                   (void*)&stages, (void*)&rowcap, (void*)&err, (void*)&wait_ns};
-  cudaError_t e = launch_pdl(fn, dim3((unsigned)grid), dim3(512), args, smem, stream);
+  cudaError_t e;
+  if (use_cluster) {
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3((unsigned)grid);
+    c.blockDim = dim3(512);
+    c.dynamicSmemBytes = smem;
+    c.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute ca[2];
+    ca[0].id = cudaLaunchAttributeClusterDimension;
+    ca[0].val.clusterDim.x = ATAX_CLUSTER;
+    ca[0].val.clusterDim.y = 1;
+    ca[0].val.clusterDim.z = 1;
+    ca[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    ca[1].val.programmaticStreamSerializationAllowed = 1;
+    c.attrs = ca;
+    c.numAttrs = 2;
+    e = cudaLaunchKernelExC(&c, fn, args);
+  } else {
+    e = launch_pdl(fn, dim3((unsigned)grid), dim3(512), args, smem, stream);
+  }
   if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
 
   cudaLaunchConfig_t cfg = {};
@@ -277,12 +385,14 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
 }
 
 // ATAX with the tuning cache: key "atax log2(m) log2(n)" holding the
-// copy-ring depth (stages field), resident blocks per SM (groups field) and
-// rows per barrier (unroll field).  On a miss, with tuning on first use
-// enabled, every fitting (rows per barrier in {1, 2}, blocks per SM in
-// {1, 2}, stages in {2, 3, 4, 6}) is timed on the call's operands (mean of
-// back-to-back launches, best of two rounds) and the fastest stored, unless
-// it gains less than 2 % over the built-in choice.
+// copy-ring depth (stages field), resident blocks per SM (groups field), rows
+// per barrier (unroll field) and whether the column partials are first added
+// inside clusters (vec field: 2 = no, otherwise yes).  On a miss, with tuning
+// on first use enabled, every fitting (cluster reduction on or off, rows per
+// barrier in {1, 2}, blocks per SM in {1, 2}, stages in {2, 3, 4, 6}) is
+// timed on the call's operands (mean of back-to-back launches, best of two
+// rounds) and the fastest stored, unless it gains less than 2 % over the
+// built-in choice.
 int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, void* ws,
                       size_t ws_bytes, void* stream, const char** why) {
   auto cls = [](int64_t v) {
@@ -300,46 +410,45 @@ int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const f
       cudaEvent_t a, b;
       cudaEventCreate(&a);
       cudaEventCreate(&b);
+      auto run = [&](int stg, int cps, int rp, bool cl) {
+        return launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, stg, cps, stream, why, rp, cl);
+      };
+      auto time_it = [&](int stg, int cps, int rp, bool cl) {
+        float tb = 1e30f;
+        for (int round = 0; round < 2; ++round) {
+          cudaEventRecord(a, st);
+          for (int r = 0; r < reps; ++r) run(stg, cps, rp, cl);
+          cudaEventRecord(b, st);
+          cudaEventSynchronize(b);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, a, b);
+          tb = std::min(tb, ms / (float)reps);
+        }
+        return tb;
+      };
       // warm up with the built-in choice, then time it
-      for (int r = 0; r < 2; ++r) launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, 0, 0, stream, why, 1);
-      float base = 1e30f;
-      for (int round = 0; round < 2; ++round) {
-        cudaEventRecord(a, st);
-        for (int r = 0; r < reps; ++r) launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, 0, 0, stream, why, 1);
-        cudaEventRecord(b, st);
-        cudaEventSynchronize(b);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        base = std::min(base, ms / (float)reps);
-      }
+      for (int r = 0; r < 2; ++r) run(0, 0, 1, true);
+      const float base = time_it(0, 0, 1, true);
       float best = 1e30f;
       MatTune bt = t;
-      for (int rp : {1, 2})
-      for (int cps : {1, 2})
-        for (int stg : {2, 3, 4, 6}) {
-          if (launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, stg, cps, stream, why, rp) != 0) {
-            (void)cudaGetLastError();
-            continue;
-          }
-          float tb = 1e30f;
-          for (int round = 0; round < 2; ++round) {
-            cudaEventRecord(a, st);
-            for (int r = 0; r < reps; ++r) launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, stg, cps, stream, why, rp);
-            cudaEventRecord(b, st);
-            cudaEventSynchronize(b);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, a, b);
-            tb = std::min(tb, ms / (float)reps);
-          }
-          if (tb < best * 0.999f) {
-            best = tb;
-            bt = MatTune{1, 0, rp, cps, stg};
-          }
-        }
+      for (int cl : {1, 2})
+        for (int rp : {1, 2})
+          for (int cps : {1, 2})
+            for (int stg : {2, 3, 4, 6}) {
+              if (run(stg, cps, rp, cl == 1) != 0) {
+                (void)cudaGetLastError();
+                continue;
+              }
+              const float tb = time_it(stg, cps, rp, cl == 1);
+              if (tb < best * 0.999f) {
+                best = tb;
+                bt = MatTune{1, cl, rp, cps, stg};
+              }
+            }
       cudaEventDestroy(a);
       cudaEventDestroy(b);
       // keep the built-in choice unless a candidate gains more than 2 %
-      if (best > base * 0.98f) bt = MatTune{1, 0, 1, 0, 0};
+      if (best > base * 0.98f) bt = MatTune{1, 1, 1, 0, 0};
       if (best < 1e29f) {
         tune_cache_put_mat(key, bt);
         t = bt;
@@ -347,7 +456,7 @@ int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const f
     }
   }
   return launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, t.stages, t.groups, stream, why,
-                            t.unroll == 2 ? 2 : 1);
+                            t.unroll == 2 ? 2 : 1, t.vec != 2);
 }
 
 }  // namespace kf

@@ -80,7 +80,7 @@ struct MatProg {
   // geometry
   int n_strips, n_groups;
   int stages;                    // per-warp bulk-copy ring depth (staged kernels)
-  int64_t blocks_per_group;      // 32-row blocks per row group
+  int64_t units_per_group;       // 8-row units per row group
   // workspace
   float* rowpart;                // [nrow_res][n_strips][m]
   float* colpart;                // [ncol_res][n_groups][n]

@@ -311,22 +311,23 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
   const int occ = occupancy(e.fn, threads, smem);
   if (occ < 1) { *why = "kernel does not fit on an SM with this tuning"; return -10; }
 
-  // Geometry: strips by the instance's strip width, groups to fill one wave.
+  // Geometry: strips by the instance's strip width, groups of 8-row units
+  // to fill one wave of resident blocks.
   const int64_t strips = P.n > 0 ? (P.n + sw - 1) / sw : 1;
-  const int64_t nrb = (P.m + 31) / 32;
+  const int64_t nunits = (P.m + 7) / 8;
   const int64_t slots = (int64_t)device_sm_count() * occ;
   int64_t G;
   if (t.groups > 0) G = t.groups;
   else G = std::max<int64_t>(1, slots / std::max<int64_t>(1, strips));
-  G = std::min<int64_t>(G, std::max<int64_t>(1, nrb));
+  G = std::min<int64_t>(G, std::max<int64_t>(1, nunits));
   G = std::min<int64_t>(G, MAT_MAXGROUPS);
-  int64_t bpg = nrb > 0 ? (nrb + G - 1) / G : 0;
-  G = nrb > 0 ? (nrb + bpg - 1) / bpg : 1;
+  int64_t upg = nunits > 0 ? (nunits + G - 1) / G : 0;
+  G = nunits > 0 ? (nunits + upg - 1) / upg : 1;
   if (strips > 0x7fffffffLL) { *why = "matrix too wide"; return -2; }
   P.n_strips = (int)strips;
   P.n_groups = (int)G;
   P.wait_ns = wait_limit_ns();
-  P.blocks_per_group = bpg;
+  P.units_per_group = upg;
   P.stages = stages;
   dim3 grid((unsigned)strips, (unsigned)G);
   void* args[] = {&P};

@@ -3,10 +3,13 @@
 // One read of an m x n matrix (or of two same-shaped matrices) serves every
 // fused GER / GEMV / GEMVT call of a fusion.  Kernel schema (the paper's
 // Algorithm 1, Section 3.3.2, re-derived for a row-major layout on sm_103a):
-//   * a block owns a column strip and a group of 32-row blocks; its NW
+//   * a block owns a column strip and a group of consecutive 8-row units
+//     (so the groups of a full-chip grid differ by at most one unit); its NW
 //     consumer warps sit side by side across the strip (each owns 32*V
 //     16-byte chunks of every row), so the block reads NW*512*V contiguous
-//     bytes of each row it visits -- long sequential runs for HBM;
+//     bytes of each row it visits -- long sequential runs for HBM.  Rows are
+//     walked in 32-row blocks of four 8-row quarters; a quarter outside the
+//     block's group is skipped (a test every warp takes alike);
 //   * "load invariant data": the column vectors that every row multiplies
 //     (x of GEMV, v of GER) are loaded once into each warp's registers;
 //   * "clear outputs of accumulated reductions": GEMVT column sums live in
@@ -403,7 +406,6 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   constexpr int SEGW = 32 * V * 16;  // bytes of one warp's slice of a row
   constexpr int SEG = NW * SEGW;     // bytes of the block's part of a row
   constexpr int BATCH = NMAT * U * SEG;
-  constexpr int NB = 32 / U;         // batches per 32-row block
   static_assert(U == 1 || U == 2 || U == 4 || U == 8, "U must divide 8");
   constexpr int NGA = NG > 0 ? NG : 1;
   constexpr bool SPEC = (SIG & SIG_SPEC) != 0;
@@ -434,10 +436,14 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   const int64_t wcol0 = col0 + (int64_t)min(warp, NW - 1) * SWW;
   const int nops = P.nops;
 
-  const int64_t nrb = (m + 31) >> 5;
-  const int64_t rb_begin = (int64_t)group * P.blocks_per_group;
-  const int64_t rb_end = min(nrb, rb_begin + P.blocks_per_group);
-  const int64_t nbatch = (rb_end > rb_begin ? rb_end - rb_begin : 0) * NB;
+  // the group's rows: 8-row units [u_begin, u_end), walked by 32-row blocks
+  constexpr int NBU = 8 / U;         // batches per 8-row unit
+  const int64_t nunits = (m + 7) >> 3;
+  const int64_t u_begin = min(nunits, (int64_t)group * P.units_per_group);
+  const int64_t u_end = min(nunits, u_begin + P.units_per_group);
+  const int64_t rb_begin = u_begin >> 2;
+  const int64_t rb_end = (u_end + 3) >> 2;
+  const int64_t nbatch = (u_end - u_begin) * NBU;
 
   const int S = STAGED ? P.stages : 1;
   const bool ring = STAGED && (col0 + SW <= n);  // block-uniform
@@ -470,7 +476,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
             break;
           }
         }
-        const int64_t rowb = ((rb_begin + jj / NB) << 5) + (jj % NB) * U;
+        const int64_t rowb = ((u_begin + jj / NBU) << 3) + (jj % NBU) * U;
         unsigned bytes = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -566,6 +572,9 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
     for (int64_t rb = rb_begin; rb < rb_end; ++rb) {
       const int64_t row0 = rb << 5;
       const bool lane_row_ok = row0 + lane < m;
+      // this lane's row (row0 + lane) belongs to the group: its partials are ours to store
+      const int64_t lane_unit = (rb << 2) + (lane >> 3);
+      const bool lane_in = lane_row_ok && lane_unit >= u_begin && lane_unit < u_end;
       float rv[NOPS];  // per-lane row scalar (GER u, GEMVT y) for row row0+lane
 #pragma unroll
       for (int k = 0; k < NOPS; ++k) {
@@ -589,12 +598,16 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
             bound = __fadd_rn(bound, __fmul_rn(fabsf(P.ops[k].alpha * rv[k]), __ldg(P.ops[k].vnorm)));
         sbrow = bound > 0.f ? __fdiv_rn(bound, QMAX) : 1.f;
         isbrow = __fdiv_rn(1.f, sbrow);
-        if (strip == 0 && warp == 0 && lane_row_ok) P.Bscale[0][row0 + lane] = sbrow;
+        if (strip == 0 && warp == 0 && lane_in) P.Bscale[0][row0 + lane] = sbrow;
       }
       float rowdot[NGA];  // this warp's partial of row row0+lane
+#pragma unroll
+      for (int g = 0; g < NGA; ++g) rowdot[g] = 0.f;
 
 #pragma unroll 1
       for (int h = 0; h < 4; ++h) {  // four quarters of 8 rows
+        const int64_t unit = (rb << 2) + h;
+        if (unit < u_begin || unit >= u_end) continue;  // another group's rows
         float dacc[NGA][8];          // per-lane partial dot of each row of the quarter
 #pragma unroll
         for (int g = 0; g < NGA; ++g)
@@ -711,7 +724,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
 #pragma unroll
         for (int g = 0; g < NGA; ++g) red[buf][g][warp][lane] = rowdot[g];
         consumer_sync(NW * 32);
-        if (warp < NGA && warp < P.nrow_res && lane_row_ok) {
+        if (warp < NGA && warp < P.nrow_res && lane_in) {
           float sum = 0.f;
 #pragma unroll
           for (int w = 0; w < NW; ++w) sum += red[buf][warp][w][lane];
@@ -796,8 +809,8 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   if (s_last[1]) {
     __threadfence();
     // Row results of this group: sum the strips' partials in strip order.
-    const int64_t r0 = rb_begin << 5;
-    const int64_t r1 = min(m, rb_end << 5);
+    const int64_t r0 = u_begin << 3;
+    const int64_t r1 = min(m, u_end << 3);
     const bool v4 = (m & 3) == 0;
     const int step = v4 ? 4 : 1;
     for (int64_t i = r0 + threadIdx.x * step; i < r1; i += (int64_t)blockDim.x * step) {

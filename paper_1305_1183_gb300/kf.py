@@ -182,7 +182,7 @@ def _mat(A, fmt=KF_F32, name="A"):
     stride (rows may be strided), on a CUDA device."""
     if A is None:
         return
-    if A.dtype not in _CODE_DTYPES[fmt]:
+    if fmt in _CODE_DTYPES and A.dtype not in _CODE_DTYPES[fmt]:
         raise TypeError(f"{name}: dtype {A.dtype} does not hold storage format {fmt}")
     if A.dim() != 2 or (A.shape[1] > 1 and A.stride(1) != 1):
         raise ValueError(f"{name}: a 2-D tensor with unit column stride is required")
@@ -264,8 +264,9 @@ def kf_gemver(A, u1, v1, u2, v2, y, z, alpha, beta, B, x, w, ws, stream=None):
 def kf_gemver_q(QA, fmt, sA, u1, v1, u2, v2, y, z, alpha, beta, QB, sB, x, w, ws, stream=None):
     """GEMVER on row-scaled codes (int16 BF16 or uint8 E4M3 tensors, n x n);
     writes codes QB and scales sB of B, x and w."""
-    _mat(QA, fmt, "QA")
-    _mat(QB, fmt, "QB")
+    if fmt != KF_F32:  # KF_F32 codes are the library's to refuse (KF_ERR_DTYPE)
+        _mat(QA, fmt, "QA")
+        _mat(QB, fmt, "QB")
     _vec(sA, u1, v1, u2, v2, y, z, sB, x, w)
     n = QA.shape[0]
     _ck(lib().kf_gemver_q(n, _p(QA), QA.stride(0), fmt, _p(sA), _p(u1), _p(v1), _p(u2), _p(v2), _p(y), _p(z),
