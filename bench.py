@@ -562,6 +562,178 @@ def time_e2e(suite, steps, warmup, st, seqs):
     return a.elapsed_time(b), h2d, d2h
 
 
+def time_e2e_pipelined(kf, sizes, device, steps, warmup, seqs):
+    """The end-to-end metric with copies overlapped across steps: two device
+    copies of the suite's buffers; step k copies its inputs host->device on
+    one stream (into copy k % 2, once the kernels of step k - 2 are done
+    with it), runs the fused suite on a second stream, and reads its results
+    back device->host on a third, so the copies of step k + 1 overlap the
+    kernels and read-back of step k.  Every step still moves all of its
+    inputs in and all of its results out.  Returns (ms per step, h2d bytes,
+    d2h bytes)."""
+    suites = [Suite(kf, sizes, device, seqs=seqs) for _ in range(2)]
+    hin = {s: [t.detach().cpu().pin_memory() for t in suites[0].inputs(s)] for s in seqs}
+    hout = {s: [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in suites[0].outputs(s)] for s in seqs}
+    h2d = sum(t.numel() * t.element_size() for s in seqs for t in hin[s])
+    d2h = sum(t.numel() * t.element_size() for s in seqs for t in hout[s])
+    s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    loaded = [ev(), ev()]
+    ran = [ev(), ev()]
+    read = [ev(), ev()]
+    used = [False, False]
+
+    def step(k):
+        b = k % 2
+        su = suites[b]
+        with torch.cuda.stream(s_in):
+            if used[b]:
+                s_in.wait_event(ran[b])           # step k - 2's kernels are done with copy b
+            for s in seqs:
+                for dst, src in zip(su.inputs(s), hin[s]):
+                    dst.copy_(src, non_blocking=True)
+            loaded[b].record(s_in)
+        with torch.cuda.stream(s_run):
+            s_run.wait_event(loaded[b])
+            if used[b]:
+                s_run.wait_event(read[b])         # step k - 2's results are read back
+            for s in seqs:
+                su.fused(s, s_run)
+            ran[b].record(s_run)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ran[b])
+            for s in seqs:
+                for dst, src in zip(hout[s], su.outputs(s)):
+                    dst.copy_(src, non_blocking=True)
+            read[b].record(s_out)
+        used[b] = True
+
+    torch.cuda.synchronize()
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    z = torch.cuda.Event(enable_timing=True)
+    a.record(s_in)
+    for k in range(warmup, warmup + steps):
+        step(k)
+    s_in.wait_stream(s_out)
+    s_in.wait_stream(s_run)
+    z.record(s_in)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(z) / steps
+    del suites
+    torch.cuda.empty_cache()
+    return ms, h2d, d2h
+
+
+# ---------------------------------------------------------------- Table 1 sequences beyond the suite
+
+def table1_bytes(seq, n):
+    """Algorithmic and unfused-chain bytes of the other Table 1 sequences
+    (FP32): SGEMV z = alpha A x + beta y; SGEMVT x = beta A^T y + z,
+    w = alpha A x (A read twice: w needs all of x); SSCAL x = alpha x;
+    MADD C = A + B; VADD x = w + y + z."""
+    f = 4
+    if seq == "sgemv":
+        return f * (n * n + 3 * n), f * (n * n + 5 * n)           # GEMV then AXPBY
+    if seq == "sgemvt":
+        return f * (2 * n * n + 5 * n), f * (2 * n * n + 7 * n)   # GEMVT, AXPBY, GEMV
+    if seq == "sscal":
+        return f * 2 * n, f * 2 * n                                # one call either way
+    if seq == "madd":
+        return f * 3 * n * n, f * 3 * n * n
+    if seq == "vadd":
+        return f * 4 * n, f * 6 * n                                # two AXPBYs
+    raise KeyError(seq)
+
+
+def table1_section(kf, d, st, steps, warmup, n_mat=8192, n_vec=1 << 26):
+    """SGEMV, SGEMVT, SSCAL, MADD and VADD of Table 1 (the sequences beyond
+    the at-scale suite), each fused against its one-kernel-per-call chain on
+    the same inputs: mean ms of back-to-back calls, GB/s of algorithmic
+    bytes and fraction of the measured copy bandwidth."""
+    g = lambda shape, tid: synth.uniform(shape, 0, tid, device=d)  # noqa: E731
+    peak, _ = hbm_peak()
+    n = n_mat
+    A, B = g((n, n), synth.TID["A"]), g((n, n), synth.TID["B"])
+    x, y, z = g((n,), synth.TID["x"]), g((n,), synth.TID["y"]), g((n,), synth.TID["z"])
+    o1, o2, t = torch.empty(n, device=d), torch.empty(n, device=d), torch.empty(n, device=d)
+    C = torch.empty(n, n, device=d)
+    W = kf.workspace(kf.KF_SEQ_SGEMVT, n, n)
+    vw, vy, vz = (g((n_vec,), synth.TID[k]) for k in ("w", "y", "z"))
+    vo, vt = torch.empty(n_vec, device=d), torch.empty(n_vec, device=d)
+    calls = {
+        "sgemv": (lambda s: kf.kf_gemv(A, x, o1, W, alpha=ALPHA, beta=BETA, y0=y, stream=s),
+                  lambda s: (kf.kf_gemv(A, x, t, W, alpha=ALPHA, stream=s),
+                             kf.kf_axpby(1.0, t, BETA, y, o1, stream=s)), n, 1, 2),
+        "sgemvt": (lambda s: kf.kf_sgemvt(A, y, z, ALPHA, BETA, o1, o2, W, stream=s),
+                   lambda s: (kf.kf_gemvt(A, y, t, W, stream=s), kf.kf_axpby(BETA, t, 1.0, z, o1, stream=s),
+                              kf.kf_gemv(A, o1, o2, W, alpha=ALPHA, stream=s)), n, 2, 3),
+        "sscal": (lambda s: kf.kf_scal(ALPHA, vw, vo, stream=s), None, n_vec, 1, 1),
+        "madd": (lambda s: kf.kf_madd(A, B, C, stream=s), None, n, 1, 1),
+        "vadd": (lambda s: kf.kf_vadd3(vw, vy, vz, vo, stream=s),
+                 lambda s: (kf.kf_axpby(1.0, vw, 1.0, vy, vt, stream=s), kf.kf_axpby(1.0, vt, 1.0, vz, vo, stream=s)),
+                 n_vec, 1, 2),
+    }
+    out = {"note": "Table 1 sequences beyond the suite; SSCAL and MADD are one call either way"}
+    for seq, (fused, unfused, size, nl_f, nl_u) in calls.items():
+        alg, unf = table1_bytes(seq, size)
+        ms = time_calls(fused, steps, warmup, st)
+        r = {"size": size, "ms": ms, "gbs": alg / (ms * 1e-3) / 1e9, "launches": nl_f}
+        r["frac"] = r["gbs"] / peak
+        if unfused is not None:
+            ums = time_calls(unfused, steps, warmup, st)
+            r.update({"unfused_ms": ums, "unfused_launches": nl_u, "speedup_vs_unfused": ums / ms,
+                      "ideal_speedup": unf / alg})
+        out[seq] = r
+    del A, B, C, vw, vy, vz, vo, vt
+    torch.cuda.empty_cache()
+    return out
+
+
+def bicgk_small_section(kf, d, st, steps, warmup, n=2048, copies=16):
+    """BiCGK on a 2048 x 2048 matrix (16.8 MB, inside the 129 MB L2): cold
+    HBM (each call reads one of `copies` distinct copies of the inputs in
+    turn, together more than twice the L2, so a copy is evicted before it is
+    read again) and warm L2 (the same copy every call)."""
+    peak, _ = hbm_peak()
+    sets = []
+    for c in range(copies):
+        sets.append(dict(A=synth.uniform((n, n), c, synth.TID["A"], device=d),
+                         p=synth.uniform((n,), c, synth.TID["p"], device=d),
+                         r=synth.uniform((n,), c, synth.TID["r"], device=d),
+                         q=torch.empty(n, device=d), s=torch.empty(n, device=d)))
+    W = kf.workspace(kf.KF_SEQ_BICGK, n, n)
+    nbytes = algorithmic_bytes("bicgk", (n, n))
+
+    def cold(stream):
+        for b in sets:
+            kf.kf_bicgk(b["A"], b["p"], b["r"], b["q"], b["s"], W, stream=stream)
+
+    def unfused_cold(stream):
+        for b in sets:
+            kf.kf_gemv(b["A"], b["p"], b["q"], W, stream=stream)
+            kf.kf_gemvt(b["A"], b["r"], b["s"], W, stream=stream)
+
+    b0 = sets[0]
+    ms_cold = time_calls(cold, steps, warmup, st) / copies
+    ms_ucold = time_calls(unfused_cold, steps, warmup, st) / copies
+    ms_warm = time_calls(lambda s: kf.kf_bicgk(b0["A"], b0["p"], b0["r"], b0["q"], b0["s"], W, stream=s),
+                         steps * copies, warmup, st)
+    ms_uwarm = time_calls(lambda s: (kf.kf_gemv(b0["A"], b0["p"], b0["q"], W, stream=s),
+                                     kf.kf_gemvt(b0["A"], b0["r"], b0["s"], W, stream=s)), steps * copies, warmup, st)
+    out = {"n": n, "bytes": nbytes, "copies_rotated": copies,
+           "cold_hbm": {"ms": ms_cold, "gbs": nbytes / (ms_cold * 1e-3) / 1e9,
+                        "frac": nbytes / (ms_cold * 1e-3) / 1e9 / peak, "unfused_ms": ms_ucold,
+                        "speedup_vs_unfused": ms_ucold / ms_cold},
+           "warm_l2": {"ms": ms_warm, "gbs": nbytes / (ms_warm * 1e-3) / 1e9, "unfused_ms": ms_uwarm,
+                       "speedup_vs_unfused": ms_uwarm / ms_warm}}
+    del sets
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- precision forms
 
 def time_calls(fn, steps, warmup, st):
@@ -879,6 +1051,8 @@ def main():
     ap.add_argument("--autotune", type=int, default=3,
                     help="timed runs per candidate of the first-use tuning search (0: built-in defaults)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-instances section")
+    ap.add_argument("--no-table1", action="store_true", help="skip SGEMV, SGEMVT, SSCAL, MADD, VADD")
+    ap.add_argument("--no-small-bicgk", action="store_true", help="skip BiCGK 2048^2 cold / warm L2")
     ap.add_argument("--only", default="", choices=["", "batched", "precision"],
                     help="run only this section and print its JSON (profiling)")
     ap.add_argument("--batched-count", type=int, default=4096, help="instances per batched launch")
@@ -959,12 +1133,20 @@ def main():
         if not args.no_batched:
             extra["batched"] = batched_section(kf, torch.device("cuda", local), st, args.steps, args.warmup,
                                                count=args.batched_count)
+        if not args.no_table1:
+            extra["table1"] = table1_section(kf, torch.device("cuda", local), st, args.steps, args.warmup)
+        if not args.no_small_bicgk:
+            extra["bicgk_2048"] = bicgk_small_section(kf, torch.device("cuda", local), st, args.steps, args.warmup)
         suite = Suite(kf, sizes, torch.device("cuda", local), seqs=seqs)
 
     e2e = None
     if not args.no_e2e:
-        e2e_ms, h2d, d2h = time_e2e(suite, max(1, min(args.steps, 5)), 1, st, seqs)
         e2e_steps = max(1, min(args.steps, 5))
+        e2e_serial_ms, h2d, d2h = time_e2e(suite, e2e_steps, 1, st, seqs)
+        del suite
+        torch.cuda.empty_cache()
+        e2e_ms_step, h2d, d2h = time_e2e_pipelined(kf, sizes, torch.device("cuda", local), max(4, e2e_steps), 2, seqs)
+        e2e_ms = e2e_ms_step * e2e_steps
 
     step_bytes = sum(algorithmic_bytes(s, sizes[s]) for s in seqs)
     dev = torch.device("cuda", local)
@@ -1027,7 +1209,13 @@ def main():
     if not args.no_e2e:
         line["e2e"] = {"value": job_gbs(world, step_bytes, e2e_ms / e2e_steps), "unit": "GB/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                       "ms_per_step": e2e_ms / e2e_steps}
+                       "ms_per_step": e2e_ms / e2e_steps,
+                       "how": ("public API from pinned host buffers; each step copies all its inputs in and all "
+                               "its results out; copies of step k+1 overlap the kernels and read-back of step k "
+                               "(two device copies of the buffers, three streams)"),
+                       "serial": {"value": job_gbs(world, step_bytes, e2e_serial_ms / e2e_steps),
+                                  "ms_per_step": e2e_serial_ms / e2e_steps,
+                                  "how": "the same steps with copies and kernels in order on one stream"}}
     line.update(extra)
     if cpu is not None:
         line["cpu_baseline"] = cpu

@@ -78,7 +78,8 @@ typedef enum {
   KF_SEQ_WAXPBY = 5,
   KF_SEQ_GEMV = 6,
   KF_SEQ_GEMVT = 7,
-  KF_SEQ_DOT = 8
+  KF_SEQ_DOT = 8,
+  KF_SEQ_SGEMVT = 9
 } kf_seq;
 
 /* Library version string (static storage). */
@@ -175,6 +176,15 @@ kf_status kf_gemver_q(int64_t n, const void* QA, int64_t lda, kf_dtype fmt, cons
 /* GESUMMV (Table 1): y = alpha A x + beta B x.  A, B: m x n with the same
  * leading dimension; x: length n; y: length m.  One launch; x is read once
  * per column strip for both matrices. */
+/* SGEMVT (Table 1): x = beta A^T y + z; w = alpha A x.  A: m x n; y, w:
+ * length m; z, x: length n.  Two launches (w needs all of x: a global
+ * barrier, Section 3.2.2), each one read of A; the second walks each row
+ * group from the rows the first read last, which are then still in L2.
+ * ws: kf_workspace_size(KF_SEQ_SGEMVT, m, n).  Errors: KF_ERR_INVALID_ARG,
+ * KF_ERR_SHAPE, KF_ERR_WORKSPACE. */
+kf_status kf_sgemvt(int64_t m, int64_t n, const float* A, int64_t lda, const float* y, const float* z,
+                    float alpha, float beta, float* x, float* w, void* ws, size_t ws_bytes, void* stream);
+
 kf_status kf_gesummv(int64_t m, int64_t n, const float* A, const float* B, int64_t lda,
                      const float* x, float alpha, float beta, float* y, void* ws, size_t ws_bytes,
                      void* stream);

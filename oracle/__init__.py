@@ -188,6 +188,14 @@ def gesummv(A, B, x, alpha, beta):
     return y
 
 
+def sgemvt(A, y, z, alpha, beta):
+    """SGEMVT of Table 1: returns (x, w) with x = beta A^T y + z and
+    w = alpha A x (the FP64 x), the script's calls in order."""
+    x = gemvt(A, y, alpha=beta, beta=1.0, x0=z)
+    w = gemv(A, x, alpha=alpha)
+    return x, w
+
+
 def atax(A, x):
     """Returns (y, t) with t = A x and y = A^T t."""
     A = _d(A); x = _d(x)

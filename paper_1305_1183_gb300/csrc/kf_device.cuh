@@ -25,6 +25,39 @@ __device__ __forceinline__ uint4 ld_stream16(const void* p) {
   return r;
 }
 
+// L2 eviction-priority policies for the cache-hinted accesses below.
+__device__ __forceinline__ uint64_t l2_policy_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// The streaming 16-byte load with an L2 eviction policy.
+__device__ __forceinline__ uint4 ld_stream16_pol(const void* p, uint64_t pol) {
+  uint4 r;
+  asm("ld.global.L1::no_allocate.L2::cache_hint.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p), "l"(pol));
+  return r;
+}
+
+// 16-byte stores with an L2 eviction policy.
+__device__ __forceinline__ void st_f4_pol(float* p, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_u4_pol(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d),
+               "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ float4 ld_stream_f4(const float* p) {
   uint4 r = ld_stream16(p);
   return make_float4(__uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z),

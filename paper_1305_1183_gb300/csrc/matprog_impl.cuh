@@ -119,7 +119,7 @@ __device__ __forceinline__ int coff(int v, int e, int lane) {
 template <int FMT, int V, bool VEC>
 __device__ __forceinline__ void load_row(const void* A, int64_t lda, int64_t row, bool row_ok,
                                          int64_t col0, int64_t n, int lane,
-                                         float (&a)[V * FmtT<FMT>::CH]) {
+                                         float (&a)[V * FmtT<FMT>::CH], uint64_t pol) {
   constexpr int CH = FmtT<FMT>::CH;
   const char* rowp = static_cast<const char*>(A) + (row * lda) * FmtT<FMT>::BYTES;
 #pragma unroll
@@ -127,7 +127,7 @@ __device__ __forceinline__ void load_row(const void* A, int64_t lda, int64_t row
     if constexpr (VEC) {
       const int64_t c = col0 + coff<CH, V, VEC>(v, 0, lane);
       if (row_ok && c + CH <= n) {
-        decode16<FMT>(ld_stream16(rowp + c * FmtT<FMT>::BYTES), &a[v * CH]);
+        decode16<FMT>(ld_stream16_pol(rowp + c * FmtT<FMT>::BYTES, pol), &a[v * CH]);
       } else {
 #pragma unroll
         for (int e = 0; e < CH; ++e)
@@ -149,7 +149,7 @@ __device__ __forceinline__ void load_row(const void* A, int64_t lda, int64_t row
 // row are assembled element by element (code 0 beyond n).
 template <int FMT, int V>
 __device__ __forceinline__ void load_row_raw(const void* A, int64_t lda, int64_t row, bool row_ok, int64_t col0,
-                                             int64_t n, int lane, uint4 (&q)[V]) {
+                                             int64_t n, int lane, uint4 (&q)[V], uint64_t pol) {
   constexpr int CH = FmtT<FMT>::CH;
   constexpr int BYTES = FmtT<FMT>::BYTES;
   const char* rowp = static_cast<const char*>(A) + (row * lda) * BYTES;
@@ -157,7 +157,7 @@ __device__ __forceinline__ void load_row_raw(const void* A, int64_t lda, int64_t
   for (int v = 0; v < V; ++v) {
     const int64_t c = col0 + coff<CH, V, true>(v, 0, lane);
     if (row_ok && c + CH <= n) {
-      q[v] = ld_stream16(rowp + c * BYTES);
+      q[v] = ld_stream16_pol(rowp + c * BYTES, pol);
     } else {
       uint32_t w[4] = {0u, 0u, 0u, 0u};
       if (row_ok) {
@@ -177,7 +177,7 @@ __device__ __forceinline__ void load_row_raw(const void* A, int64_t lda, int64_t
 
 template <int CH, int V, bool VEC>
 __device__ __forceinline__ void store_row(float* B, int64_t ldb, int64_t row, int64_t col0,
-                                          int64_t n, int lane, const float (&a)[V * CH]) {
+                                          int64_t n, int lane, const float (&a)[V * CH], uint64_t pol) {
   float* rowp = B + row * ldb;
 #pragma unroll
   for (int v = 0; v < V; ++v) {
@@ -186,8 +186,8 @@ __device__ __forceinline__ void store_row(float* B, int64_t ldb, int64_t row, in
       if (c + CH <= n) {
 #pragma unroll
         for (int q = 0; q < CH / 4; ++q)
-          st_stream_f4(rowp + c + 4 * q, make_float4(a[v * CH + 4 * q], a[v * CH + 4 * q + 1],
-                                                     a[v * CH + 4 * q + 2], a[v * CH + 4 * q + 3]));
+          st_f4_pol(rowp + c + 4 * q, make_float4(a[v * CH + 4 * q], a[v * CH + 4 * q + 1],
+                                                  a[v * CH + 4 * q + 2], a[v * CH + 4 * q + 3]), pol);
       } else {
 #pragma unroll
         for (int e = 0; e < CH; ++e)
@@ -231,7 +231,7 @@ __device__ __forceinline__ float decode1(uint32_t c) {
 template <int FMT, int V, bool VEC>
 __device__ __forceinline__ void quant_store_row(void* B, int64_t ldb, int64_t row, bool row_ok, int64_t col0,
                                                 int64_t n, int lane, float (&a)[V * FmtT<FMT>::CH], float sB,
-                                                float isB) {
+                                                float isB, uint64_t pol) {
   constexpr int CH = FmtT<FMT>::CH;
   constexpr int BYTES = FmtT<FMT>::BYTES;
   char* rowp = static_cast<char*>(B) + (row * ldb) * BYTES;
@@ -269,9 +269,7 @@ __device__ __forceinline__ void quant_store_row(void* B, int64_t ldb, int64_t ro
           if constexpr (FMT == FMT_BF16) w[q] = code[2 * q] | (code[2 * q + 1] << 16);
           else w[q] = code[4 * q] | (code[4 * q + 1] << 8) | (code[4 * q + 2] << 16) | (code[4 * q + 3] << 24);
         }
-        asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(rowp + c * BYTES), "r"(w[0]),
-                     "r"(w[1]), "r"(w[2]), "r"(w[3])
-                     : "memory");
+        st_u4_pol(rowp + c * BYTES, w[0], w[1], w[2], w[3], pol);
       } else {
 #pragma unroll
         for (int e = 0; e < CH; ++e) {
@@ -446,6 +444,11 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
   const int64_t nbatch = (u_end - u_begin) * NBU;
 
   const int S = STAGED ? P.stages : 1;
+  const bool rev = P.reverse_rows != 0;
+  // matrix loads: evict-first when the data is read once; matrix output:
+  // kept at normal priority when the next pass reads it, else evict-first
+  const uint64_t lpol = P.l2_loads_first ? l2_policy_first() : l2_policy_normal();
+  const uint64_t spol = P.l2_keep_out ? l2_policy_normal() : l2_policy_first();
   const bool ring = STAGED && (col0 + SW <= n);  // block-uniform
   char* ringp = reinterpret_cast<char*>(smem4);
 
@@ -476,7 +479,8 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
             break;
           }
         }
-        const int64_t rowb = ((u_begin + jj / NBU) << 3) + (jj % NBU) * U;
+        const int64_t unit = rev ? u_end - 1 - jj / NBU : u_begin + jj / NBU;
+        const int64_t rowb = (unit << 3) + (jj % NBU) * U;
         unsigned bytes = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -561,15 +565,16 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
           const int64_t row = row0 + r + u;
 #pragma unroll
           for (int t = 0; t < NMAT; ++t) {
-            if constexpr (RAW) load_row_raw<FMT, V>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u]);
-            else load_row<FMT, V, VEC>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u]);
+            if constexpr (RAW) load_row_raw<FMT, V>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u], lpol);
+            else load_row<FMT, V, VEC>(P.A[t], P.lda[t], row, row < m, wcol0, n, lane, a[t][u], lpol);
           }
         }
       }
     };
 
     int64_t j = 0;  // batch counter (every consumer warp visits every batch)
-    for (int64_t rb = rb_begin; rb < rb_end; ++rb) {
+    for (int64_t ri = 0; ri < rb_end - rb_begin; ++ri) {
+      const int64_t rb = rev ? rb_end - 1 - ri : rb_begin + ri;
       const int64_t row0 = rb << 5;
       const bool lane_row_ok = row0 + lane < m;
       // this lane's row (row0 + lane) belongs to the group: its partials are ours to store
@@ -605,7 +610,8 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
       for (int g = 0; g < NGA; ++g) rowdot[g] = 0.f;
 
 #pragma unroll 1
-      for (int h = 0; h < 4; ++h) {  // four quarters of 8 rows
+      for (int hi = 0; hi < 4; ++hi) {  // four quarters of 8 rows
+        const int h = rev ? 3 - hi : hi;
         const int64_t unit = (rb << 2) + h;
         if (unit < u_begin || unit >= u_end) continue;  // another group's rows
         float dacc[NGA][8];          // per-lane partial dot of each row of the quarter
@@ -695,7 +701,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
                     const int64_t row = row0 + rr;
                     quant_store_row<FMT, V, VEC>(P.Bout[0], P.ldb[0], row, row < m, wcol0, n, lane, ar[0],
                                                  __shfl_sync(FULL_MASK, sbrow, rr),
-                                                 __shfl_sync(FULL_MASK, isbrow, rr));
+                                                 __shfl_sync(FULL_MASK, isbrow, rr), spol);
                   }
                 }
               }
@@ -705,7 +711,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, 
 #pragma unroll
               for (int t = 0; t < NMAT; ++t)
                 if (P.Bout[t] != nullptr)
-                  store_row<CH, V, VEC>(P.Bout[t], P.ldb[t], row, wcol0, n, lane, ar[t]);
+                  store_row<CH, V, VEC>(P.Bout[t], P.ldb[t], row, wcol0, n, lane, ar[t], spol);
             }
           }
         }

@@ -18,7 +18,7 @@ from . import _build
 KF_OK = 0
 KF_F32, KF_BF16_ROWSCALE, KF_FP8E4M3_ROWSCALE = 0, 1, 2
 (KF_SEQ_BICGK, KF_SEQ_GEMVER, KF_SEQ_GESUMMV, KF_SEQ_ATAX, KF_SEQ_AXPYDOT, KF_SEQ_WAXPBY,
- KF_SEQ_GEMV, KF_SEQ_GEMVT, KF_SEQ_DOT) = range(9)
+ KF_SEQ_GEMV, KF_SEQ_GEMVT, KF_SEQ_DOT, KF_SEQ_SGEMVT) = range(10)
 
 (KF_ERR_INVALID_ARG, KF_ERR_SHAPE, KF_ERR_DTYPE, KF_ERR_ALIGN, KF_ERR_CYCLE, KF_ERR_UNDEFINED_VAR, KF_ERR_CUDA,
  KF_ERR_NO_MEM, KF_ERR_DEVICE_TIMEOUT, KF_ERR_UNSUPPORTED, KF_ERR_WORKSPACE) = range(-1, -12, -1)
@@ -56,6 +56,7 @@ _SIGS = {
     "kf_madd": ([i64, i64, vp, i64, vp, i64, vp, i64, vp], ci),
     "kf_gemver_q": ([i64, vp, i64, ci, vp, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, vp, sz, vp], ci),
     "kf_gesummv": ([i64, i64, vp, vp, i64, vp, f32, f32, vp, vp, sz, vp], ci),
+    "kf_sgemvt": ([i64, i64, vp, i64, vp, vp, f32, f32, vp, vp, vp, sz, vp], ci),
     "kf_atax": ([i64, i64, vp, i64, vp, vp, vp, sz, vp], ci),
     "kf_axpydot": ([i64, vp, vp, vp, f32, vp, vp, vp, sz, vp], ci),
     "kf_waxpby": ([i64, f32, vp, f32, vp, vp, vp], ci),
@@ -281,6 +282,14 @@ def kf_gesummv(A, B, x, alpha, beta, y, ws, stream=None):
     assert A.stride(0) == B.stride(0)
     _ck(lib().kf_gesummv(m, n, _p(A), _p(B), A.stride(0), _p(x), alpha, beta, _p(y),
                          _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_sgemvt(A, y, z, alpha, beta, x, w, ws, stream=None):
+    _mat(A)
+    _vec(y, z, x, w)
+    m, n = A.shape
+    _ck(lib().kf_sgemvt(m, n, _p(A), A.stride(0), _p(y), _p(z), alpha, beta, _p(x), _p(w), _p(ws), _nb(ws),
+                        _st(stream)))
 
 
 def kf_atax(A, x, y, ws, stream=None):

@@ -73,6 +73,51 @@ def test_planner_byte_counts_agree_with_the_bench(kf, seq):
         assert fused == bench.algorithmic_bytes(seq, size)
 
 
+def _sgemv(kf, n):
+    s = kf.Script()
+    s.matrix("A", n, n)
+    for v in ("x", "y", "t", "z"):
+        s.vector(v, n)
+    s.input("A", "x", "y"); s.output("z")
+    s.call("GEMV", ["t"], ["A", "x"], [1.5, 0.0])
+    s.call("AXPBY", ["z"], ["t", "y"], [1.0, 1.2])
+    return s
+
+
+def _sgemvt(kf, n):
+    s = kf.Script()
+    s.matrix("A", n, n)
+    for v in ("y", "z", "t", "x", "w"):
+        s.vector(v, n)
+    s.input("A", "y", "z"); s.output("x", "w")
+    s.call("GEMVT", ["t"], ["A", "y"], [1.0, 0.0])
+    s.call("AXPBY", ["x"], ["t", "z"], [1.2, 1.0])
+    s.call("GEMV", ["w"], ["A", "x"], [1.5, 0.0])
+    return s
+
+
+def _vadd(kf, n):
+    s = kf.Script()
+    for v in ("w", "y", "z", "t", "x"):
+        s.vector(v, n)
+    s.input("w", "y", "z"); s.output("x")
+    s.call("AXPBY", ["t"], ["w", "y"], [1.0, 1.0])
+    s.call("AXPBY", ["x"], ["t", "z"], [1.0, 1.0])
+    return s
+
+
+@pytest.mark.parametrize("seq,build,size", [("sgemv", _sgemv, 8192), ("sgemvt", _sgemvt, 8192),
+                                            ("vadd", _vadd, 1 << 26)])
+def test_table1_byte_counts_agree_with_the_planner(kf, seq, build, size):
+    """SGEMV, SGEMVT and VADD: the bench's fused and unfused byte counts are
+    the planner's for the same scripts (SGEMVT fused: two passes over A,
+    since w needs all of x)."""
+    s = build(kf, size)
+    alg, unf = bench.table1_bytes(seq, size)
+    assert s.plan(kf.KF_PLAN_ANALYTIC).describe()["bytes"] == alg
+    assert s.plan(kf.KF_PLAN_UNFUSED).describe()["bytes"] == unf
+
+
 def test_read_probe_section(monkeypatch):
     """The read-only probe times kf_dot over the AXPYDOT vectors and reports
     (8n + 4) bytes per launch; an error becomes an entry, not a crash."""

@@ -168,6 +168,42 @@ def test_gemver_rank_one_closed_form(built):
     assert np.array_equal(host(x), xe)
 
 
+# ------------------------------------------------------------------ SGEMVT
+
+@pytest.mark.parametrize("m,n", [(1, 1), (31, 33), (1000, 1003), (2048, 2048), (513, 4096), (4100, 700)])
+def test_sgemvt_parity(built, m, n):
+    """x = beta A^T y + z, w = alpha A x (Table 1), against the FP64 oracle;
+    w's tolerance takes the longer of its two reduction stages."""
+    kf = built
+    A, y, z = U((m, n), 1), U((m,), 4), U((n,), 9)
+    x = torch.empty(n, device=dev()); w = torch.empty(m, device=dev())
+    kf.kf_sgemvt(A, y, z, ALPHA, BETA, x, w, ws(kf, kf.KF_SEQ_SGEMVT, m, n))
+    Ah, yh, zh = host(A), host(y), host(z)
+    xo, wo = oracle.sgemvt(Ah, yh, zh, ALPHA, BETA)
+    sx = BETA * oracle.abs_gemvt(Ah, yh) + np.abs(zh)
+    check_reduce(host(x), xo, sx, m, "x")
+    sw = ALPHA * oracle.abs_gemv(Ah, np.abs(xo) + sx)
+    check_reduce(host(w), wo, sw, max(m, n), "w")
+
+
+def test_sgemvt_identity_and_empty(built):
+    """A = I: x = beta y + z and w = alpha x exactly for integer inputs with
+    beta = alpha = 2; an empty A gives x = z and w = 0."""
+    kf = built
+    n = 777
+    A = torch.eye(n, device=dev())
+    y, z = I((n,), 4), I((n,), 9)
+    x = torch.empty(n, device=dev()); w = torch.empty(n, device=dev())
+    kf.kf_sgemvt(A, y, z, 2.0, 2.0, x, w, ws(kf, kf.KF_SEQ_SGEMVT, n, n))
+    assert torch.equal(x, 2 * y + z) and torch.equal(w, 2 * x)
+    m, n = 0, 300
+    A = torch.zeros((1, n), device=dev())[:0]
+    z = U((n,), 9)
+    x = torch.full((n,), float("nan"), device=dev())
+    kf.kf_sgemvt(A, None, z, ALPHA, BETA, x, None, ws(kf, kf.KF_SEQ_SGEMVT, 1, n))
+    assert torch.equal(x, z)
+
+
 # ------------------------------------------------------------------ GESUMMV
 
 @pytest.mark.parametrize("m,n", [(1, 1), (31, 33), (1000, 1003), (2048, 2048), (513, 4096)])

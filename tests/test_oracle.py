@@ -409,6 +409,24 @@ def test_gemver_rowscaled_storage_bound(fmt, rel, floor, u2_gain):
     assert np.max(np.abs(B) / (sBd * qmax)) > 1.0 / 3.0
 
 
+def test_sgemvt_identity_and_rank_one():
+    """SGEMVT (Table 1) with A = I gives x = beta y + z, w = alpha x; with
+    A = u v^T, x = beta v (u.y) + z and w = alpha u (v.x) (closed forms)."""
+    n = 9
+    y = synth.uniform((n,), 0, synth.TID["y"]).numpy().astype(np.float64)
+    z = synth.uniform((n,), 0, synth.TID["z"]).numpy().astype(np.float64)
+    x, w = oracle.sgemvt(np.eye(n), y, z, 1.5, 1.2)
+    assert np.allclose(x, 1.2 * y + z, rtol=0, atol=1e-15) and np.allclose(w, 1.5 * x, rtol=0, atol=1e-15)
+    m = 7
+    u = synth.uniform((m,), 0, synth.TID["u1"]).numpy().astype(np.float64)
+    v = synth.uniform((n,), 0, synth.TID["v1"]).numpy().astype(np.float64)
+    yy = synth.uniform((m,), 1, synth.TID["y"]).numpy().astype(np.float64)
+    x, w = oracle.sgemvt(np.outer(u, v), yy, z, 1.5, 1.2)
+    xr = 1.2 * v * (u @ yy) + z
+    assert np.allclose(x, xr, rtol=1e-14, atol=1e-14)
+    assert np.allclose(w, 1.5 * u * (v @ xr), rtol=1e-14, atol=1e-14)
+
+
 def _amax_rule_store(B, fmt):
     """The amax storage rule written out from its definition, independently of
     the oracle: s_i = max_j |B_ij| / QMAX (1 for a zero row), codes rounded to
