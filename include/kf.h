@@ -442,6 +442,51 @@ kf_status kf_plan_time_all(const kf_script* s, int max_plans, void* const* bindi
                            size_t ws_bytes, void* stream, int reps, float* ms, int* count);
 
 /* ------------------------------------------------------------------------
+ * Training the learned cost model (not in the paper, whose predictor is the
+ * additive one of Section 3.2) on plan timings the caller measured with
+ * kf_plan_time / kf_plan_time_all, features from kf_plan_enumerate_info.
+ * Everything runs in the library: the features are standardised as
+ * (f - mean) / (std + 1e-6) (population std, double); the target of sample i
+ * is ln(measured_ms[i]) - analytic_weight * ln(max(analytic_us[i], 1e-3) *
+ * 1e-3), minus the mean target of its script when centre_per_script is set
+ * (script_ids required: only differences between one script's plans decide
+ * a choice); the network (kf_mlp_*, KF_PLAN_NFEATURES -> 64 -> 64 -> 1)
+ * starts from params_init (device, may be NULL) or from He-uniform weights
+ * u * sqrt(6 / fan_in) with zero biases, u the SplitMix64 stream of `seed`
+ * (counter-based, stream id 15) at the parameter's index; then `epochs`
+ * full-batch Adam steps (kf_mlp_loss_grad, kf_mlp_adam).
+ *   features     host, count x KF_PLAN_NFEATURES, row major
+ *   measured_ms  host, count (> 0);  analytic_us: host, count
+ *   script_ids   host, count, or NULL
+ *   params       device output, kf_mlp_param_count(16, 64) floats
+ *   ws           device, kf_planner_train_workspace_size bytes
+ *   model        output: params = `params`, the standardisation and
+ *                analytic_weight, ready for kf_plan_select
+ *   loss_out     host, loss_cap floats (may be NULL with loss_cap 0): the
+ *                mean squared error before step 1, every loss_every steps,
+ *                and after the last step; *n_loss (may be NULL) the count.
+ * Synchronous on `stream`.  Errors: KF_ERR_INVALID_ARG (sizes, options, a
+ * non-positive time), KF_ERR_WORKSPACE, KF_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+#define KF_PLAN_NFEATURES 16
+
+typedef struct {
+  int epochs;             /* full-batch Adam steps (>= 1)                      */
+  float lr;               /* Adam step size                                   */
+  float beta1, beta2, eps;
+  float analytic_weight;  /* weight of ln(analytic ms) in the target and score */
+  int centre_per_script;  /* centre the targets per script (needs script_ids) */
+  int loss_every;         /* record the loss every this many steps (0: no)   */
+  uint64_t seed;          /* initial weights when params_init is NULL         */
+} kf_train_options;
+
+kf_status kf_planner_train_workspace_size(int count, int d_in, size_t* bytes);
+kf_status kf_planner_train(const float* features, const double* measured_ms, const double* analytic_us,
+                           const int64_t* script_ids, int count, int d_in, const kf_train_options* opt,
+                           const float* params_init, float* params, void* ws, size_t ws_bytes, void* stream,
+                           kf_cost_model* model, float* loss_out, int loss_cap, int* n_loss);
+
+/* ------------------------------------------------------------------------
  * Autotuning (Section 3.2: block size and serial iterations are part of a
  * fusion implementation; routines are benchmarked once per architecture).
  * kf_autotune_plan runs, for every kernel of the plan on the bound data,

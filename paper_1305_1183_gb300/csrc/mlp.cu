@@ -19,7 +19,12 @@
 //   adam      : element-wise update with bias correction.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
 #include <string>
+#include <vector>
 
 #include "../../include/kf.h"
 #include "kf_device.cuh"
@@ -278,6 +283,209 @@ kf_status kf_mlp_adam(float* params, const float* grad, float* m, float* v, int 
                                                                           c1, c2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return KF_ERR_CUDA; }
+  return KF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- training
+
+namespace kf {
+namespace {
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) used counter-style: the key
+// of stream (seed, id) is mix(mix(seed) + id), element i is
+// mix(key + (i + 1) * GAMMA); its top 24 bits b give b * 2^-23 - 1 in [-1, 1).
+constexpr uint64_t SM_GAMMA = 0x9E3779B97F4A7C15ull;
+uint64_t sm_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+constexpr uint64_t INIT_STREAM_ID = 15;  // the network's stream
+
+float sm_uniform(uint64_t key, uint64_t i) {
+  const uint64_t b = sm_mix(key + (i + 1) * SM_GAMMA) >> 40;
+  return (float)b * (1.0f / 8388608.0f) - 1.0f;
+}
+
+size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct TrainLayout {
+  size_t xs, y, grad, m, v, loss, mlpws, total;
+};
+
+TrainLayout train_layout(int count, int d) {
+  TrainLayout L{};
+  const size_t np = (size_t)n_params(d);
+  size_t mlp = 0;
+  kf_mlp_workspace_size(d, H, count, &mlp);
+  size_t off = 0;
+  L.xs = off; off += al256((size_t)count * d * sizeof(float));
+  L.y = off; off += al256((size_t)count * sizeof(float));
+  L.grad = off; off += al256(np * sizeof(float));
+  L.m = off; off += al256(np * sizeof(float));
+  L.v = off; off += al256(np * sizeof(float));
+  L.loss = off; off += 256;
+  L.mlpws = off; off += al256(mlp);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+}  // namespace kf
+
+extern "C" {
+
+kf_status kf_planner_train_workspace_size(int count, int d_in, size_t* bytes) {
+  if (bytes == nullptr || count < 1 || d_in != KF_PLAN_NFEATURES) {
+    set_error_message("count >= 1 samples of KF_PLAN_NFEATURES features expected");
+    return KF_ERR_INVALID_ARG;
+  }
+  *bytes = train_layout(count, d_in).total;
+  return KF_OK;
+}
+
+kf_status kf_planner_train(const float* features, const double* measured_ms, const double* analytic_us,
+                           const int64_t* script_ids, int count, int d_in, const kf_train_options* opt,
+                           const float* params_init, float* params, void* ws, size_t ws_bytes, void* stream,
+                           kf_cost_model* model, float* loss_out, int loss_cap, int* n_loss) {
+  if (features == nullptr || measured_ms == nullptr || analytic_us == nullptr || opt == nullptr ||
+      params == nullptr || model == nullptr || count < 1 || d_in != KF_PLAN_NFEATURES) {
+    set_error_message("null argument, no samples, or not KF_PLAN_NFEATURES features");
+    return KF_ERR_INVALID_ARG;
+  }
+  if (opt->epochs < 1 || !(opt->lr > 0.f) || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) ||
+      !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || !(opt->eps > 0.f) || opt->loss_every < 0 ||
+      (opt->centre_per_script && script_ids == nullptr) || (loss_cap > 0 && loss_out == nullptr)) {
+    set_error_message("bad training options");
+    return KF_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < count; ++i) {
+    if (!(measured_ms[i] > 0.0) || !std::isfinite(measured_ms[i]) || !std::isfinite(analytic_us[i])) {
+      set_error_message("measured times must be positive and finite");
+      return KF_ERR_INVALID_ARG;
+    }
+  }
+  const int d = d_in;
+  const TrainLayout L = train_layout(count, d);
+  if (ws == nullptr || ws_bytes < L.total) {
+    set_error_message("workspace missing or smaller than kf_planner_train_workspace_size()");
+    return KF_ERR_WORKSPACE;
+  }
+  const int np = n_params(d);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = static_cast<char*>(ws);
+  float* dX = reinterpret_cast<float*>(w + L.xs);
+  float* dy = reinterpret_cast<float*>(w + L.y);
+  float* dg = reinterpret_cast<float*>(w + L.grad);
+  float* dm = reinterpret_cast<float*>(w + L.m);
+  float* dv = reinterpret_cast<float*>(w + L.v);
+  float* dloss = reinterpret_cast<float*>(w + L.loss);
+  void* dmlp = w + L.mlpws;
+  size_t mlp_bytes = L.total - L.mlpws;
+
+  // Feature standardisation: (f - mean) / (population std + 1e-6), in double.
+  std::vector<double> mean(d, 0.0), sd(d, 0.0);
+  for (int i = 0; i < count; ++i)
+    for (int c = 0; c < d; ++c) mean[c] += features[(size_t)i * d + c];
+  for (int c = 0; c < d; ++c) mean[c] /= count;
+  for (int i = 0; i < count; ++i)
+    for (int c = 0; c < d; ++c) {
+      const double t = features[(size_t)i * d + c] - mean[c];
+      sd[c] += t * t;
+    }
+  std::vector<double> inv(d);
+  for (int c = 0; c < d; ++c) inv[c] = 1.0 / (std::sqrt(sd[c] / count) + 1e-6);
+  std::vector<float> Xs((size_t)count * d);
+  for (int i = 0; i < count; ++i)
+    for (int c = 0; c < d; ++c) Xs[(size_t)i * d + c] = (float)((features[(size_t)i * d + c] - mean[c]) * inv[c]);
+  // Targets: ln(measured ms) - w ln(analytic ms) (analytic floored at 1 ns),
+  // centred per script when asked (only differences between one script's
+  // plans decide a choice).
+  std::vector<double> tgt(count);
+  for (int i = 0; i < count; ++i)
+    tgt[i] = std::log(measured_ms[i]) - (double)opt->analytic_weight * std::log(std::max(analytic_us[i], 1e-3) * 1e-3);
+  if (opt->centre_per_script) {
+    std::map<int64_t, std::pair<double, int>> acc;
+    for (int i = 0; i < count; ++i) {
+      auto& a = acc[script_ids[i]];
+      a.first += tgt[i];
+      a.second += 1;
+    }
+    for (int i = 0; i < count; ++i) {
+      const auto& a = acc[script_ids[i]];
+      tgt[i] -= a.first / a.second;
+    }
+  }
+  std::vector<float> y(count);
+  for (int i = 0; i < count; ++i) y[i] = (float)tgt[i];
+
+  cudaError_t e = cudaMemcpyAsync(dX, Xs.data(), Xs.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y.data(), y.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  // Initial weights: the caller's, or He-uniform (u * sqrt(6 / fan_in), u from
+  // the SplitMix64 stream (seed, 15) at the parameter's index) with zero biases.
+  std::vector<float> init;
+  if (e == cudaSuccess) {
+    if (params_init != nullptr) {
+      e = cudaMemcpyAsync(params, params_init, (size_t)np * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    } else {
+      init.assign(np, 0.f);
+      const uint64_t key = sm_mix(sm_mix(opt->seed) + INIT_STREAM_ID);
+      const Layout Lp = layout(d);
+      auto fill = [&](int off, int count_w, int fan_in) {
+        const double g = std::sqrt(6.0 / fan_in);
+        for (int k = 0; k < count_w; ++k)
+          init[off + k] = (float)((double)sm_uniform(key, (uint64_t)(off + k)) * g);
+      };
+      fill(Lp.w1, H * d, d);
+      fill(Lp.w2, H * H, H);
+      fill(Lp.w3, H, H);
+      e = cudaMemcpyAsync(params, init.data(), (size_t)np * sizeof(float), cudaMemcpyHostToDevice, st);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(dm, 0, (size_t)np * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dv, 0, (size_t)np * sizeof(float), st);
+  if (e != cudaSuccess) {
+    set_error_message(std::string("training set-up: ") + cudaGetErrorString(e));
+    return KF_ERR_CUDA;
+  }
+  int nl = 0;
+  auto record = [&]() -> kf_status {
+    float h = 0.f;
+    cudaError_t r = cudaMemcpyAsync(&h, dloss, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+    if (r != cudaSuccess) {
+      set_error_message(std::string("reading the loss: ") + cudaGetErrorString(r));
+      return KF_ERR_CUDA;
+    }
+    if (nl < loss_cap) loss_out[nl] = h;
+    ++nl;
+    return KF_OK;
+  };
+  // Full-batch Adam (Kingma and Ba, Algorithm 1), every step in the
+  // library's kernels.
+  for (int t = 1; t <= opt->epochs; ++t) {
+    kf_status sst = kf_mlp_loss_grad(params, d, H, dX, dy, count, dg, dloss, dmlp, mlp_bytes, stream);
+    if (sst != KF_OK) return sst;
+    if (t == 1 || (opt->loss_every > 0 && t % opt->loss_every == 0)) {
+      sst = record();
+      if (sst != KF_OK) return sst;
+    }
+    sst = kf_mlp_adam(params, dg, dm, dv, np, t, opt->lr, opt->beta1, opt->beta2, opt->eps, stream);
+    if (sst != KF_OK) return sst;
+  }
+  kf_status sst = kf_mlp_loss_grad(params, d, H, dX, dy, count, dg, dloss, dmlp, mlp_bytes, stream);
+  if (sst != KF_OK) return sst;
+  sst = record();
+  if (sst != KF_OK) return sst;
+  if (n_loss != nullptr) *n_loss = nl;
+  model->params = params;
+  for (int c = 0; c < KF_PLAN_NFEATURES; ++c) {
+    model->mean[c] = (float)mean[c];
+    model->inv_std[c] = (float)inv[c];
+  }
+  model->analytic_weight = opt->analytic_weight;
   return KF_OK;
 }
 

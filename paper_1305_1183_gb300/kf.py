@@ -122,6 +122,10 @@ _SIGS = {
     "kf_plan_select": ([vp, vp, vp, ctypes.POINTER(vp), ci, vp, sz, vp, ctypes.POINTER(vp), vp], ci),
     "kf_plan_time_all": ([vp, ci, ctypes.POINTER(vp), ci, vp, sz, vp, ci, ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ci)], ci),
+    "kf_planner_train_workspace_size": ([ci, ci, ctypes.POINTER(sz)], ci),
+    "kf_planner_train": ([ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ci, ci, vp, vp, vp, vp,
+                          sz, vp, vp, ctypes.POINTER(ctypes.c_float), ci, ctypes.POINTER(ci)], ci),
 }
 
 
@@ -761,6 +765,48 @@ def kf_mlp_forward(params, X, out, hidden=MLP_HIDDEN, stream=None):
 def kf_mlp_loss_grad(params, X, y, grad, loss, ws, hidden=MLP_HIDDEN, stream=None):
     _ck(lib().kf_mlp_loss_grad(_p(params), X.shape[1], hidden, _p(X), _p(y), X.shape[0], _p(grad), _p(loss),
                                _p(ws), _nb(ws), _st(stream)))
+
+
+class _TrainOptions(ctypes.Structure):
+    _fields_ = [("epochs", ci), ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("analytic_weight", ctypes.c_float), ("centre_per_script", ci),
+                ("loss_every", ci), ("seed", ctypes.c_uint64)]
+
+
+def kf_planner_train_workspace_size(count, d_in=NFEATURES):
+    b = sz(0)
+    _ck(lib().kf_planner_train_workspace_size(count, d_in, ctypes.byref(b)))
+    return b.value
+
+
+def kf_planner_train(X, ms, analytic_us, script_ids=None, epochs=3000, lr=3e-3, b1=0.9, b2=0.999, eps=1e-8,
+                     analytic_weight=1.0, centre=True, loss_every=500, seed=0, params_init=None, device="cuda",
+                     stream=None):
+    """Train the plan cost model in the library (kf_planner_train): host
+    arrays in, a CostModel (device parameters, standardisation) and the
+    recorded losses [(step, loss)] out."""
+    import numpy as np
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    count, d = X.shape
+    msd = np.ascontiguousarray(ms, dtype=np.float64)
+    pud = np.ascontiguousarray(analytic_us, dtype=np.float64)
+    sid = None if script_ids is None else np.ascontiguousarray(script_ids, dtype=np.int64)
+    params = torch.empty(kf_mlp_param_count(d), dtype=torch.float32, device=device)
+    ws = torch.empty(kf_planner_train_workspace_size(count, d), dtype=torch.uint8, device=device)
+    opt = _TrainOptions(epochs, lr, b1, b2, eps, analytic_weight, 1 if centre else 0, loss_every, seed)
+    cap = epochs // loss_every + 2 if loss_every > 0 else 2
+    losses = (ctypes.c_float * cap)()
+    nl = ci(0)
+    cm = _CostModel()
+    fp, dp = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
+    _ck(lib().kf_planner_train(X.ctypes.data_as(fp), msd.ctypes.data_as(dp), pud.ctypes.data_as(dp),
+                               None if sid is None else sid.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                               count, d, ctypes.byref(opt), _p(params_init), _p(params), _p(ws), _nb(ws),
+                               _st(stream), ctypes.byref(cm), losses, cap, ctypes.byref(nl)))
+    steps = [1] + ([t for t in range(loss_every, epochs + 1, loss_every)] if loss_every > 0 else []) + [epochs + 1]
+    hist = list(zip(steps, [float(losses[i]) for i in range(min(nl.value, cap))]))
+    model = CostModel(params, list(cm.mean), list(cm.inv_std), cm.analytic_weight)
+    return model, hist
 
 
 def kf_mlp_adam(params, grad, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):

@@ -153,7 +153,9 @@ def load_timings(path, key):
 
 
 def he_uniform_params(d_in, seed, device):
-    """He-uniform weights from the seeded generator, zero biases (kf_mlp layout)."""
+    """He-uniform weights from the seeded generator, zero biases (kf_mlp
+    layout): the initial weights kf_planner_train draws itself when given
+    none, here for tests that train step by step."""
     H = kf.MLP_HIDDEN
     count = kf.kf_mlp_param_count(d_in)
     u = synth.uniform((count,), seed, synth.TID["mlp"]).double()
@@ -168,38 +170,15 @@ def he_uniform_params(d_in, seed, device):
 
 
 def train(X, ms, pred_us, script_ids=None, analytic_weight=1.0, epochs=3000, lr=3e-3, seed=0, device="cuda"):
-    """Full-batch Adam, all steps in libkf kernels, on standardised features.
-    Target: ln(ms) - analytic_weight * ln(analytic ms), so that with weight
-    1 the network learns the analytic model's error and the score
-    ln(analytic ms) + f(x) ranks plans.  With script ids the target is
-    centred per script: only differences between the plans of one script
-    decide a choice, so the script's common level is removed from what the
-    network has to fit.  Returns (CostModel, loss history)."""
-    mean = X.mean(axis=0)
-    inv_std = 1.0 / (X.std(axis=0) + 1e-6)
-    Xs = torch.tensor((X - mean) * inv_std, dtype=torch.float32, device=device)
-    target = np.log(ms) - analytic_weight * np.log(np.maximum(pred_us, 1e-3) * 1e-3)
-    if script_ids is not None:
-        for sidv in np.unique(script_ids):
-            sel = script_ids == sidv
-            target[sel] -= target[sel].mean()
-    yt = torch.tensor(target, dtype=torch.float32, device=device)
-    d = X.shape[1]
-    p = he_uniform_params(d, seed, device)
-    g = torch.empty_like(p)
-    m = torch.zeros_like(p)
-    v = torch.zeros_like(p)
-    loss = torch.empty(1, device=device)
-    ws = torch.zeros(kf.kf_mlp_workspace_size(d, X.shape[0]), dtype=torch.uint8, device=device)
-    hist = []
-    for t in range(1, epochs + 1):
-        kf.kf_mlp_loss_grad(p, Xs, yt, g, loss, ws)
-        if t == 1 or t % 500 == 0:
-            hist.append((t, float(loss)))
-        kf.kf_mlp_adam(p, g, m, v, t, lr=lr)
-    kf.kf_mlp_loss_grad(p, Xs, yt, g, loss, ws)
-    hist.append((epochs + 1, float(loss)))
-    return kf.CostModel(p, mean, inv_std, analytic_weight), hist
+    """Train the cost model with the library's kf_planner_train: it
+    standardises the features, forms the targets ln(ms) - analytic_weight *
+    ln(analytic ms) (centred per script when script ids are given: only
+    differences between one script's plans decide a choice), draws the
+    initial weights and runs full-batch Adam, all in libkf.  With weight 1
+    the network learns the analytic model's error and the score
+    ln(analytic ms) + f(x) ranks plans.  Returns (CostModel, loss history)."""
+    return kf.kf_planner_train(X, ms, pred_us, script_ids, epochs=epochs, lr=lr, analytic_weight=analytic_weight,
+                               centre=script_ids is not None, loss_every=500, seed=seed, device=device)
 
 
 def evaluate(seed, indices, kmin, kmax, model, reps, top_k=3, cap=2000, margin=0.1, device="cuda"):

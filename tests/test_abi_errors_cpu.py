@@ -328,3 +328,32 @@ def test_wait_limit_and_probe_errors(L, K):
     assert L.kf_wait_probe(5000, None, 0, None, None) == K.KF_ERR_WORKSPACE
     assert L.kf_wait_probe(5000, P, 255, None, None) == K.KF_ERR_WORKSPACE
     assert L.kf_wait_probe(10, P, 256, None, None) == K.KF_ERR_INVALID_ARG
+
+
+def test_planner_train_errors(L, K):
+    """kf_planner_train checks its sizes, options and times before any
+    device work."""
+    import numpy as np
+    n, d = 8, 16
+    X = np.zeros((n, d), np.float32)
+    ms = np.ones(n)
+    pu = np.ones(n)
+    fp, dp = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
+    cm = K._CostModel()
+
+    def call(opt, d_in=d, count=n, ms_=ms, sid=None, ws=P, wsb=1 << 30):
+        return L.kf_planner_train(X.ctypes.data_as(fp), ms_.ctypes.data_as(dp), pu.ctypes.data_as(dp), sid,
+                                  count, d_in, ctypes.byref(opt), None, P, ws, wsb, None, ctypes.byref(cm), None,
+                                  0, None)
+    good = K._TrainOptions(10, 1e-3, 0.9, 0.999, 1e-8, 1.0, 0, 0, 0)
+    assert call(good, d_in=15) == K.KF_ERR_INVALID_ARG
+    assert call(good, count=0) == K.KF_ERR_INVALID_ARG
+    assert call(K._TrainOptions(0, 1e-3, 0.9, 0.999, 1e-8, 1.0, 0, 0, 0)) == K.KF_ERR_INVALID_ARG   # no epochs
+    assert call(K._TrainOptions(10, 1e-3, 1.0, 0.999, 1e-8, 1.0, 0, 0, 0)) == K.KF_ERR_INVALID_ARG  # beta1
+    assert call(K._TrainOptions(10, 1e-3, 0.9, 0.999, 1e-8, 1.0, 1, 0, 0)) == K.KF_ERR_INVALID_ARG  # centring, no ids
+    bad = ms.copy(); bad[3] = 0.0
+    assert call(good, ms_=bad) == K.KF_ERR_INVALID_ARG                                                 # time 0
+    assert call(good, ws=None, wsb=0) == K.KF_ERR_WORKSPACE
+    b = ctypes.c_size_t(0)
+    assert L.kf_planner_train_workspace_size(n, d, ctypes.byref(b)) == 0 and b.value > n * d * 4
+    assert L.kf_planner_train_workspace_size(n, 12, ctypes.byref(b)) == K.KF_ERR_INVALID_ARG
