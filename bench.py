@@ -866,11 +866,12 @@ def learned_planner_section(device, scripts=80, ntrain=60, kmin=10, kmax=13, per
     res, _ = learn.run(seed=0, scripts=scripts, ntrain=ntrain, kmin=kmin, kmax=kmax, per_script=per_script,
                        reps=reps, epochs=epochs, top_k=3, device=device, log=None)
     names = {"mlp": "learned model, first choice (no timing)", "mlp_topk": "learned model, top 3 re-timed",
+             "mlp_top2k": "learned model, top 6 re-timed",
              "mlp_margin": "learned model, top 3 and scores within 0.1 re-timed",
              "analytic": "analytic predictor max(t_t, t_c) + launch cost", "greedy": "fewest kernels",
              "unfused": "one kernel per call"}
     return {"config": res["config"], "seconds": round(time.time() - t0, 1),
-            "test": {names[k]: v for k, v in res["test"].items()},
+            "test": {names.get(k, k): v for k, v in res["test"].items()},
             "plans_timed_per_test_script": res["timed_per_script"],
             "plans_per_test_script": res["test_plans_per_script"],
             "train_plans_timed": res["train_plans_timed"]}

@@ -16,8 +16,8 @@ namespace kf {
 
 bool atax_single_pass_ok(int64_t m, int64_t n, int64_t lda, const void* A, const void* x, const void* y);
 size_t atax_workspace_bytes(int64_t n);
-int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, void* ws,
-                      size_t ws_bytes, void* stream, const char** why);
+int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, float scale,
+                      void* ws, size_t ws_bytes, void* stream, const char** why);
 int launch_madd_strided(int64_t m, int64_t n, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
                         int64_t ldc, void* stream, const char** why);
 int launch_quantize_rows(const float* A, int64_t lda, int64_t m, int64_t n, int fmt, void* Q,
@@ -178,6 +178,47 @@ kf_status check_vec(int64_t len, const void* p, const char* name) {
 
 }  // namespace
 
+namespace kf {
+
+size_t atax_plan_workspace_bytes(int64_t m, int64_t n) {
+  return std::max(atax_workspace_bytes(n),
+                  256 + align256((size_t)m * sizeof(float)) + matprog_workspace_bytes(m, n, 1, 1, FMT_F32));
+}
+
+// y = scale * A^T (A x).  One read of A when the rows fit the shared-memory
+// ring and are 16-byte aligned; else the paper's two passes, t = A x into
+// the workspace (after its first 256 bytes, the device error word), then
+// y = scale * A^T t.
+int atax_run(int64_t m, int64_t n, const float* A, int64_t lda, const float* x, float* y, float scale, void* ws,
+             size_t ws_bytes, void* stream) {
+  if (n == 0) return KF_OK;
+  if (atax_single_pass_ok(m, n, lda, A, x, y)) {
+    const char* why = nullptr;
+    if (ws == nullptr) return fail(KF_ERR_WORKSPACE, "workspace required");
+    return from_launch(launch_atax_tuned(A, lda, m, n, x, y, scale, ws, ws_bytes, stream, &why), why);
+  }
+  REQ(ws != nullptr, KF_ERR_WORKSPACE, "workspace required");
+  float* t = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
+  const size_t toff = 256 + align256((size_t)m * sizeof(float));
+  REQ(ws_bytes >= toff, KF_ERR_WORKSPACE, "workspace too small");
+  void* ws2 = static_cast<char*>(ws) + toff;
+  const size_t ws2b = ws_bytes - toff;
+  MatProg P = new_prog(m, n);
+  P.nmat = 1; P.fmt = FMT_F32; P.A[0] = A; P.lda[0] = lda;
+  P.nops = 1; P.ops[0] = op_gemv(0, 0, x);
+  P.nrow_res = 1; P.ncol_res = 1;
+  P.nrow_out = m > 0 ? 1 : 0; P.row_out[0] = epi1(t, 1.f);
+  if (m > 0) CHK(run_mat(P, ws2, ws2b, stream));
+  MatProg Q = new_prog(m, n);
+  Q.nmat = 1; Q.fmt = FMT_F32; Q.A[0] = A; Q.lda[0] = lda;
+  Q.nops = 1; Q.ops[0] = op_gemvt(0, 0, t);
+  Q.nrow_res = 1; Q.ncol_res = 1;
+  Q.ncol_out = 1; Q.col_out[0] = epi1(y, scale);
+  return run_mat(Q, ws2, ws2b, stream);
+}
+
+}  // namespace kf
+
 extern "C" {
 
 const char* kf_version(void) { return "kf 0.1.0 (sm_103a)"; }
@@ -199,10 +240,7 @@ kf_status kf_workspace_size(kf_seq seq, int64_t m, int64_t n, kf_dtype fmt, size
     case KF_SEQ_BICGK: *bytes = matprog_workspace_bytes(m, n, 1, 1, f); break;
     case KF_SEQ_GEMVER: *bytes = matprog_workspace_bytes(n, n, 1, 1, f); break;
     case KF_SEQ_GESUMMV: *bytes = matprog_workspace_bytes(m, n, 2, 0, f); break;
-    case KF_SEQ_ATAX:
-      *bytes = std::max(atax_workspace_bytes(n),
-                        256 + align256((size_t)m * sizeof(float)) + matprog_workspace_bytes(m, n, 1, 1, f));
-      break;
+    case KF_SEQ_ATAX: *bytes = atax_plan_workspace_bytes(m, n); break;
     case KF_SEQ_AXPYDOT:
     case KF_SEQ_DOT: *bytes = vecprog_workspace_bytes(1); break;
     case KF_SEQ_SGEMVT: *bytes = matprog_workspace_bytes(m, n, 1, 1, f); break;
@@ -395,31 +433,7 @@ kf_status kf_atax(int64_t m, int64_t n, const float* A, int64_t lda, const float
   CHK(check_mat(m, n, A, lda));
   CHK(check_vec(n, x, "x")); CHK(check_vec(n, y, "y"));
   if (n == 0) return KF_OK;
-  if (atax_single_pass_ok(m, n, lda, A, x, y)) {
-    const char* why = nullptr;
-    if (ws == nullptr) return fail(KF_ERR_WORKSPACE, "workspace required");
-    return from_launch(launch_atax_tuned(A, lda, m, n, x, y, ws, ws_bytes, stream, &why), why);
-  }
-  // Two passes (the paper's form): t = A x, then y = A^T t.
-  // The first 256 bytes stay reserved for the device error word.
-  REQ(ws != nullptr, KF_ERR_WORKSPACE, "workspace required");
-  float* t = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
-  const size_t toff = 256 + align256((size_t)m * sizeof(float));
-  REQ(ws_bytes >= toff, KF_ERR_WORKSPACE, "workspace too small");
-  void* ws2 = static_cast<char*>(ws) + toff;
-  const size_t ws2b = ws_bytes - toff;
-  MatProg P = new_prog(m, n);
-  P.nmat = 1; P.fmt = FMT_F32; P.A[0] = A; P.lda[0] = lda;
-  P.nops = 1; P.ops[0] = op_gemv(0, 0, x);
-  P.nrow_res = 1; P.ncol_res = 1;
-  P.nrow_out = m > 0 ? 1 : 0; P.row_out[0] = epi1(t, 1.f);
-  if (m > 0) CHK(run_mat(P, ws2, ws2b, stream));
-  MatProg Q = new_prog(m, n);
-  Q.nmat = 1; Q.fmt = FMT_F32; Q.A[0] = A; Q.lda[0] = lda;
-  Q.nops = 1; Q.ops[0] = op_gemvt(0, 0, t);
-  Q.nrow_res = 1; Q.ncol_res = 1;
-  Q.ncol_out = 1; Q.col_out[0] = epi1(y, 1.f);
-  return run_mat(Q, ws2, ws2b, stream);
+  return kf::atax_run(m, n, A, lda, x, y, 1.f, ws, ws_bytes, stream);
 }
 
 kf_status kf_axpydot(int64_t n, const float* w, const float* v, const float* u, float alpha,

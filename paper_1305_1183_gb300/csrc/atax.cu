@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(NT, VA <= 4 ? 2 : 1) atax_rows_kernel(const fl
 constexpr int FIN_COLS = 4, FIN_SLICES = 64, FIN_LOADS = 5;
 
 __global__ void __launch_bounds__(FIN_COLS * FIN_SLICES) atax_finish_kernel(const float* __restrict__ ypart,
-                                                                            int nparts, int64_t n,
+                                                                            int nparts, int64_t n, float scale,
                                                                             float* __restrict__ y) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ float4 sh[FIN_SLICES][FIN_COLS];
@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(FIN_COLS * FIN_SLICES) atax_finish_kernel(cons
     for (int q = 1; q < FIN_SLICES; ++q) {
       r.x += sh[q][col].x; r.y += sh[q][col].y; r.z += sh[q][col].z; r.w += sh[q][col].w;
     }
+    r.x *= scale; r.y *= scale; r.z *= scale; r.w *= scale;
     reinterpret_cast<float4*>(y)[c4] = r;
   }
 }
@@ -278,7 +279,7 @@ size_t atax_workspace_bytes(int64_t n) {
 
 int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y,
                        void* ws, size_t ws_bytes, int stages_req, int ctas_per_sm, void* stream,
-                       const char** why, int rows_per_round, bool cluster) {
+                       const char** why, int rows_per_round, bool cluster, float scale) {
   const int VA = (int)((n / 4 + 511) / 512);
   const int va = VA <= 1 ? 1 : (VA <= 2 ? 2 : (VA <= 4 ? 4 : 8));
   const int64_t rowcap = (n + 31) / 32 * 32;  // 128-byte aligned stages
@@ -379,7 +380,7 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const float* yp = ypart;
-  e = cudaLaunchKernelEx(&cfg, atax_finish_kernel, yp, nparts, n, y);
+  e = cudaLaunchKernelEx(&cfg, atax_finish_kernel, yp, nparts, n, scale, y);
   if (e != cudaSuccess) { *why = cudaGetErrorString(e); return -7; }
   return 0;
 }
@@ -393,8 +394,8 @@ int launch_atax_single(const float* A, int64_t lda, int64_t m, int64_t n, const 
 // timed on the call's operands (mean of back-to-back launches, best of two
 // rounds) and the fastest stored, unless it gains less than 2 % over the
 // built-in choice.
-int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, void* ws,
-                      size_t ws_bytes, void* stream, const char** why) {
+int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, float scale,
+                      void* ws, size_t ws_bytes, void* stream, const char** why) {
   auto cls = [](int64_t v) {
     int b = 0;
     while (b < 62 && (int64_t(1) << (b + 1)) <= v) ++b;
@@ -411,7 +412,7 @@ int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const f
       cudaEventCreate(&a);
       cudaEventCreate(&b);
       auto run = [&](int stg, int cps, int rp, bool cl) {
-        return launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, stg, cps, stream, why, rp, cl);
+        return launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, stg, cps, stream, why, rp, cl, scale);
       };
       auto time_it = [&](int stg, int cps, int rp, bool cl) {
         float tb = 1e30f;
@@ -456,7 +457,7 @@ int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const f
     }
   }
   return launch_atax_single(A, lda, m, n, x, y, ws, ws_bytes, t.stages, t.groups, stream, why,
-                            t.unroll == 2 ? 2 : 1, t.vec != 2);
+                            t.unroll == 2 ? 2 : 1, t.vec != 2, scale);
 }
 
 }  // namespace kf

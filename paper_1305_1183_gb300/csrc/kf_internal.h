@@ -147,6 +147,14 @@ void matprog_geometry(MatProg& P, const MatTune& t, int sm_count, int* threads, 
 
 int device_sm_count();
 
+// ATAX, y = scale * A^T (A x): the single pass when the shape and pointers
+// allow it, else the two matrix passes; workspace as kf_workspace_size's
+// KF_SEQ_ATAX (atax_plan_workspace_bytes).
+// Returns a kf_status; the calling thread's error message is set on failure.
+int atax_run(int64_t m, int64_t n, const float* A, int64_t lda, const float* x, float* y, float scale, void* ws,
+             size_t ws_bytes, void* stream);
+size_t atax_plan_workspace_bytes(int64_t m, int64_t n);
+
 // Bound of the kernels' waits on data (kf_set_wait_limit_ns; 1 s by default).
 uint64_t wait_limit_ns();
 

@@ -87,6 +87,18 @@ size_t plan_vec_region() { return (vecprog_workspace_bytes(VP_MAXDOT) + 255) & ~
 // Bind variable pointers into a copy of a kernel's program and launch it.
 kf_status launch_kernel(const Kernel& K, void* const* bindings, int nb, void* ws, size_t ws_bytes, void* stream,
                         const MatTune& tune) {
+  if (K.is_atax) {
+    void* p[3] = {nullptr, nullptr, nullptr};
+    for (auto& b : K.bind) {
+      if (b.second < 0 || b.second >= nb || bindings[b.second] == nullptr)
+        return err(KF_ERR_INVALID_ARG, "variable " + std::to_string(b.second) + " is not bound");
+      p[(size_t)(uintptr_t)b.first] = bindings[b.second];
+    }
+    char* wsm = ws ? static_cast<char*>(ws) + plan_vec_region() : nullptr;
+    const size_t wsm_bytes = ws_bytes > plan_vec_region() ? ws_bytes - plan_vec_region() : 0;
+    return atax_run(K.m, K.n, static_cast<const float*>(p[0]), K.n, static_cast<const float*>(p[1]),
+                    static_cast<float*>(p[2]), K.atax_scale, wsm, wsm_bytes, stream);
+  }
   if (K.is_mat) {
     MatProg P = K.mp;
     for (auto& b : K.bind) {
@@ -133,7 +145,11 @@ kf_status check_kernel(const Kernel& K, void* const* bindings, int nb, void* ws,
   for (auto& b : K.bind)
     if (b.second < 0 || b.second >= nb || bindings[b.second] == nullptr)
       return err(KF_ERR_INVALID_ARG, "variable " + std::to_string(b.second) + " is not bound");
-  if (K.is_mat) {
+  if (K.is_atax) {
+    const size_t need = plan_vec_region() + atax_plan_workspace_bytes(K.m, K.n);
+    if (ws == nullptr || ws_bytes < need)
+      return err(KF_ERR_WORKSPACE, "workspace missing or smaller than kf_plan_workspace_size()");
+  } else if (K.is_mat) {
     MatProg P = K.mp;
     char* wsm = ws ? static_cast<char*>(ws) + plan_vec_region() : nullptr;
     const size_t wsm_bytes = ws_bytes > plan_vec_region() ? ws_bytes - plan_vec_region() : 0;
@@ -201,6 +217,7 @@ kf_status time_plan(const Plan& P, int nvars, void* const* bindings, int nb, voi
 // Name of the program field at byte offset `o` (for plan descriptions).
 std::string field_name(const Kernel& K, size_t o) {
   auto at = [&](const void* base, const void* f) { return (size_t)((const char*)f - (const char*)base); };
+  if (K.is_atax) return o == 0 ? "A" : o == 1 ? "x" : o == 2 ? "y" : "?";
   if (K.is_mat) {
     const MatProg& P = K.mp;
     for (int t = 0; t < 2; ++t) {
@@ -388,7 +405,7 @@ kf_status kf_plan_describe(const kf_plan* p, char* buf, size_t cap, size_t* need
   o << "{\"predicted_us\":" << p->p.predicted_us << ",\"bytes\":" << p->p.bytes << ",\"kernels\":[";
   for (size_t i = 0; i < p->p.kernels.size(); ++i) {
     const Kernel& K = p->p.kernels[i];
-    o << (i ? "," : "") << "{\"kind\":\"" << (K.is_mat ? "matrix" : "vector") << "\",\"calls\":[";
+    o << (i ? "," : "") << "{\"kind\":\"" << (K.is_atax ? "atax" : K.is_mat ? "matrix" : "vector") << "\",\"calls\":[";
     for (size_t j = 0; j < K.calls.size(); ++j) o << (j ? "," : "") << K.calls[j];
     o << "],\"bytes\":" << K.bytes << ",\"m\":" << K.m << ",\"n\":" << K.n << ",\"bind\":[";
     for (size_t j = 0; j < K.bind.size(); ++j)
@@ -442,6 +459,7 @@ kf_status kf_autotune_plan(const kf_plan* p, void* const* bindings, int n_bindin
   float tsum = 0.f, asum = 0.f;
   for (const Kernel& K : p->p.kernels) {
     float bm = 0.f, am = 0.f;
+    if (K.is_atax) continue;  // tuned on first use by its own search (ring depth, blocks per SM, clusters)
     if (K.is_mat) {
       MatProg P = K.mp;
       for (auto& b : K.bind) {

@@ -166,6 +166,27 @@ void add_scaled(Expr& dst, const Expr& src, double a) {
 
 }  // namespace
 
+// Single-pass ATAX: {t = a1 A x; y = a2 A^T t} over one version of A, with t
+// needed by nothing else and no accumulated terms.  The row dot t_i is a
+// reduction consumed in the same kernel, which the fusion rules otherwise
+// forbid (a global barrier is needed); a block that owns whole rows (the
+// persistent row reuse Section 4.2 names) finishes t_i before it uses it, so
+// the pair runs with one read of A when a row fits the shared-memory ring.
+bool atax_pair(const Script& s, const std::vector<int>& g0, const std::vector<char>* placed) {
+  if (g0.size() != 2) return false;
+  std::vector<int> g = g0;
+  std::sort(g.begin(), g.end());
+  const Call& a = s.calls[g[0]];
+  const Call& b = s.calls[g[1]];
+  if (a.op != OP_GEMV || b.op != OP_GEMVT) return false;
+  if (a.ins[0] != b.ins[0] || a.in_ver[0] != b.in_ver[0]) return false;
+  if (b.ins[1] != a.outs[0] || b.in_ver[1] != a.out_ver) return false;
+  if ((a.ins.size() > 2 && a.sc[1] != 0.0) || (b.ins.size() > 2 && b.sc[1] != 0.0)) return false;
+  if (live_out(s, g, a.outs[0], a.out_ver, placed)) return false;
+  const Var& A = s.vars[a.ins[0]];
+  return A.m >= 1 && A.n >= 4 && A.n % 4 == 0 && A.n <= 16384;
+}
+
 bool legal_group_impl(const Script& s, const std::vector<int>& g, std::string* why,
                       const std::vector<char>* placed) {
   auto fail = [&](const char* m) { if (why) *why = m; return false; };
@@ -213,6 +234,8 @@ bool legal_group_impl(const Script& s, const std::vector<int>& g, std::string* w
     if (ndot > VP_MAXDOT) return fail("too many dot products");
     return true;
   }
+
+  if (atax_pair(s, g, placed)) return true;
 
   // ---- matrix pass (depth-2 core) with optional linear epilogue maps
   int64_t m = -1, n = -1;
@@ -616,6 +639,23 @@ static std::string build_mat_kernel(const Script& s, const std::vector<int>& g, 
   return "";
 }
 
+static std::string build_atax_kernel(const Script& s, const std::vector<int>& g0, Kernel* K) {
+  std::vector<int> g = g0;
+  std::sort(g.begin(), g.end());
+  const Call& a = s.calls[g[0]];
+  const Call& b = s.calls[g[1]];
+  const int A = a.ins[0];
+  K->is_atax = true;
+  K->atax_scale = (float)(a.sc[0] * b.sc[0]);
+  K->bind.push_back({(void**)(uintptr_t)0, A});
+  K->bind.push_back({(void**)(uintptr_t)1, a.ins[1]});
+  K->bind.push_back({(void**)(uintptr_t)2, b.outs[0]});
+  K->m = s.vars[A].m;
+  K->n = s.vars[A].n;
+  K->bytes = 4.0 * (double)K->m * (double)K->n + 8.0 * (double)K->n;  // A once, x in, y out
+  return "";
+}
+
 std::string make_plan(const Script& s, const std::vector<std::vector<int>>& groups, Plan* p) {
   p->groups = groups;
   for (auto& g : p->groups) std::sort(g.begin(), g.end());
@@ -635,9 +675,12 @@ std::string make_plan(const Script& s, const std::vector<std::vector<int>>& grou
     int depth = 1;
     for (int c : g) depth = std::max(depth, s.calls[c].depth);
     K.depth = depth;
-    std::string e = depth == 2 ? build_mat_kernel(s, g, &K) : build_vec_kernel(s, g, &K);
+    std::string e = depth == 2 ? (atax_pair(s, g, nullptr) ? build_atax_kernel(s, g, &K) : build_mat_kernel(s, g, &K))
+                               : build_vec_kernel(s, g, &K);
     if (!e.empty()) return e;
-    if (K.is_mat) {
+    if (K.is_atax) {
+      p->ws_bytes = std::max(p->ws_bytes, vec_region + atax_plan_workspace_bytes(K.m, K.n));
+    } else if (K.is_mat) {
       const size_t w = matprog_workspace_bytes(K.mp.m, K.mp.n, std::max(K.mp.nrow_res, 1), std::max(K.mp.ncol_res, 1), FMT_F32);
       p->ws_bytes = std::max(p->ws_bytes, vec_region + w);
     } else {
@@ -660,7 +703,16 @@ void features(const Script& s, const Plan& p, std::vector<float>* f) {
   int64_t nmax = 1;
   for (const auto& K : p.kernels) {
     minb = std::min(minb, K.bytes);
-    if (K.is_mat) {
+    if (K.is_atax) {
+      // one matrix pass (two matrix calls) whose column results need a second phase
+      nmat += 1;
+      matb += 4.0 * K.m * K.n;
+      vecb += K.bytes - 4.0 * K.m * K.n;
+      maxops = std::max(maxops, 2.f);
+      colfin += 1;
+      nepi += 1;
+      nmax = std::max<int64_t>(nmax, std::max(K.m, K.n));
+    } else if (K.is_mat) {
       nmat += 1;
       matb += 4.0 * K.m * K.n * K.mp.nmat;
       vecb += K.bytes - 4.0 * K.m * K.n * K.mp.nmat;

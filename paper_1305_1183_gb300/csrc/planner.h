@@ -66,6 +66,10 @@ struct Kernel {
   std::vector<int> calls;  // in script order
   int depth = 1;
   bool is_mat = false;
+  // Single-pass ATAX, y = atax_scale * A^T (A x): bind holds A, x, y in that
+  // order (their offsets are 0, 1, 2); it runs as kf_atax's kernels.
+  bool is_atax = false;
+  float atax_scale = 1.f;
   MatProg mp{};            // pointers hold var ids (cast) until bound
   VecProg vp{};
   // binding maps: for each pointer field, which variable it refers to

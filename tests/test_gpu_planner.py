@@ -173,3 +173,18 @@ def test_planner_gemver_matches_fixed_entry_point(built):
                  B, x, w, kf.workspace(kf.KF_SEQ_GEMVER, n, n))
     torch.cuda.synchronize()
     assert torch.equal(bind["B"], B) and torch.equal(bind["x"], x) and torch.equal(bind["w"], w)
+
+
+@pytest.mark.parametrize("m,n", [(3000, 2048), (40, 16384), (777, 1000)])
+def test_planner_single_pass_atax(built, m, n):
+    """{t = 1.5 A x; y = -0.5 A^T t}: the planner's choice is the single-pass
+    ATAX kernel (one read of A), and it and the two-kernel plan both match
+    the oracle's call-by-call evaluation."""
+    kf = built
+    sd = {"n": max(m, n), "vars": {"A": ("m", m, n), "x": ("v", n), "t": ("v", m), "y": ("v", n)},
+          "inputs": ["A", "x"], "outputs": ["y"],
+          "calls": [("GEMV", ["t"], ["A", "x"], [1.5, 0.0]), ("GEMVT", ["y"], ["A", "t"], [-0.5, 0.0])]}
+    s = to_kf(kf, sd)
+    assert [k["kind"] for k in s.plan(kf.KF_PLAN_ANALYTIC).describe()["kernels"]] == ["atax"]
+    assert run_plans(kf, sd, integer=False) == 2
+    assert run_plans(kf, sd, integer=True) == 2

@@ -86,7 +86,7 @@ def waxpby(kf, n=1000):
 
 
 @pytest.mark.parametrize("name,nplans,fused_kernels", [
-    ("bicgk", 2, 1), ("gemver", None, 2), ("gesummv", None, 1), ("atax", 1, 2),
+    ("bicgk", 2, 1), ("gemver", None, 2), ("gesummv", None, 1), ("atax", 2, 1),
     ("axpydot", 2, 1), ("waxpby", 2, 1)])
 def test_canonical_scripts(kf, name, nplans, fused_kernels):
     s = globals()[name](kf)
@@ -107,6 +107,53 @@ def test_canonical_scripts(kf, name, nplans, fused_kernels):
     assert sum(len(k["calls"]) for k in d["kernels"]) == unf.kernel_count()
     assert len(p.features()) == 16
     assert ncalls is None
+
+
+def _atax_script(kf, m, n, t_out=False, beta=0.0, a1=1.0, a2=1.0):
+    s = kf.Script()
+    s.matrix("A", m, n); s.vector("x", n); s.vector("t", m); s.vector("y", n); s.vector("y0", m)
+    s.input("A", "x", "y0"); s.output("y")
+    if t_out:
+        s.output("t")
+    s.call("GEMV", ["t"], ["A", "x", "y0"] if beta else ["A", "x"], [a1, beta])
+    s.call("GEMVT", ["y"], ["A", "t"], [a2, 0.0])
+    return s
+
+
+def test_atax_single_pass_fusion(kf):
+    """{t = a1 A x; y = a2 A^T t}: the GEMV result is consumed in the same
+    kernel, which is legal only for the row-owning single pass (one read of
+    A, Section 4.2's persistent row reuse): one "atax" kernel moving
+    4 (m n + 2 n) bytes, scale a1 a2."""
+    m, n = 300, 512
+    s = _atax_script(kf, m, n, a1=1.5, a2=-0.5)
+    assert s.count_plans()[0] == 2
+    d = s.plan(kf.KF_PLAN_ANALYTIC).describe()
+    assert [k["kind"] for k in d["kernels"]] == ["atax"]
+    assert d["bytes"] == 4 * (m * n + 2 * n)
+    assert [b[0] for b in d["kernels"][0]["bind"]] == ["A", "x", "y"]
+    assert s.plan(kf.KF_PLAN_GREEDY).kernel_count() == 1
+
+
+@pytest.mark.parametrize("case", ["t_is_output", "gemv_accumulates", "row_too_long", "row_not_float4"])
+def test_atax_fusion_refused(kf, case):
+    """No single pass when t is needed after the kernel, when the GEMV adds a
+    term the rows pass does not compute, or when a row does not fit the
+    ring's 16-byte chunks (n > 16384 or n not a multiple of 4): the paper's
+    two kernels remain."""
+    m, n = 100, 512
+    kw = {}
+    if case == "t_is_output":
+        kw["t_out"] = True
+    elif case == "gemv_accumulates":
+        kw["beta"] = 1.0
+    elif case == "row_too_long":
+        n = 16388
+    else:
+        n = 514
+    s = _atax_script(kf, m, n, **kw)
+    assert s.count_plans()[0] == 1
+    assert s.plan(kf.KF_PLAN_ANALYTIC).kernel_count() == 2
 
 
 def test_gemver_fusion_shape(kf):
