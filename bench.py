@@ -886,14 +886,17 @@ def batched_shapes(count=4096, lo=32, hi=2048):
     return list(zip(ms_, ns_))
 
 
-def make_batched(kind, d, shapes):
-    """Instances packed back to back (matrices with lda = n, vectors in
-    four long buffers) with their descriptors: (descs, views, buffers,
-    algorithmic bytes).  views[i] = (A_i, B_i or None, x_i, r_i, y_i, s_i)."""
+def make_batched(kind, d, shapes, aligned=False):
+    """Instances packed back to back (matrices with lda = n, or with rows
+    padded to a multiple of 4 floats so that every row starts 16-byte
+    aligned; vectors in four long buffers) with their descriptors: (descs,
+    views, buffers, algorithmic bytes, counted on m x n, not on the padding).
+    views[i] = (A_i, B_i or None, x_i, r_i, y_i, s_i)."""
+    ldas = [(n + 3) // 4 * 4 if aligned else n for m, n in shapes]
     offs, tot, vm, vn, tm, tn = [], 0, [], [], 0, 0
-    for m, n in shapes:
+    for (m, n), ld in zip(shapes, ldas):
         offs.append(tot); vm.append(tm); vn.append(tn)
-        tot += m * n; tm += m; tn += n
+        tot += m * ld; tm += m; tn += n
     A = synth.uniform((max(tot, 1),), 0, synth.TID["A"], device=d)
     Bm = synth.uniform((max(tot, 1),), 0, synth.TID["B"], device=d) if kind == "gesummv" else None
     X = synth.uniform((max(tn, 1),), 0, synth.TID["x"], device=d)
@@ -902,11 +905,12 @@ def make_batched(kind, d, shapes):
     S = torch.empty(max(tn, 1), device=d)
     descs, views = [], []
     for i, (m, n) in enumerate(shapes):
-        a = A[offs[i]:offs[i] + m * n].view(m, n)
-        b = Bm[offs[i]:offs[i] + m * n].view(m, n) if Bm is not None else None
+        ld = ldas[i]
+        a = A[offs[i]:offs[i] + m * ld].view(m, ld)[:, :n]
+        b = Bm[offs[i]:offs[i] + m * ld].view(m, ld)[:, :n] if Bm is not None else None
         x, r = X[vn[i]:vn[i] + n], R[vm[i]:vm[i] + m]
         y, sv = Y[vm[i]:vm[i] + m], S[vn[i]:vn[i] + n]
-        dd = {"m": m, "n": n, "lda": n, "A": a.data_ptr(), "x": x.data_ptr(), "r": r.data_ptr(),
+        dd = {"m": m, "n": n, "lda": ld, "A": a.data_ptr(), "x": x.data_ptr(), "r": r.data_ptr(),
               "y": y.data_ptr(), "s": sv.data_ptr(), "alpha": ALPHA, "beta": BETA}
         if b is not None:
             dd["B"] = b.data_ptr()
@@ -921,51 +925,60 @@ def make_batched(kind, d, shapes):
 
 def batched_section(kf, d, st, steps, warmup, count=4096, lo=32, hi=2048):
     """`count` independent BiCGK and GESUMMV instances, m and n each
-    log-uniform in [lo, hi], matrices packed back to back (lda = n) with
-    offset tables: one persistent launch replayed from a CUDA graph, tile
-    height from the library's autotuner, against the same fused kernel
-    launched once per instance (a stream loop, and the loop captured in a
-    CUDA graph)."""
+    log-uniform in [lo, hi], matrices packed back to back with offset tables:
+    one persistent launch replayed from a CUDA graph, tile height from the
+    library's autotuner.  Two packings: rows padded to 16 bytes (lda a
+    multiple of 4: the kernel's 16-byte loads; the primary figures, beside
+    the same fused kernel launched once per instance, as a stream loop and
+    as that loop captured in a CUDA graph) and lda = n (rows at any
+    alignment: element-interleaved loads)."""
     shapes = batched_shapes(count, lo, hi)
-    out = {"instances": count, "m_n_range": [lo, hi], "matrix_elements": sum(m * n for m, n in shapes)}
+    peak, _ = hbm_peak()
+    out = {"instances": count, "m_n_range": [lo, hi], "matrix_elements": sum(m * n for m, n in shapes),
+           "packing": "rows padded to a multiple of 4 floats (16-byte aligned rows); 'lda_n': rows back to back"}
     WB = kf.workspace(kf.KF_SEQ_BICGK, hi, hi)
     WG = kf.workspace(kf.KF_SEQ_GESUMMV, hi, hi)
-    for kind in ("bicgk", "gesummv"):
-        descs, views, bufs, nbytes = make_batched(kind, d, shapes)
-        if kind == "bicgk":
-            seq = kf.KF_SEQ_BICGK
+    for aligned in (True, False):
+        for kind in ("bicgk", "gesummv"):
+            descs, views, bufs, nbytes = make_batched(kind, d, shapes, aligned=aligned)
+            if kind == "bicgk":
+                seq = kf.KF_SEQ_BICGK
 
-            def one(s, v):
-                kf.kf_bicgk(v[0], v[2], v[3], v[4], v[5], WB, stream=s)
-        else:
-            seq = kf.KF_SEQ_GESUMMV
+                def one(s, v):
+                    kf.kf_bicgk(v[0], v[2], v[3], v[4], v[5], WB, stream=s)
+            else:
+                seq = kf.KF_SEQ_GESUMMV
 
-            def one(s, v):
-                kf.kf_gesummv(v[0], v[1], v[2], ALPHA, BETA, v[4], WG, stream=s)
-        band, _ = kf.kf_batched_autotune(seq, descs, reps=3)
-        bt = kf.Batched(seq, descs, band)
-        ws = torch.zeros(max(bt.workspace_size(), 256), dtype=torch.uint8, device=d)
-        bt.upload(ws)
-        bt.capture(ws)
-        t_graph = time_calls(lambda s: bt.replay(s), steps, warmup, st)
-        loop_steps = max(1, min(steps, 3))
-        t_loop = time_calls(lambda s: [one(s, v) for v in views], loop_steps, 1, st)
-        t_loop_graph = None
-        try:
-            gph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(gph, stream=st):
-                for v in views:
-                    one(None, v)
-            t_loop_graph = time_calls(lambda s: gph.replay(), loop_steps, 1, st)
-        except Exception as e:  # capture of per-instance launches is a comparison only
-            out.setdefault("notes", []).append(f"{kind}: per-instance graph capture failed: {e}")
-        out[kind] = {"band_rows": band, "bytes": nbytes, "ms": t_graph, "gbs": nbytes / (t_graph * 1e-3) / 1e9,
-                     "per_instance_loop_ms": t_loop,
-                     "per_instance_graph_ms": t_loop_graph,
-                     "speedup_vs_per_instance_loop": t_loop / t_graph,
-                     "speedup_vs_per_instance_graph": (t_loop_graph / t_graph) if t_loop_graph else None}
-        del bt, ws, bufs, views, descs
-        torch.cuda.empty_cache()
+                def one(s, v):
+                    kf.kf_gesummv(v[0], v[1], v[2], ALPHA, BETA, v[4], WG, stream=s)
+            band, _ = kf.kf_batched_autotune(seq, descs, reps=3)
+            bt = kf.Batched(seq, descs, band)
+            ws = torch.zeros(max(bt.workspace_size(), 256), dtype=torch.uint8, device=d)
+            bt.upload(ws)
+            bt.capture(ws)
+            t_graph = time_calls(lambda s: bt.replay(s), steps, warmup, st)
+            r = {"band_rows": band, "bytes": nbytes, "ms": t_graph, "gbs": nbytes / (t_graph * 1e-3) / 1e9,
+                 "frac": nbytes / (t_graph * 1e-3) / 1e9 / peak}
+            if aligned:
+                loop_steps = max(1, min(steps, 3))
+                t_loop = time_calls(lambda s: [one(s, v) for v in views], loop_steps, 1, st)
+                t_loop_graph = None
+                try:
+                    gph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(gph, stream=st):
+                        for v in views:
+                            one(None, v)
+                    t_loop_graph = time_calls(lambda s: gph.replay(), loop_steps, 1, st)
+                except Exception as e:  # capture of per-instance launches is a comparison only
+                    out.setdefault("notes", []).append(f"{kind}: per-instance graph capture failed: {e}")
+                r.update({"per_instance_loop_ms": t_loop, "per_instance_graph_ms": t_loop_graph,
+                          "speedup_vs_per_instance_loop": t_loop / t_graph,
+                          "speedup_vs_per_instance_graph": (t_loop_graph / t_graph) if t_loop_graph else None})
+                out[kind] = r
+            else:
+                out.setdefault("lda_n", {})[kind] = r
+            del bt, ws, bufs, views, descs
+            torch.cuda.empty_cache()
     return out
 
 

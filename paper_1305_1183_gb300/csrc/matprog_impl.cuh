@@ -389,12 +389,24 @@ constexpr int min_blocks() {
                                                               : ((FMT != FMT_F32 && VEC) ? 2 : 1);
 }
 
+// BF16 GEMVER passes (GER chain + GEMVT, and GEMV) with 8 rows in flight
+// run at three blocks per SM: a few spilled bytes cost less than the extra
+// warps gain (measured 310 -> 289 us for GEMVER at n = 16384); BiCGK and
+// E4M3 spill too much at that bound and keep two.
+template <int NW, int V, int NMAT, int FMT, bool VEC, int U, int SIG>
+constexpr int min_blocks_sig() {
+  return (FMT == FMT_BF16 && VEC && V == 1 && U == 8 && NMAT == 1 &&
+          (SIG == SIG_GEMVER1 || SIG == SIG_GEMV))
+             ? 3
+             : min_blocks<NW, V, NMAT, FMT, VEC, U>();
+}
+
 // Registers of one batch of rows: decoded floats, or packed chunks.
 template <bool RAW, int NMAT, int U, int V, int W> struct BatchOf { using type = float[NMAT][U][W]; };
 template <int NMAT, int U, int V, int W> struct BatchOf<true, NMAT, U, V, W> { using type = uint4[NMAT][U][V]; };
 
 template <int NW, int V, int U, int NOPS, int NMAT, int NG, int FMT, bool VEC, bool STAGED, int SIG>
-__global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks<NW, V, NMAT, FMT, VEC, U>()))
+__global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks_sig<NW, V, NMAT, FMT, VEC, U, SIG>()))
     matprog_kernel(const __grid_constant__ MatProg P) {
   constexpr int CH = FmtT<FMT>::CH;
   constexpr int BYTES = FmtT<FMT>::BYTES;
