@@ -925,60 +925,54 @@ def make_batched(kind, d, shapes, aligned=False):
 
 def batched_section(kf, d, st, steps, warmup, count=4096, lo=32, hi=2048):
     """`count` independent BiCGK and GESUMMV instances, m and n each
-    log-uniform in [lo, hi], matrices packed back to back with offset tables:
-    one persistent launch replayed from a CUDA graph, tile height from the
-    library's autotuner.  Two packings: rows padded to 16 bytes (lda a
-    multiple of 4: the kernel's 16-byte loads; the primary figures, beside
-    the same fused kernel launched once per instance, as a stream loop and
-    as that loop captured in a CUDA graph) and lda = n (rows at any
-    alignment: element-interleaved loads)."""
+    log-uniform in [lo, hi], matrices packed back to back (lda = n) with
+    offset tables: one persistent launch replayed from a CUDA graph, tile
+    height from the library's autotuner, against the same fused kernel
+    launched once per instance (a stream loop, and the loop captured in a
+    CUDA graph)."""
     shapes = batched_shapes(count, lo, hi)
     peak, _ = hbm_peak()
     out = {"instances": count, "m_n_range": [lo, hi], "matrix_elements": sum(m * n for m, n in shapes),
-           "packing": "rows padded to a multiple of 4 floats (16-byte aligned rows); 'lda_n': rows back to back"}
+           "packing": "matrices back to back, lda = n (rows at any alignment)"}
     WB = kf.workspace(kf.KF_SEQ_BICGK, hi, hi)
     WG = kf.workspace(kf.KF_SEQ_GESUMMV, hi, hi)
-    for aligned in (True, False):
-        for kind in ("bicgk", "gesummv"):
-            descs, views, bufs, nbytes = make_batched(kind, d, shapes, aligned=aligned)
-            if kind == "bicgk":
-                seq = kf.KF_SEQ_BICGK
+    for kind in ("bicgk", "gesummv"):
+        descs, views, bufs, nbytes = make_batched(kind, d, shapes)
+        if kind == "bicgk":
+            seq = kf.KF_SEQ_BICGK
 
-                def one(s, v):
-                    kf.kf_bicgk(v[0], v[2], v[3], v[4], v[5], WB, stream=s)
-            else:
-                seq = kf.KF_SEQ_GESUMMV
+            def one(s, v):
+                kf.kf_bicgk(v[0], v[2], v[3], v[4], v[5], WB, stream=s)
+        else:
+            seq = kf.KF_SEQ_GESUMMV
 
-                def one(s, v):
-                    kf.kf_gesummv(v[0], v[1], v[2], ALPHA, BETA, v[4], WG, stream=s)
-            band, _ = kf.kf_batched_autotune(seq, descs, reps=3)
-            bt = kf.Batched(seq, descs, band)
-            ws = torch.zeros(max(bt.workspace_size(), 256), dtype=torch.uint8, device=d)
-            bt.upload(ws)
-            bt.capture(ws)
-            t_graph = time_calls(lambda s: bt.replay(s), steps, warmup, st)
-            r = {"band_rows": band, "bytes": nbytes, "ms": t_graph, "gbs": nbytes / (t_graph * 1e-3) / 1e9,
-                 "frac": nbytes / (t_graph * 1e-3) / 1e9 / peak}
-            if aligned:
-                loop_steps = max(1, min(steps, 3))
-                t_loop = time_calls(lambda s: [one(s, v) for v in views], loop_steps, 1, st)
-                t_loop_graph = None
-                try:
-                    gph = torch.cuda.CUDAGraph()
-                    with torch.cuda.graph(gph, stream=st):
-                        for v in views:
-                            one(None, v)
-                    t_loop_graph = time_calls(lambda s: gph.replay(), loop_steps, 1, st)
-                except Exception as e:  # capture of per-instance launches is a comparison only
-                    out.setdefault("notes", []).append(f"{kind}: per-instance graph capture failed: {e}")
-                r.update({"per_instance_loop_ms": t_loop, "per_instance_graph_ms": t_loop_graph,
-                          "speedup_vs_per_instance_loop": t_loop / t_graph,
-                          "speedup_vs_per_instance_graph": (t_loop_graph / t_graph) if t_loop_graph else None})
-                out[kind] = r
-            else:
-                out.setdefault("lda_n", {})[kind] = r
-            del bt, ws, bufs, views, descs
-            torch.cuda.empty_cache()
+            def one(s, v):
+                kf.kf_gesummv(v[0], v[1], v[2], ALPHA, BETA, v[4], WG, stream=s)
+        band, _ = kf.kf_batched_autotune(seq, descs, reps=3)
+        bt = kf.Batched(seq, descs, band)
+        ws = torch.zeros(max(bt.workspace_size(), 256), dtype=torch.uint8, device=d)
+        bt.upload(ws)
+        bt.capture(ws)
+        t_graph = time_calls(lambda s: bt.replay(s), steps, warmup, st)
+        loop_steps = max(1, min(steps, 3))
+        t_loop = time_calls(lambda s: [one(s, v) for v in views], loop_steps, 1, st)
+        t_loop_graph = None
+        try:
+            gph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gph, stream=st):
+                for v in views:
+                    one(None, v)
+            t_loop_graph = time_calls(lambda s: gph.replay(), loop_steps, 1, st)
+        except Exception as e:  # capture of per-instance launches is a comparison only
+            out.setdefault("notes", []).append(f"{kind}: per-instance graph capture failed: {e}")
+        gbs = nbytes / (t_graph * 1e-3) / 1e9
+        out[kind] = {"band_rows": band, "bytes": nbytes, "ms": t_graph, "gbs": gbs, "frac": gbs / peak,
+                     "per_instance_loop_ms": t_loop,
+                     "per_instance_graph_ms": t_loop_graph,
+                     "speedup_vs_per_instance_loop": t_loop / t_graph,
+                     "speedup_vs_per_instance_graph": (t_loop_graph / t_graph) if t_loop_graph else None}
+        del bt, ws, bufs, views, descs
+        torch.cuda.empty_cache()
     return out
 
 

@@ -17,13 +17,10 @@
 // which tile, and equals the same instance run alone.  The queue and the
 // counters reset themselves, so the launch can be replayed from a CUDA graph.
 //
-// Loads: an instance whose matrices start 16-byte aligned with a leading
-// dimension that keeps every row so (lda a multiple of 4) is read with one
-// 16-byte load per lane and row (lane l owns columns 4l..4l+3 of its
-// 128-column slice); any other instance is read element-interleaved (lane l
-// reads columns l, l+32, l+64, l+96), so every load instruction still covers
-// 128 contiguous bytes for any row length and alignment.  A warp keeps 8
-// rows of one matrix (BiCGK) or 4 rows of two (GESUMMV) in flight.
+// Loads are element-interleaved (lane l of a warp reads columns l, l+32,
+// l+64, l+96 of its 128-column slice), so every load instruction covers 128
+// contiguous bytes for any row length and alignment; a warp keeps 8 rows
+// of one matrix (BiCGK) or 4 rows of two (GESUMMV) in flight.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,7 +49,6 @@ struct BDesc {
   float alpha, beta;
   int64_t rowpart_off, colpart_off;
   int ntiles, nstrips, nbands, cw;  // cw: warps side by side across the strip (width-adapted form)
-  int vec4;                         // rows 16-byte aligned: 16-byte loads
 };
 
 struct BTile {
@@ -117,14 +113,11 @@ __global__ void __launch_bounds__(BNW * 32, 3)
     const int64_t r0 = (int64_t)tl.band * band_rows;
     const int64_t r1 = min(m, r0 + band_rows);
     const int64_t wc = (int64_t)tl.strip * cw * 128 + wcol * 128;  // this warp's slice
-    const bool v4 = d.vec4 != 0;  // block-uniform
-    // offset in the slice of this lane's value e
-    auto pos = [&](int e) { return v4 ? 4 * lane + e : e * 32 + lane; };
 
     float xv[4], acc[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const int64_t c = wc + pos(e);
+      const int64_t c = wc + e * 32 + lane;
       xv[e] = c < n ? __ldg(d.x + c) : 0.f;
       acc[e] = 0.f;
     }
@@ -157,16 +150,10 @@ __global__ void __launch_bounds__(BNW * 32, 3)
 #pragma unroll
               for (int kk = 0; kk < NM; ++kk) {
                 const float* rowp = (kk == 0 ? d.A : d.B) + row * d.lda;
-                const int64_t c4 = wc + 4 * lane;
-                if (v4 && rok && c4 + 4 <= n) {
-                  const float4 q = __ldcs(reinterpret_cast<const float4*>(rowp + c4));
-                  a[kk][u][0] = q.x; a[kk][u][1] = q.y; a[kk][u][2] = q.z; a[kk][u][3] = q.w;
-                } else {
 #pragma unroll
-                  for (int e = 0; e < 4; ++e) {
-                    const int64_t c = wc + pos(e);
-                    a[kk][u][e] = (rok && c < n) ? __ldcs(rowp + c) : 0.f;
-                  }
+                for (int e = 0; e < 4; ++e) {
+                  const int64_t c = wc + e * 32 + lane;
+                  a[kk][u][e] = (rok && c < n) ? __ldcs(rowp + c) : 0.f;
                 }
               }
             }
@@ -216,19 +203,19 @@ __global__ void __launch_bounds__(BNW * 32, 3)
       if (rw == 1) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int64_t c = wc + pos(e);
+          const int64_t c = wc + e * 32 + lane;
           if (c < n) colpart[d.colpart_off + (int64_t)tl.band * n + c] = acc[e];
         }
       } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) csum[warp][pos(e)] = acc[e];
+        for (int e = 0; e < 4; ++e) csum[warp][e * 32 + lane] = acc[e];
         __syncthreads();
         if (wrow == 0) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             float sum = 0.f;
-            for (int q = 0; q < rw; ++q) sum += csum[q * cw + wcol][pos(e)];
-            const int64_t c = wc + pos(e);
+            for (int q = 0; q < rw; ++q) sum += csum[q * cw + wcol][e * 32 + lane];
+            const int64_t c = wc + e * 32 + lane;
             if (c < n) colpart[d.colpart_off + (int64_t)tl.band * n + c] = sum;
           }
         }
@@ -366,8 +353,6 @@ kf_status kf_batched_create(kf_seq seq, const kf_batch_desc* descs, int count, i
     d.m = u.m; d.n = u.n; d.lda = u.lda;
     d.A = u.A; d.B = u.B; d.x = u.x; d.r = u.r; d.y = u.y; d.s = u.s;
     d.alpha = u.alpha; d.beta = u.beta;
-    auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
-    d.vec4 = (u.lda % 4 == 0 && al16(u.A) && (b->kind == 0 || al16(u.B))) ? 1 : 0;
     // narrow matrices take fewer warps per row and more row blocks at once
     d.cw = u.n <= 128 ? 1 : u.n <= 256 ? 2 : u.n <= 512 ? 4 : BNW;
     d.nstrips = (int)std::max<int64_t>(1, (u.n + d.cw * 128 - 1) / (d.cw * 128));

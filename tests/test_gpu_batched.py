@@ -2,8 +2,8 @@
 
 Instances have log-uniform sizes (plus degenerate ones), are packed into
 one buffer with per-instance offsets, either back to back (lda = n, rows
-generally unaligned: element-interleaved loads) or with rows padded to
-16 bytes (lda a multiple of 4: 16-byte loads), and are checked one by one.  A batched instance equals the same instance
+generally unaligned) or with rows padded to a multiple of 4 floats, and
+are checked one by one.  A batched instance equals the same instance
 batched alone bit for bit (fixed per-instance reduction order), and a
 CUDA-graph replay gives the same bits as the direct launch.
 """
