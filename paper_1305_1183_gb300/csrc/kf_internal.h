@@ -27,6 +27,8 @@ constexpr int MAT_MAXOPS = 4;
 constexpr int EPI_MAXTERM = 4;
 constexpr int EPI_MAXOUT = 4;
 constexpr int MAT_MAXGROUPS = 128;     // bound on row groups (workspace sizing)
+constexpr int MAT_COLSET = 8;          // column partials added per first-level finisher
+constexpr int MAT_MAXSETS = MAT_MAXGROUPS / MAT_COLSET;
 constexpr int MAT_MAXSTAGES = 8;       // bound on the per-warp copy ring depth
 constexpr size_t WS_HEADER = 256;      // every workspace starts with a 256-byte header (error word at 0)
 constexpr size_t WS_AUX = 64;          // header offset of per-launch device scalars (vector norms)
@@ -83,8 +85,8 @@ struct MatProg {
   int64_t units_per_group;       // 8-row units per row group
   // workspace
   float* rowpart;                // [nrow_res][n_strips][m]
-  float* colpart;                // [ncol_res][n_groups][n]
-  unsigned* counters;            // [n_strips + n_groups], zero between launches
+  float* colpart;                // [ncol_res][n_groups + sets][n] (group partials, then set partials)
+  unsigned* counters;            // [n_strips + MAT_MAXGROUPS + n_strips * MAT_MAXSETS], zero between launches
   unsigned* errword;             // device error word (bounded waits that ran out)
   uint64_t wait_ns;              // bound of every wait on data (set by launch_matprog)
   // L2 use: matrix loads evict-first (data read once), the matrix output kept

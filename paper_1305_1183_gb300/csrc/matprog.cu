@@ -138,14 +138,16 @@ size_t matprog_workspace_bytes(int64_t m, int64_t n, int nrow_res, int ncol_res,
   const int64_t ch = fmt_ch(fmt);
   const int64_t max_strips = n > 0 ? (n + 32 * ch - 1) / (32 * ch) : 1;
   size_t b = WS_HEADER;
-  b += align256((size_t)(max_strips + MAT_MAXGROUPS) * sizeof(unsigned));
+  b += align256((size_t)(max_strips + MAT_MAXGROUPS + max_strips * MAT_MAXSETS) * sizeof(unsigned));
   b += align256((size_t)nrow_res * max_strips * (size_t)m * sizeof(float));
-  b += (size_t)ncol_res * MAT_MAXGROUPS * (size_t)n * sizeof(float);
+  b += (size_t)ncol_res * (MAT_MAXGROUPS + MAT_MAXSETS) * (size_t)n * sizeof(float);
   return b;
 }
 
 // Workspace layout of a matrix pass:
-// [header (error word) | counters | row partials | column partials].
+// [header (error word) | counters (strips, groups, strip x set) | row partials |
+//  column partials (per result: one slot per group, then one per set of
+//  MAT_COLSET groups)].
 int matprog_bind_workspace(MatProg& P, void* ws, size_t bytes) {
   P.errword = ws ? static_cast<unsigned*>(ws) : nullptr;
   // partial sums are written for every reduction, stored or not
@@ -158,7 +160,7 @@ int matprog_bind_workspace(MatProg& P, void* ws, size_t bytes) {
   char* b = static_cast<char*>(ws);
   size_t off = WS_HEADER;
   P.counters = reinterpret_cast<unsigned*>(b + off);
-  off += align256((size_t)(max_strips + MAT_MAXGROUPS) * sizeof(unsigned));
+  off += align256((size_t)(max_strips + MAT_MAXGROUPS + max_strips * MAT_MAXSETS) * sizeof(unsigned));
   P.rowpart = reinterpret_cast<float*>(b + off);
   off += align256((size_t)P.nrow_res * max_strips * (size_t)P.m * sizeof(float));
   P.colpart = reinterpret_cast<float*>(b + off);

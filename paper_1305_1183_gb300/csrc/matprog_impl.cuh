@@ -456,6 +456,11 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks_sig<
   const int64_t nbatch = (u_end - u_begin) * NBU;
 
   const int S = STAGED ? P.stages : 1;
+  // column partial slots per result: one per group, then (more than
+  // MAT_COLSET groups) one per set of MAT_COLSET groups
+  const int nsets = (P.n_groups + MAT_COLSET - 1) / MAT_COLSET;
+  const int64_t cslots = (int64_t)P.n_groups + (nsets > 1 ? nsets : 0);
+  unsigned* setcnt = P.counters + P.n_strips + MAT_MAXGROUPS;  // [n_strips][MAT_MAXSETS]
   const bool rev = P.reverse_rows != 0;
   // matrix loads: evict-first when the data is read once; matrix output:
   // kept at normal priority when the next pass reads it, else evict-first
@@ -754,7 +759,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks_sig<
 #pragma unroll
     for (int k = 0; k < NOPS; ++k) {
       if ((SPEC ? sig_kind(SIG, k) : (k < nops ? P.ops[k].kind : 0)) == MOP_GEMVT) {
-        float* part = P.colpart + ((int64_t)P.ops[k].res * P.n_groups + group) * n;
+        float* part = P.colpart + ((int64_t)P.ops[k].res * cslots + group) * n;
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
@@ -766,22 +771,38 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks_sig<
     }
   }
 
-  // Last-block completion of the cross-block reductions.
+  // Cross-block completion (Section 3.2.2, option (ii), in a fixed order).
+  // Row results: the last block of a group adds the strips' partials in
+  // strip order.  Column results: with at most MAT_COLSET groups the last
+  // block of a strip adds the groups' partials in group order; with more, the
+  // last block of each set of MAT_COLSET groups adds its set's partials in
+  // group order into a set partial, and the last set of the strip to finish
+  // adds the set partials in set order, so the sets finish side by side
+  // instead of one block adding every group's partial.
+  const int G = P.n_groups;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     int ls = 0, lg = 0;
-    if (P.ncol_out > 0) ls = atomicAdd(&P.counters[strip], 1u) == (unsigned)P.n_groups - 1u;
+    if (P.ncol_out > 0) {
+      if (nsets == 1) {
+        ls = atomicAdd(&P.counters[strip], 1u) == (unsigned)G - 1u ? 2 : 0;
+      } else {
+        const int set = group / MAT_COLSET;
+        const int ssize = min(MAT_COLSET, G - set * MAT_COLSET);
+        ls = atomicAdd(&setcnt[strip * MAT_MAXSETS + set], 1u) == (unsigned)ssize - 1u ? 1 : 0;
+      }
+    }
     if (P.nrow_out > 0)
       lg = atomicAdd(&P.counters[P.n_strips + group], 1u) == (unsigned)P.n_strips - 1u;
     s_last[0] = ls;
     s_last[1] = lg;
   }
   __syncthreads();
-  if (s_last[0]) {
-    __threadfence();
-    // Column results of this strip: sum the groups' partials in group order.
-    // Four adjacent columns per thread and eight loads in flight.
+  // Sum of column partial slots [first, first + count) in slot order for the
+  // strip's columns, four adjacent columns per thread and eight loads in
+  // flight; into slot `to`, or (to < 0) through the column epilogue.
+  auto col_sum = [&](int first, int count, int to) {
     const bool v4 = (n & 3) == 0;
     const int step = v4 ? 4 : 1;
     for (int c = threadIdx.x * step; c < SW; c += blockDim.x * step) {
@@ -792,36 +813,64 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks_sig<
       for (int q = 0; q < NOPS; ++q) {
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         if (q < P.ncol_res) {
-          const float* part = P.colpart + (int64_t)q * P.n_groups * n + col;
+          const float* part = P.colpart + ((int64_t)q * cslots + first) * n + col;
           int g = 0;
           if (v4) {
-            for (; g + 8 <= P.n_groups; g += 8) {
+            for (; g + 8 <= count; g += 8) {
               float4 t[8];
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) t[jj] = __ldcg(reinterpret_cast<const float4*>(part + (int64_t)(g + jj) * n));
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) { acc.x += t[jj].x; acc.y += t[jj].y; acc.z += t[jj].z; acc.w += t[jj].w; }
             }
-            for (; g < P.n_groups; ++g) {
+            for (; g < count; ++g) {
               const float4 t = __ldcg(reinterpret_cast<const float4*>(part + (int64_t)g * n));
               acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
             }
           } else {
-            for (; g + 8 <= P.n_groups; g += 8) {
+            for (; g + 8 <= count; g += 8) {
               float t[8];
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) t[jj] = __ldcg(part + (int64_t)(g + jj) * n);
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) acc.x += t[jj];
             }
-            for (; g < P.n_groups; ++g) acc.x += __ldcg(part + (int64_t)g * n);
+            for (; g < count; ++g) acc.x += __ldcg(part + (int64_t)g * n);
+          }
+          if (to >= 0) {
+            float* dst = P.colpart + ((int64_t)q * cslots + to) * n + col;
+            if (v4) {
+              *reinterpret_cast<float4*>(dst) = acc;
+            } else {
+              dst[0] = acc.x;
+            }
           }
         }
         raw[0][q] = acc.x; raw[1][q] = acc.y; raw[2][q] = acc.z; raw[3][q] = acc.w;
       }
-      for (int e = 0; e < step; ++e)
-        if (col + e < n) epilogue<NOPS>(P.col_out, P.ncol_out, raw[e], col + e);
+      if (to < 0)
+        for (int e = 0; e < step; ++e)
+          if (col + e < n) epilogue<NOPS>(P.col_out, P.ncol_out, raw[e], col + e);
     }
+  };
+  if (s_last[0] == 1) {
+    // first level: this block closes its set of groups
+    __threadfence();
+    const int set = group / MAT_COLSET;
+    col_sum(set * MAT_COLSET, min(MAT_COLSET, G - set * MAT_COLSET), G + set);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      setcnt[strip * MAT_MAXSETS + set] = 0u;
+      s_last[0] = atomicAdd(&P.counters[strip], 1u) == (unsigned)nsets - 1u ? 2 : 0;
+    }
+    __syncthreads();
+  }
+  if (s_last[0] == 2) {
+    // the strip's column results
+    __threadfence();
+    if (nsets == 1) col_sum(0, G, -1);
+    else col_sum(G, nsets, -1);
     if (threadIdx.x == 0) P.counters[strip] = 0u;
   }
   if (s_last[1]) {
