@@ -491,8 +491,10 @@ kf_status kf_planner_train(const float* features, const double* measured_ms, con
  * fusion implementation; routines are benchmarked once per architecture).
  * kf_autotune_plan runs, for every kernel of the plan on the bound data,
  * each compiled implementation that fits its op shape (warps, 16-byte chunks
- * per lane, rows per batch, direct loads or a bulk-copy ring of depth 2..4;
- * for vector passes rows in flight and grid size), each timed as the mean
+ * per lane, rows per batch, direct loads or a bulk-copy ring of depth 2..4,
+ * and for matrices of at most 16384 rows also 16, 32 or 64 row groups in
+ * place of one wave's worth; for vector passes rows in flight and grid
+ * size), each timed as the mean
  * of `reps` back-to-back launches (best of two rounds, after a warm-up of
  * the current choice), and stores the fastest in a process-wide tuning
  * cache (keeping the current choice unless the fastest gains more than 2 %,

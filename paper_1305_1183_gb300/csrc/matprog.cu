@@ -341,8 +341,9 @@ int launch_matprog(MatProg& P, const MatTune& tune, void* stream, const char** w
 
 // Empirical search over the compiled instances that fit P's op shape:
 // every (warps, chunks, rows per batch, direct or staged with ring depth
-// 2/3/4) is launched `reps` times after one warm-up and the median event
-// time kept; the best goes to the tuning cache.  Synchronous; P must be
+// 2/3/4; for up to 2048 8-row units also 16, 32 or 64 row groups) is
+// launched `reps` times after one warm-up and the median event time kept;
+// the best goes to the tuning cache.  Synchronous; P must be
 // bound (pointers and workspace).  In-place operands are overwritten.
 // Marks the calling thread as inside a search (no nested first-use tuning).
 struct SearchScope {
@@ -368,6 +369,11 @@ int autotune_matprog(MatProg& P, void* stream, int reps, MatTune* best, float* b
       for (int st : {2, 3, 4}) cands.push_back(MatTune{e.nw, e.v, e.u, 0, st});
     } else {
       cands.push_back(MatTune{e.nw, e.v, e.u, 0, 0});
+      // Small problems (at most 2048 8-row units): also fewer, longer row
+      // groups than one wave of blocks would take; fewer partial sums to
+      // add at the end against less parallelism while streaming.
+      if ((P.m + 7) / 8 <= 2048)
+        for (int g : {16, 32, 64}) cands.push_back(MatTune{e.nw, e.v, e.u, g, 0});
     }
   }
   if (cands.empty()) return -10;
