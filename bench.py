@@ -1229,6 +1229,22 @@ def main():
 
     read_probe = read_probe_section(kf, suite, sizes, args.steps, args.warmup, st) if "axpydot" in seqs else None
 
+    gemver_forms = None
+    if "gemver" in seqs:
+        # GEMVER's two forms on the suite's operands: two kernels chained by
+        # programmatic dependent launch, and one cooperative launch
+        b = suite.gemver
+        try:
+            ms1 = time_calls(lambda s_: kf.kf_gemver_single(b["A"], b["u1"], b["v1"], b["u2"], b["v2"], b["y"], b["z"],
+                                                            ALPHA, BETA, b["B"], b["x"], b["w"], b["ws"], stream=s_),
+                             args.steps, args.warmup, st)
+            gb = algorithmic_bytes("gemver", sizes["gemver"])
+            gemver_forms = {"single_launch_ms": ms1, "single_launch_gbs": gb / (ms1 * 1e-3) / 1e9,
+                            "kf_gemver_ms": per["gemver"], "kf_gemver_gbs": gb / (per["gemver"] * 1e-3) / 1e9,
+                            "note": "kf_gemver takes the form its first-use tuning measured faster"}
+        except Exception as e:
+            gemver_forms = {"error": str(e)[:200]}
+
     extra = {}
     if not args.no_cublas:
         extra["cublas_chain"] = cublas_section(suite, st, args.steps, args.warmup, seqs, per)
@@ -1320,6 +1336,8 @@ def main():
     }
     if read_probe is not None:
         line["read_probe"] = read_probe
+    if gemver_forms is not None:
+        line["gemver_forms"] = gemver_forms
     if not args.no_e2e:
         line["e2e"] = {"value": job_gbs(world, step_bytes, e2e_ms / e2e_steps), "unit": "GB/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

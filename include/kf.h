@@ -150,6 +150,20 @@ kf_status kf_gemver(int64_t n, const float* A, int64_t lda, const float* u1, con
                     float beta, float* B, int64_t ldb, float* x, float* w, void* ws,
                     size_t ws_bytes, void* stream);
 
+/* GEMVER in one cooperative launch (Table 1; Section 4.2's persistent-thread
+ * remark): the same results as kf_gemver (B bit for bit; x and w in another
+ * fixed summation order), with the global barrier on x crossed by bounded
+ * grid-wide barriers instead of a kernel boundary, the cross-block sums of x
+ * and w finished by the whole grid, and B read back in reverse row order.
+ * Needs n a multiple of 4 (n >= 8), 16-byte aligned operands, lda and ldb
+ * multiples of 4 and B not in place of A (else KF_ERR_UNSUPPORTED).  ws:
+ * kf_workspace_size(KF_SEQ_GEMVER, n, n).  kf_gemver picks this form when
+ * its tuning on first use measured it faster at that size class. */
+kf_status kf_gemver_single(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
+                           const float* u2, const float* v2, const float* y, const float* z, float alpha,
+                           float beta, float* B, int64_t ldb, float* x, float* w, void* ws, size_t ws_bytes,
+                           void* stream);
+
 /* GEMVER with row-scaled low-precision storage (not in the paper, whose
  * kernels are FP32 only).  A is given as codes QA (fmt BF16 or FP8-E4M3,
  * row stride lda elements) with per-row scales sA (kf_quantize_rows):

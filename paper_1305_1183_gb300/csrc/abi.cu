@@ -18,6 +18,14 @@ bool atax_single_pass_ok(int64_t m, int64_t n, int64_t lda, const void* A, const
 size_t atax_workspace_bytes(int64_t n);
 int launch_atax_tuned(const float* A, int64_t lda, int64_t m, int64_t n, const float* x, float* y, float scale,
                       void* ws, size_t ws_bytes, void* stream, const char** why);
+bool gemver_single_ok(int64_t n, const float* A, int64_t lda, const float* B, int64_t ldb, const float* const* vecs,
+                      int nvec);
+int launch_gemver_single(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1, const float* u2,
+                         const float* v2, const float* y, const float* z, float alpha, float beta, float* B,
+                         int64_t ldb, float* x, float* w, void* ws, size_t ws_bytes, void* stream, const char** why);
+bool tune_cache_get_mat(const std::string& k, MatTune* t);
+void tune_cache_put_mat(const std::string& k, const MatTune& t);
+bool tune_on_first_use(void* stream);
 int launch_madd_strided(int64_t m, int64_t n, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
                         int64_t ldc, void* stream, const char** why);
 int launch_quantize_rows(const float* A, int64_t lda, int64_t m, int64_t n, int fmt, void* Q,
@@ -294,17 +302,10 @@ kf_status kf_bicgk(int64_t m, int64_t n, const void* A, int64_t lda, kf_dtype fm
   return run_mat(P, ws, ws_bytes, stream);
 }
 
-kf_status kf_gemver(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
+static kf_status gemver_two_pass(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
                     const float* u2, const float* v2, const float* y, const float* z, float alpha,
                     float beta, float* B, int64_t ldb, float* x, float* w, void* ws,
                     size_t ws_bytes, void* stream) {
-  CHK(check_mat(n, n, A, lda));
-  CHK(check_mat(n, n, B, ldb));
-  CHK(check_vec(n, u1, "u1")); CHK(check_vec(n, v1, "v1")); CHK(check_vec(n, u2, "u2"));
-  CHK(check_vec(n, v2, "v2")); CHK(check_vec(n, y, "y")); CHK(check_vec(n, z, "z"));
-  CHK(check_vec(n, x, "x")); CHK(check_vec(n, w, "w"));
-  REQ((const void*)B != (const void*)A || ldb == lda, KF_ERR_SHAPE, "in-place B needs ldb == lda");
-  if (n == 0) return KF_OK;
   // Pass 1: B = A + u1 v1^T + u2 v2^T (written once), x = beta B^T y + z.
   MatProg P = new_prog(n, n);
   P.nmat = 1; P.fmt = FMT_F32; P.A[0] = A; P.lda[0] = lda; P.Bout[0] = B; P.ldb[0] = ldb;
@@ -328,6 +329,85 @@ kf_status kf_gemver(int64_t n, const float* A, int64_t lda, const float* u1, con
   Q.nrow_res = 1; Q.ncol_res = 1;
   Q.nrow_out = 1; Q.row_out[0] = epi1(w, alpha);
   return run_mat(Q, ws, ws_bytes, stream);
+}
+
+static kf_status check_gemver(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
+                       const float* u2, const float* v2, const float* y, const float* z, float* B, int64_t ldb,
+                       float* x, float* w) {
+  CHK(check_mat(n, n, A, lda));
+  CHK(check_mat(n, n, B, ldb));
+  CHK(check_vec(n, u1, "u1")); CHK(check_vec(n, v1, "v1")); CHK(check_vec(n, u2, "u2"));
+  CHK(check_vec(n, v2, "v2")); CHK(check_vec(n, y, "y")); CHK(check_vec(n, z, "z"));
+  CHK(check_vec(n, x, "x")); CHK(check_vec(n, w, "w"));
+  REQ((const void*)B != (const void*)A || ldb == lda, KF_ERR_SHAPE, "in-place B needs ldb == lda");
+  return KF_OK;
+}
+
+kf_status kf_gemver_single(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
+                           const float* u2, const float* v2, const float* y, const float* z, float alpha,
+                           float beta, float* B, int64_t ldb, float* x, float* w, void* ws, size_t ws_bytes,
+                           void* stream) {
+  CHK(check_gemver(n, A, lda, u1, v1, u2, v2, y, z, B, ldb, x, w));
+  if (n == 0) return KF_OK;
+  const float* vecs[8] = {u1, v1, u2, v2, y, z, x, w};
+  REQ(gemver_single_ok(n, A, lda, B, ldb, vecs, 8), KF_ERR_UNSUPPORTED,
+      "the single launch needs n a multiple of 4 (n >= 8), 16-byte aligned operands and B not in place of A");
+  const char* why = nullptr;
+  return from_launch(launch_gemver_single(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes,
+                                          stream, &why), why);
+}
+
+kf_status kf_gemver(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
+                    const float* u2, const float* v2, const float* y, const float* z, float alpha,
+                    float beta, float* B, int64_t ldb, float* x, float* w, void* ws,
+                    size_t ws_bytes, void* stream) {
+  CHK(check_gemver(n, A, lda, u1, v1, u2, v2, y, z, B, ldb, x, w));
+  if (n == 0) return KF_OK;
+  const float* vecs[8] = {u1, v1, u2, v2, y, z, x, w};
+  const bool single_ok = gemver_single_ok(n, A, lda, B, ldb, vecs, 8) && ws != nullptr &&
+                         ws_bytes >= matprog_workspace_bytes(n, n, 1, 1, FMT_F32) && cur_tune().warps == 0;
+  // The form, by the tuning cache ("gemver_form log2(n)": warps 1 = single
+  // launch, 2 = two passes); on a miss with tuning on first use, both forms
+  // are timed on the call's operands and the faster stored (two passes
+  // unless the single launch gains more than 2 %); else two passes.
+  int form = 2;
+  if (single_ok) {
+    int b = 0;
+    while (b < 62 && (int64_t(1) << (b + 1)) <= n) ++b;
+    const std::string key = "gemver_form " + std::to_string(b);
+    MatTune t{};
+    if (tune_cache_get_mat(key, &t)) {
+      form = t.warps;
+    } else if (tune_on_first_use(stream)) {
+      cudaStream_t st = (cudaStream_t)stream;
+      const int reps = std::max(1, g_autotune_reps.load());
+      CHK(gemver_two_pass(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream));
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best[3] = {0.f, 1e30f, 1e30f};
+      kf_status rc = KF_OK;
+      for (int f : {2, 1, 2, 1}) {
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && rc == KF_OK; ++r)
+          rc = f == 2 ? gemver_two_pass(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream)
+                      : kf_gemver_single(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best[f] = std::min(best[f], ms / (float)reps);
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (rc != KF_OK) return rc;
+      form = best[1] < 0.98f * best[2] ? 1 : 2;
+      tune_cache_put_mat(key, MatTune{form, 0, 0, 0, 0});
+    }
+  }
+  if (form == 1)
+    return kf_gemver_single(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream);
+  return gemver_two_pass(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream);
 }
 
 kf_status kf_gemver_q(int64_t n, const void* QA, int64_t lda, kf_dtype fmt, const float* sA, const float* u1,

@@ -54,6 +54,7 @@ _SIGS = {
     "kf_bicgk": ([i64, i64, vp, i64, ci, vp, vp, vp, vp, vp, vp, sz, vp], ci),
     "kf_gemver": ([i64, vp, i64, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, sz, vp], ci),
     "kf_madd": ([i64, i64, vp, i64, vp, i64, vp, i64, vp], ci),
+    "kf_gemver_single": ([i64, vp, i64, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, sz, vp], ci),
     "kf_gemver_q": ([i64, vp, i64, ci, vp, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, vp, sz, vp], ci),
     "kf_gesummv": ([i64, i64, vp, vp, i64, vp, f32, f32, vp, vp, sz, vp], ci),
     "kf_sgemvt": ([i64, i64, vp, i64, vp, vp, f32, f32, vp, vp, vp, sz, vp], ci),
@@ -264,6 +265,16 @@ def kf_gemver(A, u1, v1, u2, v2, y, z, alpha, beta, B, x, w, ws, stream=None):
     n = A.shape[0]
     _ck(lib().kf_gemver(n, _p(A), A.stride(0), _p(u1), _p(v1), _p(u2), _p(v2), _p(y), _p(z),
                         alpha, beta, _p(B), B.stride(0), _p(x), _p(w), _p(ws), _nb(ws), _st(stream)))
+
+
+def kf_gemver_single(A, u1, v1, u2, v2, y, z, alpha, beta, B, x, w, ws, stream=None):
+    """GEMVER in one cooperative launch (see include/kf.h)."""
+    _mat(A)
+    _mat(B, name="B")
+    _vec(u1, v1, u2, v2, y, z, x, w)
+    n = A.shape[0]
+    _ck(lib().kf_gemver_single(n, _p(A), A.stride(0), _p(u1), _p(v1), _p(u2), _p(v2), _p(y), _p(z),
+                               alpha, beta, _p(B), B.stride(0), _p(x), _p(w), _p(ws), _nb(ws), _st(stream)))
 
 
 def kf_gemver_q(QA, fmt, sA, u1, v1, u2, v2, y, z, alpha, beta, QB, sB, x, w, ws, stream=None):

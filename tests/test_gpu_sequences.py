@@ -168,6 +168,57 @@ def test_gemver_rank_one_closed_form(built):
     assert np.array_equal(host(x), xe)
 
 
+# ------------------------------------------------------------------ GEMVER, one launch
+
+@pytest.mark.parametrize("n", [8, 516, 1024, 2500, 4100])
+def test_gemver_single_launch(built, n):
+    """kf_gemver_single (grid-wide barriers instead of a kernel boundary):
+    B bit for bit the two-pass form's, x and w within the oracle tolerance;
+    twice in a row and after a two-pass call on the same workspace (its
+    barrier words and the passes' counters are left at zero)."""
+    kf = built
+    A = U((n, n), 1)
+    u1, v1, u2, v2, y, z = (U((n,), t) for t in (5, 6, 7, 8, 4, 9))
+    W = ws(kf, kf.KF_SEQ_GEMVER, n, n)
+    B2 = torch.empty_like(A); x2 = torch.empty(n, device=dev()); w2 = torch.empty(n, device=dev())
+    H = [host(t) for t in (A, u1, v1, u2, v2, y, z)]
+    Bo, xo, wo = oracle.gemver(*H, ALPHA, BETA)
+    Ah, u1h, v1h, u2h, v2h, yh, zh = H
+    sx = BETA * oracle.abs_gemvt(Bo, yh) + np.abs(zh)
+    sw = ALPHA * oracle.abs_gemv(Bo, np.abs(xo) + sx)
+    for call in range(3):
+        B = torch.full_like(A, float("nan")); x = torch.full((n,), float("nan"), device=dev())
+        w = torch.full((n,), float("nan"), device=dev())
+        kf.kf_gemver_single(A, u1, v1, u2, v2, y, z, ALPHA, BETA, B, x, w, W)
+        check_reduce(host(x), xo, sx, n, f"x, call {call}")
+        check_reduce(host(w), wo, sw, n, f"w, call {call}")
+        kf.kf_gemver(A, u1, v1, u2, v2, y, z, ALPHA, BETA, B2, x2, w2, W)   # the two-pass form, same workspace
+        torch.cuda.synchronize()
+        assert torch.equal(B, B2)
+        check_reduce(host(x2), xo, sx, n, "x two-pass")
+        check_reduce(host(w2), wo, sw, n, "w two-pass")
+    kf.kf_workspace_status(W)
+
+
+def test_gemver_single_launch_refusals(built):
+    kf = built
+    n = 514
+    A = U((n, n), 1)
+    vs = [U((n,), t) for t in (5, 6, 7, 8, 4, 9)]
+    x = torch.empty(n, device=dev()); w = torch.empty(n, device=dev())
+    W = ws(kf, kf.KF_SEQ_GEMVER, n, n)
+    with pytest.raises(kf.KFError) as e:
+        kf.kf_gemver_single(A, *vs, ALPHA, BETA, torch.empty_like(A), x, w, W)   # n not a multiple of 4
+    assert e.value.status == kf.KF_ERR_UNSUPPORTED
+    n = 512
+    A = U((n, n), 1)
+    vs = [U((n,), t) for t in (5, 6, 7, 8, 4, 9)]
+    x = torch.empty(n, device=dev()); w = torch.empty(n, device=dev())
+    with pytest.raises(kf.KFError) as e:
+        kf.kf_gemver_single(A, *vs, ALPHA, BETA, A, x, w, ws(kf, kf.KF_SEQ_GEMVER, n, n))   # in place
+    assert e.value.status == kf.KF_ERR_UNSUPPORTED
+
+
 # ------------------------------------------------------------------ SGEMVT
 
 @pytest.mark.parametrize("m,n", [(1, 1), (31, 33), (1000, 1003), (2048, 2048), (513, 4096), (4100, 700)])
