@@ -1158,6 +1158,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-instances section")
     ap.add_argument("--no-table1", action="store_true", help="skip SGEMV, SGEMVT, SSCAL, MADD, VADD")
     ap.add_argument("--no-small-bicgk", action="store_true", help="skip BiCGK 2048^2 cold / warm L2")
+    ap.add_argument("--tune-cache", default="",
+                    help="tuning cache file: loaded before the run if it exists, saved after it (profiling a "
+                         "run with the tunings of an earlier one, without the search's own launches)")
     ap.add_argument("--learned-scripts", type=int, default=80,
                     help="random scripts of the learned-planner run (3/4 train, 1/4 held out; 0: skip)")
     ap.add_argument("--only", default="", choices=["", "batched", "precision"],
@@ -1194,6 +1197,8 @@ def main():
     _build.build()
     kf.lib()
 
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        kf.kf_tune_cache_load(args.tune_cache)  # tunings measured by an earlier run on this device
     if args.mat_tuning:
         kf.kf_set_matrix_tuning(*[int(v) for v in args.mat_tuning.split(",")])
     elif args.autotune > 0:
@@ -1351,6 +1356,8 @@ def main():
     line.update(extra)
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if args.tune_cache and rank == 0:
+        kf.kf_tune_cache_save(args.tune_cache)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
