@@ -316,14 +316,14 @@ static kf_status gemver_two_pass(int64_t n, const float* A, int64_t lda, const f
   P.nrow_res = 1; P.ncol_res = 1;  // layout shared with pass 2
   P.ncol_out = 1; P.col_out[0] = epi1(x, beta);
   epi_add_ext(P.col_out[0], z, 1.f);
-  // A is read once (evict-first); B is read again by pass 2 (kept in L2)
-  P.l2_loads_first = 1; P.l2_keep_out = 1;
+  // B is read again by pass 2: stored at normal L2 priority
+  P.l2_keep_out = 1;
   CHK(run_mat(P, ws, ws_bytes, stream));
   // Pass 2 (after the global barrier on x): w = alpha B x, each row group
   // walked from its last rows, the ones pass 1 wrote last (still in L2).
   MatProg Q = new_prog(n, n);
   Q.nmat = 1; Q.fmt = FMT_F32; Q.A[0] = B; Q.lda[0] = ldb;
-  Q.l2_loads_first = 1; Q.reverse_rows = 1;
+  Q.reverse_rows = 1;
   Q.nops = 1;
   Q.ops[0] = op_gemv(0, 0, x);
   Q.nrow_res = 1; Q.ncol_res = 1;
@@ -447,12 +447,12 @@ kf_status kf_gemver_q(int64_t n, const void* QA, int64_t lda, kf_dtype fmt, cons
   const float* vs[2] = {v1, v2};
   const char* why = nullptr;
   CHK(from_launch(launch_colnorms(vs, 2, n, norms, stream, &why), why));
-  P.l2_loads_first = 1; P.l2_keep_out = 1;  // as kf_gemver: QB stays in L2 for pass 2
+  P.l2_keep_out = 1;  // as kf_gemver: QB stays in L2 for pass 2
   CHK(run_mat(P, ws, ws_bytes, stream));
   // Pass 2: w = alpha Bhat x, rows walked from those written last.
   MatProg Q = new_prog(n, n);
   Q.nmat = 1; Q.fmt = (int)fmt; Q.A[0] = QB; Q.rscale[0] = sB; Q.lda[0] = ldb;
-  Q.l2_loads_first = 1; Q.reverse_rows = 1;
+  Q.reverse_rows = 1;
   Q.nops = 1;
   Q.ops[0] = op_gemv(0, 0, x);
   Q.nrow_res = 1; Q.ncol_res = 1;
@@ -466,8 +466,7 @@ kf_status kf_sgemvt(int64_t m, int64_t n, const float* A, int64_t lda, const flo
   CHK(check_vec(m, y, "y")); CHK(check_vec(n, z, "z"));
   CHK(check_vec(n, x, "x")); CHK(check_vec(m, w, "w"));
   if (m == 0 && n == 0) return KF_OK;
-  // Pass 1: x = beta A^T y + z.  A is read at normal L2 priority, so the
-  // rows read last are still in L2 when pass 2 starts.
+  // Pass 1: x = beta A^T y + z.
   MatProg P = new_prog(m, n);
   P.nmat = 1; P.fmt = FMT_F32; P.A[0] = A; P.lda[0] = lda;
   P.nops = 1;
@@ -478,10 +477,10 @@ kf_status kf_sgemvt(int64_t m, int64_t n, const float* A, int64_t lda, const flo
   CHK(run_mat(P, ws, ws_bytes, stream));
   if (m == 0) return KF_OK;
   // Pass 2 (after the global barrier on x): w = alpha A x, each row group
-  // walked from its last rows, evict-first.
+  // walked from its last rows (the likeliest still in L2).
   MatProg Q = new_prog(m, n);
   Q.nmat = 1; Q.fmt = FMT_F32; Q.A[0] = A; Q.lda[0] = lda;
-  Q.l2_loads_first = 1; Q.reverse_rows = 1;
+  Q.reverse_rows = 1;
   Q.nops = 1;
   Q.ops[0] = op_gemv(0, 0, x);
   Q.nrow_res = 1; Q.ncol_res = 1;

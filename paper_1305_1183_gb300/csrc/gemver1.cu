@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
   const int64_t u0 = std::min<int64_t>(nunits, (int64_t)group * a.upg);
   const int64_t u1e = std::min<int64_t>(nunits, u0 + a.upg);
   const int64_t r0 = u0 << 3, r1 = std::min<int64_t>(n, u1e << 3);
-  const uint64_t pol_first = l2_policy_first(), pol_keep = l2_policy_normal();
+  const uint64_t pol_first = l2_policy_first();
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   unsigned k = 0;  // barriers passed
   bool ok = true;
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
             b.y = fmaf(s2, v2c.y, fmaf(s1, v1c.y, av[u].y));
             b.z = fmaf(s2, v2c.z, fmaf(s1, v1c.z, av[u].z));
             b.w = fmaf(s2, v2c.w, fmaf(s1, v1c.w, av[u].w));
-            if (col_ok) st_f4_pol(a.B + rr * a.ldb + col, b, pol_keep);
+            if (col_ok) st_f4_keep(a.B + rr * a.ldb + col, b);  // reread in phase 2
             t.x = fmaf(b.x, sy, t.x);
             t.y = fmaf(b.y, sy, t.y);
             t.z = fmaf(b.z, sy, t.z);

@@ -89,11 +89,10 @@ struct MatProg {
   unsigned* counters;            // [n_strips + MAT_MAXGROUPS + n_strips * MAT_MAXSETS], zero between launches
   unsigned* errword;             // device error word (bounded waits that ran out)
   uint64_t wait_ns;              // bound of every wait on data (set by launch_matprog)
-  // L2 use: matrix loads evict-first (data read once), the matrix output kept
-  // at normal priority (read again by the next pass), rows walked from the
-  // last 8-row unit of each group to the first (reading first what an
-  // earlier pass over the same rows wrote last).  All 0: plain streaming.
-  int l2_loads_first;
+  // L2 use: the matrix output stored at normal priority (read again by the
+  // next pass) instead of streamed, and rows walked from the last 8-row unit
+  // of each group to the first (reading first what an earlier pass over the
+  // same rows wrote last).  Matrix loads always stream (evict-first).
   int l2_keep_out;
   int reverse_rows;
 };

@@ -177,7 +177,7 @@ __device__ __forceinline__ void load_row_raw(const void* A, int64_t lda, int64_t
 
 template <int CH, int V, bool VEC>
 __device__ __forceinline__ void store_row(float* B, int64_t ldb, int64_t row, int64_t col0,
-                                          int64_t n, int lane, const float (&a)[V * CH], uint64_t pol) {
+                                          int64_t n, int lane, const float (&a)[V * CH], bool keep) {
   float* rowp = B + row * ldb;
 #pragma unroll
   for (int v = 0; v < V; ++v) {
@@ -186,8 +186,12 @@ __device__ __forceinline__ void store_row(float* B, int64_t ldb, int64_t row, in
       if (c + CH <= n) {
 #pragma unroll
         for (int q = 0; q < CH / 4; ++q)
-          st_f4_pol(rowp + c + 4 * q, make_float4(a[v * CH + 4 * q], a[v * CH + 4 * q + 1],
-                                                  a[v * CH + 4 * q + 2], a[v * CH + 4 * q + 3]), pol);
+        {
+          const float4 t4 = make_float4(a[v * CH + 4 * q], a[v * CH + 4 * q + 1], a[v * CH + 4 * q + 2],
+                                        a[v * CH + 4 * q + 3]);
+          if (keep) st_f4_keep(rowp + c + 4 * q, t4);
+          else st_stream_f4(rowp + c + 4 * q, t4);
+        }
       } else {
 #pragma unroll
         for (int e = 0; e < CH; ++e)
@@ -231,7 +235,7 @@ __device__ __forceinline__ float decode1(uint32_t c) {
 template <int FMT, int V, bool VEC>
 __device__ __forceinline__ void quant_store_row(void* B, int64_t ldb, int64_t row, bool row_ok, int64_t col0,
                                                 int64_t n, int lane, float (&a)[V * FmtT<FMT>::CH], float sB,
-                                                float isB, uint64_t pol) {
+                                                float isB, bool keep) {
   constexpr int CH = FmtT<FMT>::CH;
   constexpr int BYTES = FmtT<FMT>::BYTES;
   char* rowp = static_cast<char*>(B) + (row * ldb) * BYTES;
@@ -269,7 +273,7 @@ __device__ __forceinline__ void quant_store_row(void* B, int64_t ldb, int64_t ro
           if constexpr (FMT == FMT_BF16) w[q] = code[2 * q] | (code[2 * q + 1] << 16);
           else w[q] = code[4 * q] | (code[4 * q + 1] << 8) | (code[4 * q + 2] << 16) | (code[4 * q + 3] << 24);
         }
-        st_u4_pol(rowp + c * BYTES, w[0], w[1], w[2], w[3], pol);
+        st_u4(rowp + c * BYTES, w[0], w[1], w[2], w[3], keep);
       } else {
 #pragma unroll
         for (int e = 0; e < CH; ++e) {
@@ -385,8 +389,9 @@ constexpr int sig_last_ger(int sig) {
 // FP32 forms are latency bound and need four blocks of eight warps.
 template <int NW, int V, int NMAT, int FMT, bool VEC, int U>
 constexpr int min_blocks() {
-  return (NW == 8 && V == 1 && NMAT == 1 && FMT == FMT_F32) ? (U >= 8 ? 3 : 4)
-                                                              : ((FMT != FMT_F32 && VEC) ? 2 : 1);
+  return (NW == 8 && V == 1 && NMAT == 1 && FMT == FMT_F32)   ? (U >= 8 ? 3 : 4)
+         : (NW == 8 && V == 1 && NMAT == 2 && FMT == FMT_F32) ? (U >= 8 ? 2 : 3)
+                                                                : ((FMT != FMT_F32 && VEC) ? 2 : 1);
 }
 
 // BF16 GEMVER passes (GER chain + GEMVT, and GEMV) with 8 rows in flight
@@ -462,10 +467,10 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks_sig<
   const int64_t cslots = (int64_t)P.n_groups + (nsets > 1 ? nsets : 0);
   unsigned* setcnt = P.counters + P.n_strips + MAT_MAXGROUPS;  // [n_strips][MAT_MAXSETS]
   const bool rev = P.reverse_rows != 0;
-  // matrix loads: evict-first when the data is read once; matrix output:
-  // kept at normal priority when the next pass reads it, else evict-first
-  const uint64_t lpol = P.l2_loads_first ? l2_policy_first() : l2_policy_normal();
-  const uint64_t spol = P.l2_keep_out ? l2_policy_normal() : l2_policy_first();
+  // matrix loads stream with the evict-first hint; a matrix output the next
+  // pass reads is stored plainly (normal L2 priority), else streamed
+  const uint64_t lpol = l2_policy_first();
+  const bool keep_out = P.l2_keep_out != 0;
   const bool ring = STAGED && (col0 + SW <= n);  // block-uniform
   char* ringp = reinterpret_cast<char*>(smem4);
 
@@ -718,7 +723,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks_sig<
                     const int64_t row = row0 + rr;
                     quant_store_row<FMT, V, VEC>(P.Bout[0], P.ldb[0], row, row < m, wcol0, n, lane, ar[0],
                                                  __shfl_sync(FULL_MASK, sbrow, rr),
-                                                 __shfl_sync(FULL_MASK, isbrow, rr), spol);
+                                                 __shfl_sync(FULL_MASK, isbrow, rr), keep_out);
                   }
                 }
               }
@@ -728,7 +733,7 @@ __global__ void __launch_bounds__((NW + (STAGED ? 1 : 0)) * 32, (min_blocks_sig<
 #pragma unroll
               for (int t = 0; t < NMAT; ++t)
                 if (P.Bout[t] != nullptr)
-                  store_row<CH, V, VEC>(P.Bout[t], P.ldb[t], row, wcol0, n, lane, ar[t], spol);
+                  store_row<CH, V, VEC>(P.Bout[t], P.ldb[t], row, wcol0, n, lane, ar[t], keep_out);
             }
           }
         }
