@@ -255,6 +255,27 @@ class Suite:
 SEQS = ["bicgk", "gemver", "gesummv", "atax", "axpydot", "waxpby"]
 
 
+def fused_launches(kf, seq, sizes):
+    """Kernel launches of one fused call of `seq`.  GEMVER takes one launch
+    when its first-use tuning chose the single cooperative launch (the tuning
+    cache's "gemver_form" entry for the size class is 1), else two."""
+    if seq != "gemver":
+        return Suite.FUSED_LAUNCHES[seq]
+    import tempfile
+    n = sizes["gemver"]
+    key = f"gemver_form {n.bit_length() - 1} : "
+    fd, path = tempfile.mkstemp(suffix=".txt")
+    os.close(fd)
+    try:
+        kf.kf_tune_cache_save(path)
+        for line in open(path):
+            if line.startswith(key):
+                return 1 if line[len(key):].split()[0] == "1" else 2
+    finally:
+        os.unlink(path)
+    return 2
+
+
 # ---------------------------------------------------------------- cuBLAS context
 
 class CublasChain:
@@ -1337,7 +1358,7 @@ def main():
         "sequences": seqinfo,
         "roofline": roof,
         "clocks": clk,
-        "gpu_launches": args.steps * sum(Suite.FUSED_LAUNCHES[s] for s in seqs),
+        "gpu_launches": args.steps * sum(fused_launches(kf, s, sizes) for s in seqs),
     }
     if read_probe is not None:
         line["read_probe"] = read_probe
