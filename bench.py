@@ -255,15 +255,11 @@ class Suite:
 SEQS = ["bicgk", "gemver", "gesummv", "atax", "axpydot", "waxpby"]
 
 
-def fused_launches(kf, seq, sizes):
-    """Kernel launches of one fused call of `seq`.  GEMVER takes one launch
-    when its first-use tuning chose the single cooperative launch (the tuning
-    cache's "gemver_form" entry for the size class is 1), else two."""
-    if seq != "gemver":
-        return Suite.FUSED_LAUNCHES[seq]
+def cached_form(kf, key):
+    """The form (1 = one launch, 2 = two) the tuning cache holds for `key`
+    ("gemver_form b" or "sgemvt_form bm bn"), 2 when it holds none."""
     import tempfile
-    n = sizes["gemver"]
-    key = f"gemver_form {n.bit_length() - 1} : "
+    key = key + " : "
     fd, path = tempfile.mkstemp(suffix=".txt")
     os.close(fd)
     try:
@@ -274,6 +270,15 @@ def fused_launches(kf, seq, sizes):
     finally:
         os.unlink(path)
     return 2
+
+
+def fused_launches(kf, seq, sizes):
+    """Kernel launches of one fused call of `seq`.  GEMVER takes one launch
+    when its first-use tuning chose the single cooperative launch (the tuning
+    cache's "gemver_form" entry for the size class is 1), else two."""
+    if seq != "gemver":
+        return Suite.FUSED_LAUNCHES[seq]
+    return cached_form(kf, f"gemver_form {sizes['gemver'].bit_length() - 1}")
 
 
 # ---------------------------------------------------------------- cuBLAS context
@@ -701,7 +706,14 @@ def table1_section(kf, d, st, steps, warmup, n_mat=8192, n_vec=1 << 26):
     for seq, (fused, unfused, size, nl_f, nl_u) in calls.items():
         alg, unf = table1_bytes(seq, size)
         ms = time_calls(fused, steps, warmup, st)
+        if seq == "sgemvt":  # the form kf_sgemvt's first-use tuning chose (the call above ran it)
+            b = n.bit_length() - 1
+            nl_f = cached_form(kf, f"sgemvt_form {b} {b}")
         r = {"size": size, "ms": ms, "gbs": alg / (ms * 1e-3) / 1e9, "launches": nl_f}
+        if seq == "sgemvt":
+            ms1 = time_calls(lambda s: kf.kf_sgemvt_single(A, y, z, ALPHA, BETA, o1, o2, W, stream=s),
+                             steps, warmup, st)
+            r.update({"single_launch_ms": ms1, "single_launch_gbs": alg / (ms1 * 1e-3) / 1e9})
         r["frac"] = r["gbs"] / peak
         if unfused is not None:
             ums = time_calls(unfused, steps, warmup, st)

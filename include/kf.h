@@ -187,18 +187,30 @@ kf_status kf_gemver_q(int64_t n, const void* QA, int64_t lda, kf_dtype fmt, cons
                       float alpha, float beta, void* QB, int64_t ldb, float* sB, float* x, float* w, void* ws,
                       size_t ws_bytes, void* stream);
 
-/* GESUMMV (Table 1): y = alpha A x + beta B x.  A, B: m x n with the same
- * leading dimension; x: length n; y: length m.  One launch; x is read once
- * per column strip for both matrices. */
 /* SGEMVT (Table 1): x = beta A^T y + z; w = alpha A x.  A: m x n; y, w:
- * length m; z, x: length n.  Two launches (w needs all of x: a global
- * barrier, Section 3.2.2), each one read of A; the second walks each row
- * group from the rows the first read last, which are then still in L2.
- * ws: kf_workspace_size(KF_SEQ_SGEMVT, m, n).  Errors: KF_ERR_INVALID_ARG,
- * KF_ERR_SHAPE, KF_ERR_WORKSPACE. */
+ * length m; z, x: length n.  w needs all of x (a global barrier, Section
+ * 3.2.2).  Two forms, each reading A twice: two launches, the second
+ * walking each row group from the rows the first read last (then still in
+ * L2); or kf_sgemvt_single's one cooperative launch.  kf_sgemvt takes the
+ * single launch where its tuning on first use measured it more than 2 %
+ * faster at that size class (tuning cache key "sgemvt_form log2(m)
+ * log2(n)"), else two launches.  ws: kf_workspace_size(KF_SEQ_SGEMVT, m, n).
+ * Errors: KF_ERR_INVALID_ARG, KF_ERR_SHAPE, KF_ERR_WORKSPACE. */
 kf_status kf_sgemvt(int64_t m, int64_t n, const float* A, int64_t lda, const float* y, const float* z,
                     float alpha, float beta, float* x, float* w, void* ws, size_t ws_bytes, void* stream);
 
+/* SGEMVT in one cooperative launch: the kernel of kf_gemver_single without
+ * the rank-one updates and the stored matrix; the second phase rereads A in
+ * reverse row order.  x and w are sums in another fixed order than the two
+ * launches'.  Needs m >= 8, n a multiple of 4, lda a multiple of 4 and
+ * 16-byte aligned operands (else KF_ERR_UNSUPPORTED).  ws:
+ * kf_workspace_size(KF_SEQ_SGEMVT, m, n). */
+kf_status kf_sgemvt_single(int64_t m, int64_t n, const float* A, int64_t lda, const float* y, const float* z,
+                           float alpha, float beta, float* x, float* w, void* ws, size_t ws_bytes, void* stream);
+
+/* GESUMMV (Table 1): y = alpha A x + beta B x.  A, B: m x n with the same
+ * leading dimension; x: length n; y: length m.  One launch; x is read once
+ * per column strip for both matrices. */
 kf_status kf_gesummv(int64_t m, int64_t n, const float* A, const float* B, int64_t lda,
                      const float* x, float alpha, float beta, float* y, void* ws, size_t ws_bytes,
                      void* stream);

@@ -23,6 +23,10 @@ bool gemver_single_ok(int64_t n, const float* A, int64_t lda, const float* B, in
 int launch_gemver_single(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1, const float* u2,
                          const float* v2, const float* y, const float* z, float alpha, float beta, float* B,
                          int64_t ldb, float* x, float* w, void* ws, size_t ws_bytes, void* stream, const char** why);
+bool sgemvt_single_ok(int64_t m, int64_t n, const float* A, int64_t lda, const float* const* vecs, int nvec);
+int launch_sgemvt_single(int64_t m, int64_t n, const float* A, int64_t lda, const float* y, const float* z,
+                         float alpha, float beta, float* x, float* w, void* ws, size_t ws_bytes, void* stream,
+                         const char** why);
 bool tune_cache_get_mat(const std::string& k, MatTune* t);
 void tune_cache_put_mat(const std::string& k, const MatTune& t);
 bool tune_on_first_use(void* stream);
@@ -331,6 +335,50 @@ static kf_status gemver_two_pass(int64_t n, const float* A, int64_t lda, const f
   return run_mat(Q, ws, ws_bytes, stream);
 }
 
+static int log2_floor(int64_t v) {
+  int b = 0;
+  while (b < 62 && (int64_t(1) << (b + 1)) <= v) ++b;
+  return b;
+}
+
+// The form of a sequence with a one-launch and a two-launch implementation,
+// by the tuning cache (key: warps 1 = one launch, 2 = two); on a miss with
+// tuning on first use, both forms are timed on the call's operands (mean of
+// `reps` back-to-back calls, best of two rounds, after one run of the
+// two-launch form that lets its passes tune) and the one launch kept only if
+// it gains more than 2 %; else the two-launch form.
+extern "C++" {
+template <class Two, class One>
+static int choose_form(const std::string& key, void* stream, Two two, One one) {
+  MatTune t{};
+  if (tune_cache_get_mat(key, &t)) return t.warps == 1 ? 1 : 2;
+  if (!tune_on_first_use(stream)) return 2;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int reps = std::max(1, g_autotune_reps.load());
+  if (two() != KF_OK) return 2;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best[3] = {0.f, 1e30f, 1e30f};
+  kf_status rc = KF_OK;
+  for (int f : {2, 1, 2, 1}) {
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && rc == KF_OK; ++r) rc = f == 2 ? two() : one();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best[f] = std::min(best[f], ms / (float)reps);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != KF_OK) return 2;
+  const int form = best[1] < 0.98f * best[2] ? 1 : 2;
+  tune_cache_put_mat(key, MatTune{form, 0, 0, 0, 0});
+  return form;
+}
+}  // extern "C++"
+
 static kf_status check_gemver(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
                        const float* u2, const float* v2, const float* y, const float* z, float* B, int64_t ldb,
                        float* x, float* w) {
@@ -366,45 +414,13 @@ kf_status kf_gemver(int64_t n, const float* A, int64_t lda, const float* u1, con
   const float* vecs[8] = {u1, v1, u2, v2, y, z, x, w};
   const bool single_ok = gemver_single_ok(n, A, lda, B, ldb, vecs, 8) && ws != nullptr &&
                          ws_bytes >= matprog_workspace_bytes(n, n, 1, 1, FMT_F32) && cur_tune().warps == 0;
-  // The form, by the tuning cache ("gemver_form log2(n)": warps 1 = single
-  // launch, 2 = two passes); on a miss with tuning on first use, both forms
-  // are timed on the call's operands and the faster stored (two passes
-  // unless the single launch gains more than 2 %); else two passes.
-  int form = 2;
-  if (single_ok) {
-    int b = 0;
-    while (b < 62 && (int64_t(1) << (b + 1)) <= n) ++b;
-    const std::string key = "gemver_form " + std::to_string(b);
-    MatTune t{};
-    if (tune_cache_get_mat(key, &t)) {
-      form = t.warps;
-    } else if (tune_on_first_use(stream)) {
-      cudaStream_t st = (cudaStream_t)stream;
-      const int reps = std::max(1, g_autotune_reps.load());
-      CHK(gemver_two_pass(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream));
-      cudaEvent_t e0, e1;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      float best[3] = {0.f, 1e30f, 1e30f};
-      kf_status rc = KF_OK;
-      for (int f : {2, 1, 2, 1}) {
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < reps && rc == KF_OK; ++r)
-          rc = f == 2 ? gemver_two_pass(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream)
-                      : kf_gemver_single(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        best[f] = std::min(best[f], ms / (float)reps);
-      }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      if (rc != KF_OK) return rc;
-      form = best[1] < 0.98f * best[2] ? 1 : 2;
-      tune_cache_put_mat(key, MatTune{form, 0, 0, 0, 0});
-    }
-  }
+  auto two = [&]() {
+    return gemver_two_pass(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream);
+  };
+  auto one = [&]() {
+    return kf_gemver_single(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream);
+  };
+  const int form = single_ok ? choose_form("gemver_form " + std::to_string(log2_floor(n)), stream, two, one) : 2;
   if (form == 1)
     return kf_gemver_single(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream);
   return gemver_two_pass(n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream);
@@ -460,12 +476,8 @@ kf_status kf_gemver_q(int64_t n, const void* QA, int64_t lda, kf_dtype fmt, cons
   return run_mat(Q, ws, ws_bytes, stream);
 }
 
-kf_status kf_sgemvt(int64_t m, int64_t n, const float* A, int64_t lda, const float* y, const float* z,
+static kf_status sgemvt_two_pass(int64_t m, int64_t n, const float* A, int64_t lda, const float* y, const float* z,
                      float alpha, float beta, float* x, float* w, void* ws, size_t ws_bytes, void* stream) {
-  CHK(check_mat(m, n, A, lda));
-  CHK(check_vec(m, y, "y")); CHK(check_vec(n, z, "z"));
-  CHK(check_vec(n, x, "x")); CHK(check_vec(m, w, "w"));
-  if (m == 0 && n == 0) return KF_OK;
   // Pass 1: x = beta A^T y + z.
   MatProg P = new_prog(m, n);
   P.nmat = 1; P.fmt = FMT_F32; P.A[0] = A; P.lda[0] = lda;
@@ -486,6 +498,36 @@ kf_status kf_sgemvt(int64_t m, int64_t n, const float* A, int64_t lda, const flo
   Q.nrow_res = 1; Q.ncol_res = 1;
   Q.nrow_out = 1; Q.row_out[0] = epi1(w, alpha);
   return run_mat(Q, ws, ws_bytes, stream);
+}
+
+kf_status kf_sgemvt_single(int64_t m, int64_t n, const float* A, int64_t lda, const float* y, const float* z,
+                           float alpha, float beta, float* x, float* w, void* ws, size_t ws_bytes, void* stream) {
+  CHK(check_mat(m, n, A, lda));
+  CHK(check_vec(m, y, "y")); CHK(check_vec(n, z, "z"));
+  CHK(check_vec(n, x, "x")); CHK(check_vec(m, w, "w"));
+  if (m == 0 && n == 0) return KF_OK;
+  const float* vecs[4] = {y, z, x, w};
+  REQ(sgemvt_single_ok(m, n, A, lda, vecs, 4), KF_ERR_UNSUPPORTED,
+      "the single launch needs m >= 8, n a multiple of 4 and 16-byte aligned operands");
+  const char* why = nullptr;
+  return from_launch(launch_sgemvt_single(m, n, A, lda, y, z, alpha, beta, x, w, ws, ws_bytes, stream, &why), why);
+}
+
+kf_status kf_sgemvt(int64_t m, int64_t n, const float* A, int64_t lda, const float* y, const float* z,
+                    float alpha, float beta, float* x, float* w, void* ws, size_t ws_bytes, void* stream) {
+  CHK(check_mat(m, n, A, lda));
+  CHK(check_vec(m, y, "y")); CHK(check_vec(n, z, "z"));
+  CHK(check_vec(n, x, "x")); CHK(check_vec(m, w, "w"));
+  if (m == 0 && n == 0) return KF_OK;
+  const float* vecs[4] = {y, z, x, w};
+  const bool single_ok = sgemvt_single_ok(m, n, A, lda, vecs, 4) && ws != nullptr &&
+                         ws_bytes >= matprog_workspace_bytes(m, n, 1, 1, FMT_F32) && cur_tune().warps == 0;
+  auto two = [&]() { return sgemvt_two_pass(m, n, A, lda, y, z, alpha, beta, x, w, ws, ws_bytes, stream); };
+  auto one = [&]() { return kf_sgemvt_single(m, n, A, lda, y, z, alpha, beta, x, w, ws, ws_bytes, stream); };
+  const int form = single_ok ? choose_form("sgemvt_form " + std::to_string(log2_floor(m)) + " " +
+                                               std::to_string(log2_floor(n)), stream, two, one)
+                             : 2;
+  return form == 1 ? one() : two();
 }
 
 kf_status kf_gesummv(int64_t m, int64_t n, const float* A, const float* B, int64_t lda,

@@ -34,7 +34,7 @@ constexpr int G1_U = 4;                   // rows loaded together
 constexpr int G1_SET = 8;                 // group partials per first-level sum
 
 struct GemverArgs {
-  int64_t n, lda, ldb;
+  int64_t m, n, lda, ldb;  // A (and B) m x n; GEMVER: m = n
   const float* A;
   float* B;
   const float *u1, *v1, *u2, *v2, *y, *z;
@@ -42,7 +42,7 @@ struct GemverArgs {
   float* x;
   float* w;
   float* colpart;     // [groups + sets][n]
-  float* rowpart;     // [strips][n]
+  float* rowpart;     // [strips][m]
   unsigned* bar;      // [0]: arrivals, [1]: blocks done (zero between launches)
   unsigned* err;      // device error word
   int strips, groups, upg;
@@ -106,17 +106,22 @@ __device__ __forceinline__ float g1_reduce8(float (&d)[8], int lane) {
   return d[0];
 }
 
+// GER: GEMVER (B = A + u1 v1^T + u2 v2^T written in phase 1 and reread in
+// phase 2, A read evict-first); !GER: SGEMVT (x = beta A^T y + z,
+// w = alpha A x: phase 2 rereads A, which phase 1 reads at normal L2
+// priority so that the rows it read last are still in L2).
+template <bool GER>
 __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const __grid_constant__ GemverArgs a) {
   __shared__ float red[G1_WARPS][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int strip = (int)(blockIdx.x % a.strips), group = (int)(blockIdx.x / a.strips);
-  const int64_t n = a.n;
+  const int64_t m = a.m, n = a.n;
   const int64_t col = (int64_t)strip * G1_SW + warp * 128 + lane * 4;  // this lane's four columns
   const bool col_ok = col < n;                                         // n is a multiple of 4
-  const int64_t nunits = (n + 7) >> 3;
+  const int64_t nunits = (m + 7) >> 3;
   const int64_t u0 = std::min<int64_t>(nunits, (int64_t)group * a.upg);
   const int64_t u1e = std::min<int64_t>(nunits, u0 + a.upg);
-  const int64_t r0 = u0 << 3, r1 = std::min<int64_t>(n, u1e << 3);
+  const int64_t r0 = u0 << 3, r1 = std::min<int64_t>(m, u1e << 3);
   const uint64_t pol_first = l2_policy_first();
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   unsigned k = 0;  // barriers passed
@@ -124,15 +129,15 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
 
   // ---- phase 1: B = A + u1 v1^T + u2 v2^T (written once), column sums of B^T y
   {
-    const float4 v1c = col_ok ? __ldg(reinterpret_cast<const float4*>(a.v1 + col)) : z4;
-    const float4 v2c = col_ok ? __ldg(reinterpret_cast<const float4*>(a.v2 + col)) : z4;
+    const float4 v1c = (GER && col_ok) ? __ldg(reinterpret_cast<const float4*>(a.v1 + col)) : z4;
+    const float4 v2c = (GER && col_ok) ? __ldg(reinterpret_cast<const float4*>(a.v2 + col)) : z4;
     float4 t = z4;
     for (int64_t rb = r0 & ~(int64_t)31; rb < r1; rb += 32) {
       // the 32-row block's row scalars, one per lane, shared by shuffles
       const int64_t lr = rb + lane;
       const bool lr_ok = lr >= r0 && lr < r1;
-      const float lu1 = lr_ok ? __ldg(a.u1 + lr) : 0.f;
-      const float lu2 = lr_ok ? __ldg(a.u2 + lr) : 0.f;
+      const float lu1 = (GER && lr_ok) ? __ldg(a.u1 + lr) : 0.f;
+      const float lu2 = (GER && lr_ok) ? __ldg(a.u2 + lr) : 0.f;
       const float ly = lr_ok ? __ldg(a.y + lr) : 0.f;
       const int64_t lo = std::max(r0, rb), hi = std::min(r1, rb + 32);
       for (int64_t row = lo; row < hi; row += G1_U) {
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
         for (int u = 0; u < G1_U; ++u) {
           const int64_t rr = row + u;
           if (rr < hi && col_ok) {
-            const uint4 q = ld_stream16_pol(a.A + rr * a.lda + col, pol_first);
+            const uint4 q = GER ? ld_stream16_pol(a.A + rr * a.lda + col, pol_first) : ld_stream16(a.A + rr * a.lda + col);
             av[u] = make_float4(__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z), __uint_as_float(q.w));
           } else {
             av[u] = z4;
@@ -155,12 +160,14 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
           const float s2 = __shfl_sync(FULL_MASK, lu2, src);
           const float sy = __shfl_sync(FULL_MASK, ly, src);
           if (rr < hi) {
-            float4 b;
-            b.x = fmaf(s2, v2c.x, fmaf(s1, v1c.x, av[u].x));
-            b.y = fmaf(s2, v2c.y, fmaf(s1, v1c.y, av[u].y));
-            b.z = fmaf(s2, v2c.z, fmaf(s1, v1c.z, av[u].z));
-            b.w = fmaf(s2, v2c.w, fmaf(s1, v1c.w, av[u].w));
-            if (col_ok) st_f4_keep(a.B + rr * a.ldb + col, b);  // reread in phase 2
+            float4 b = av[u];
+            if constexpr (GER) {
+              b.x = fmaf(s2, v2c.x, fmaf(s1, v1c.x, av[u].x));
+              b.y = fmaf(s2, v2c.y, fmaf(s1, v1c.y, av[u].y));
+              b.z = fmaf(s2, v2c.z, fmaf(s1, v1c.z, av[u].z));
+              b.w = fmaf(s2, v2c.w, fmaf(s1, v1c.w, av[u].w));
+              if (col_ok) st_f4_keep(a.B + rr * a.ldb + col, b);  // reread in phase 2
+            }
             t.x = fmaf(b.x, sy, t.x);
             t.y = fmaf(b.y, sy, t.y);
             t.z = fmaf(b.z, sy, t.z);
@@ -215,9 +222,11 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
   }
 
   // ---- phase 2: w's row partials over the same rows, walked from the last
-  // 8-row unit to the first (this thread reads back what it wrote)
+  // 8-row unit to the first (GEMVER: this thread reads back what it wrote)
   if (ok) {
     const float4 xv = col_ok ? ld_cg4(a.x + col) : z4;
+    const float* M2 = GER ? a.B : a.A;
+    const int64_t ld2 = GER ? a.ldb : a.lda;
     for (int64_t un = u1e - 1; un >= u0; --un) {
       float dacc[8];
 #pragma unroll
@@ -228,8 +237,8 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
 #pragma unroll
         for (int u = 0; u < G1_U; ++u) {
           const int64_t rr = (un << 3) + r + u;
-          if (rr < n && col_ok) {
-            const uint4 q = ld_stream16_pol(a.B + rr * a.ldb + col, pol_first);
+          if (rr < m && col_ok) {
+            const uint4 q = ld_stream16_pol(M2 + rr * ld2 + col, pol_first);
             bv[u] = make_float4(__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z), __uint_as_float(q.w));
           } else {
             bv[u] = z4;
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
         float s = 0.f;
 #pragma unroll
         for (int wq = 0; wq < G1_WARPS; ++wq) s += red[wq][threadIdx.x];
-        if (rr < n) a.rowpart[(int64_t)strip * n + rr] = s;
+        if (rr < m) a.rowpart[(int64_t)strip * m + rr] = s;
       }
       __syncthreads();
     }
@@ -260,9 +269,9 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
 
   // ---- w = alpha * (strip partials, added in strip order), by the whole grid
   if (ok) {
-    for (int64_t i = gtid; i < n; i += gstride) {
+    for (int64_t i = gtid; i < m; i += gstride) {
       float s = 0.f;
-      for (int st = 0; st < a.strips; ++st) s += __ldcg(a.rowpart + (int64_t)st * n + i);
+      for (int st = 0; st < a.strips; ++st) s += __ldcg(a.rowpart + (int64_t)st * m + i);
       a.w[i] = __fmul_rn(a.alpha, s);
     }
   }
@@ -293,37 +302,43 @@ bool gemver_single_ok(int64_t n, const float* A, int64_t lda, const float* B, in
   return true;
 }
 
-// The workspace is kf_gemver's: the matrix pass's layout, whose row and
-// column partial regions this launch uses (its counters stay untouched), and
-// two barrier words at byte 128 of the header, zero between launches.
-int launch_gemver_single(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1, const float* u2,
-                         const float* v2, const float* y, const float* z, float alpha, float beta, float* B,
-                         int64_t ldb, float* x, float* w, void* ws, size_t ws_bytes, void* stream, const char** why) {
+// The workspace is the matrix pass's layout for an m x n pass with one row
+// and one column result (kf_gemver's and kf_sgemvt's): this launch uses its
+// row and column partial regions (the counters stay untouched) and two
+// barrier words at byte 128 of the header, zero between launches.
+namespace {
+int launch_single(bool ger, int64_t m, int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
+                  const float* u2, const float* v2, const float* y, const float* z, float alpha, float beta, float* B,
+                  int64_t ldb, float* x, float* w, void* ws, size_t ws_bytes, void* stream, const char** why) {
   MatProg L{};
-  L.m = n; L.n = n; L.fmt = FMT_F32; L.nrow_res = 1; L.ncol_res = 1; L.nrow_out = 1; L.ncol_out = 1;
+  L.m = m; L.n = n; L.fmt = FMT_F32; L.nrow_res = 1; L.ncol_res = 1; L.nrow_out = 1; L.ncol_out = 1;
   if (matprog_bind_workspace(L, ws, ws_bytes) != 0) {
     *why = "workspace missing or smaller than kf_workspace_size()";
     return -11;
   }
-  const void* fn = (const void*)&gemver_single_kernel;
+  const void* fn = ger ? (const void*)&gemver_single_kernel<true> : (const void*)&gemver_single_kernel<false>;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, G1_WARPS * 32, 0) != cudaSuccess || occ < 1) {
     *why = "occupancy query failed";
     return -7;
   }
   GemverArgs a{};
-  a.n = n; a.lda = lda; a.ldb = ldb; a.A = A; a.B = B;
+  a.m = m; a.n = n; a.lda = lda; a.ldb = ldb; a.A = A; a.B = B;
   a.u1 = u1; a.v1 = v1; a.u2 = u2; a.v2 = v2; a.y = y; a.z = z;
   a.alpha = alpha; a.beta = beta; a.x = x; a.w = w;
   char* b = static_cast<char*>(ws);
   a.err = reinterpret_cast<unsigned*>(b);
   a.bar = reinterpret_cast<unsigned*>(b + 128);
   a.colpart = L.colpart;  // (MAT_MAXGROUPS + MAT_MAXSETS) x n floats
-  a.rowpart = L.rowpart;  // ceil(n / 128) x n floats >= strips x n
+  a.rowpart = L.rowpart;  // ceil(n / 128) x m floats >= strips x m
   a.strips = (int)((n + G1_SW - 1) / G1_SW);
   // every block resident at once: strips x groups within one wave
   const int64_t slots = (int64_t)device_sm_count() * occ;
-  const int64_t nunits = (n + 7) / 8;
+  const int64_t nunits = (m + 7) / 8;
+  if (a.strips > slots) {
+    *why = "matrix too wide for one wave of blocks";
+    return -10;
+  }
   int64_t G = std::max<int64_t>(1, slots / a.strips);
   G = std::min<int64_t>(G, std::min<int64_t>(nunits, MAT_MAXGROUPS));
   const int64_t upg = (nunits + G - 1) / G;
@@ -339,6 +354,30 @@ int launch_gemver_single(int64_t n, const float* A, int64_t lda, const float* u1
     return -7;
   }
   return 0;
+}
+}  // namespace
+
+int launch_gemver_single(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1, const float* u2,
+                         const float* v2, const float* y, const float* z, float alpha, float beta, float* B,
+                         int64_t ldb, float* x, float* w, void* ws, size_t ws_bytes, void* stream, const char** why) {
+  return launch_single(true, n, n, A, lda, u1, v1, u2, v2, y, z, alpha, beta, B, ldb, x, w, ws, ws_bytes, stream, why);
+}
+
+// SGEMVT in one launch: x = beta A^T y + z, w = alpha A x (A m x n, m >= 8,
+// n a multiple of 4, operands 16-byte aligned: sgemvt_single_ok).
+bool sgemvt_single_ok(int64_t m, int64_t n, const float* A, int64_t lda, const float* const* vecs, int nvec) {
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (m < 8 || n < 4 || n % 4 != 0 || lda % 4 != 0 || !al(A)) return false;
+  for (int i = 0; i < nvec; ++i)
+    if (!al(vecs[i])) return false;
+  return true;
+}
+
+int launch_sgemvt_single(int64_t m, int64_t n, const float* A, int64_t lda, const float* y, const float* z,
+                         float alpha, float beta, float* x, float* w, void* ws, size_t ws_bytes, void* stream,
+                         const char** why) {
+  return launch_single(false, m, n, A, lda, nullptr, nullptr, nullptr, nullptr, y, z, alpha, beta, nullptr, 0, x, w,
+                       ws, ws_bytes, stream, why);
 }
 
 }  // namespace kf

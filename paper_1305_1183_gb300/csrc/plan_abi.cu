@@ -550,7 +550,8 @@ kf_status kf_tune_cache_load(const char* path, int* loaded) {
     const std::string key = line.substr(0, colon);
     int v[5] = {0, 0, 0, 0, 0};
     const int got = std::sscanf(line.c_str() + colon + 3, "%d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4]);
-    if ((key.rfind("mat ", 0) == 0 || key.rfind("atax ", 0) == 0 || key.rfind("gemver_form ", 0) == 0) &&
+    if ((key.rfind("mat ", 0) == 0 || key.rfind("atax ", 0) == 0 || key.rfind("gemver_form ", 0) == 0 ||
+         key.rfind("sgemvt_form ", 0) == 0) &&
         got == 5) {
       tune_cache_put_mat(key, MatTune{v[0], v[1], v[2], v[3], v[4]});
       ++n;

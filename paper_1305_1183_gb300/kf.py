@@ -58,6 +58,7 @@ _SIGS = {
     "kf_gemver_q": ([i64, vp, i64, ci, vp, vp, vp, vp, vp, vp, vp, f32, f32, vp, i64, vp, vp, vp, vp, sz, vp], ci),
     "kf_gesummv": ([i64, i64, vp, vp, i64, vp, f32, f32, vp, vp, sz, vp], ci),
     "kf_sgemvt": ([i64, i64, vp, i64, vp, vp, f32, f32, vp, vp, vp, sz, vp], ci),
+    "kf_sgemvt_single": ([i64, i64, vp, i64, vp, vp, f32, f32, vp, vp, vp, sz, vp], ci),
     "kf_atax": ([i64, i64, vp, i64, vp, vp, vp, sz, vp], ci),
     "kf_axpydot": ([i64, vp, vp, vp, f32, vp, vp, vp, sz, vp], ci),
     "kf_waxpby": ([i64, f32, vp, f32, vp, vp, vp], ci),
@@ -305,6 +306,15 @@ def kf_sgemvt(A, y, z, alpha, beta, x, w, ws, stream=None):
     m, n = A.shape
     _ck(lib().kf_sgemvt(m, n, _p(A), A.stride(0), _p(y), _p(z), alpha, beta, _p(x), _p(w), _p(ws), _nb(ws),
                         _st(stream)))
+
+
+def kf_sgemvt_single(A, y, z, alpha, beta, x, w, ws, stream=None):
+    """SGEMVT in one cooperative launch (see include/kf.h)."""
+    _mat(A)
+    _vec(y, z, x, w)
+    m, n = A.shape
+    _ck(lib().kf_sgemvt_single(m, n, _p(A), A.stride(0), _p(y), _p(z), alpha, beta, _p(x), _p(w), _p(ws),
+                               _nb(ws), _st(stream)))
 
 
 def kf_atax(A, x, y, ws, stream=None):

@@ -255,6 +255,49 @@ def test_sgemvt_identity_and_empty(built):
     assert torch.equal(x, z)
 
 
+@pytest.mark.parametrize("m,n", [(8, 4), (31, 36), (513, 4096), (2048, 2048), (4100, 700), (3001, 516),
+                                 (64, 8192)])
+def test_sgemvt_single_launch(built, m, n):
+    """kf_sgemvt_single (grid-wide barriers instead of a kernel boundary,
+    rectangular A): x and w within the oracle tolerance; three calls in a
+    row, each followed by the two-launch form on the same workspace."""
+    kf = built
+    A, y, z = U((m, n), 1), U((m,), 4), U((n,), 9)
+    W = ws(kf, kf.KF_SEQ_SGEMVT, m, n)
+    Ah, yh, zh = host(A), host(y), host(z)
+    xo, wo = oracle.sgemvt(Ah, yh, zh, ALPHA, BETA)
+    sx = BETA * oracle.abs_gemvt(Ah, yh) + np.abs(zh)
+    sw = ALPHA * oracle.abs_gemv(Ah, np.abs(xo) + sx)
+    for call in range(3):
+        x = torch.full((n,), float("nan"), device=dev()); w = torch.full((m,), float("nan"), device=dev())
+        kf.kf_sgemvt_single(A, y, z, ALPHA, BETA, x, w, W)
+        check_reduce(host(x), xo, sx, m, f"x, call {call}")
+        check_reduce(host(w), wo, sw, max(m, n), f"w, call {call}")
+        x2 = torch.empty(n, device=dev()); w2 = torch.empty(m, device=dev())
+        kf.kf_sgemvt(A, y, z, ALPHA, BETA, x2, w2, W)
+        check_reduce(host(x2), xo, sx, m, "x two-pass")
+        check_reduce(host(w2), wo, sw, max(m, n), "w two-pass")
+    kf.kf_workspace_status(W)
+
+
+def test_sgemvt_single_launch_exact_and_refusals(built):
+    """A = I with integer inputs: x = 2 y + z and w = 2 x bit for bit in one
+    launch; shapes outside the single launch's rule are refused."""
+    kf = built
+    n = 776
+    A = torch.eye(n, device=dev())
+    y, z = I((n,), 4), I((n,), 9)
+    x = torch.empty(n, device=dev()); w = torch.empty(n, device=dev())
+    kf.kf_sgemvt_single(A, y, z, 2.0, 2.0, x, w, ws(kf, kf.KF_SEQ_SGEMVT, n, n))
+    assert torch.equal(x, 2 * y + z) and torch.equal(w, 2 * x)
+    for m, n in [(100, 514), (7, 64)]:   # n not a multiple of 4; m < 8
+        A, y, z = U((m, n), 1), U((m,), 4), U((n,), 9)
+        x = torch.empty(n, device=dev()); w = torch.empty(m, device=dev())
+        with pytest.raises(kf.KFError) as e:
+            kf.kf_sgemvt_single(A, y, z, ALPHA, BETA, x, w, ws(kf, kf.KF_SEQ_SGEMVT, m, n))
+        assert e.value.status == kf.KF_ERR_UNSUPPORTED
+
+
 # ------------------------------------------------------------------ GESUMMV
 
 @pytest.mark.parametrize("m,n", [(1, 1), (31, 33), (1000, 1003), (2048, 2048), (513, 4096)])

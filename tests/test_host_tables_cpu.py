@@ -121,16 +121,17 @@ def test_tuning_cache_file_round_trip(kf, tmp_path):
         assert len(dev) == 1 and len(lines) == 2
         f = tmp_path / "cache.txt"
         f.write_text(f"# hand-written\n{dev[0]}\nmat key one : 8 2 2 0 4\nvec key two : 256 4 1\n"
-                     "atax 13 13 : 1 1 1 0 0\ngemver_form 13 : 1 0 0 0 0\n"
+                     "atax 13 13 : 1 1 1 0 0\ngemver_form 13 : 1 0 0 0 0\nsgemvt_form 12 13 : 2 0 0 0 0\n"
                      "device another_part_sm1\nmat foreign : 8 1 4 0 4\n")
         assert L.kf_tune_cache_load(str(f).encode(), ctypes.byref(n)) == 0
-        assert n.value == 4
-        assert L.kf_tune_cache_entries(ctypes.byref(n)) == 0 and n.value == 4
+        assert n.value == 5
+        assert L.kf_tune_cache_entries(ctypes.byref(n)) == 0 and n.value == 5
         p1 = tmp_path / "saved.txt"
         assert L.kf_tune_cache_save(str(p1).encode()) == 0
         saved = p1.read_text().splitlines()
         assert "mat key one : 8 2 2 0 4" in saved and "vec key two : 256 4 1" in saved
         assert "atax 13 13 : 1 1 1 0 0" in saved and "gemver_form 13 : 1 0 0 0 0" in saved
+        assert "sgemvt_form 12 13 : 2 0 0 0 0" in saved
         assert not any("foreign" in ln for ln in saved)
         g = tmp_path / "broken.txt"
         g.write_text(f"{dev[0]}\nmat no separator 8 2 2 0 4\n")
