@@ -253,6 +253,15 @@ class Suite:
 
 
 SEQS = ["bicgk", "gemver", "gesummv", "atax", "axpydot", "waxpby"]
+# the kernel the roofline names when a sequence is the first of a run
+DOMINANT_KERNEL = {
+    "bicgk": "matprog_kernel (BiCGK q=Ap, s=A^T r, one pass over A)",
+    "gemver": "GEMVER (single cooperative launch or two matrix passes, by first-use tuning)",
+    "gesummv": "matprog_kernel (GESUMMV y = alpha A x + beta B x, one pass over A and B)",
+    "atax": "atax_rows_kernel + atax_finish_kernel (y = A^T (A x), one read of A)",
+    "axpydot": "vecprog_kernel (AXPYDOT)",
+    "waxpby": "vecprog_kernel (WAXPBY)",
+}
 
 
 def cached_form(kf, key):
@@ -1342,7 +1351,7 @@ def main():
     achieved = dom_bytes / (per[dom] * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": committed_traffic() if (not args.small and args.bicgk == 0 and dom == "bicgk") else None,
-            "kernel": "matprog_kernel (BiCGK q=Ap, s=A^T r, one pass over A)",
+            "kernel": DOMINANT_KERNEL.get(dom, dom),
             "algorithmic_bytes_per_launch": dom_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else "fallback 6.8 TB/s"}
     if read_probe is not None and "gbs" in read_probe:

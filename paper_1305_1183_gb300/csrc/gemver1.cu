@@ -30,7 +30,8 @@ namespace {
 
 constexpr int G1_WARPS = 8;
 constexpr int G1_SW = G1_WARPS * 32 * 4;  // strip width: 1024 columns
-constexpr int G1_U = 4;                   // rows loaded together
+constexpr int G1_U_GER = 4;               // rows loaded together: GEMVER (B also written)
+constexpr int G1_U_MV = 8;                // SGEMVT (reads only: more rows in flight)
 constexpr int G1_SET = 8;                 // group partials per first-level sum
 
 struct GemverArgs {
@@ -112,6 +113,7 @@ __device__ __forceinline__ float g1_reduce8(float (&d)[8], int lane) {
 // priority so that the rows it read last are still in L2).
 template <bool GER>
 __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const __grid_constant__ GemverArgs a) {
+  constexpr int G1_U = GER ? G1_U_GER : G1_U_MV;
   __shared__ float red[G1_WARPS][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int strip = (int)(blockIdx.x % a.strips), group = (int)(blockIdx.x / a.strips);
