@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["abi.cu", "matprog.cu", "matprog_f32s.cu", "matprog_f32p.cu", "matprog_f32e.cu", "matprog_f32sig.cu",
            "matprog_bf16.cu", "matprog_e4m3.cu",
            "vecprog.cu", "atax.cu", "quant.cu", "noalloc.cu", "diag.cu", "gemver1.cu", "planner.cu", "plan_abi.cu", "batched.cu", "mlp.cu"]
-HEADERS = ["kf_internal.h", "kf_device.cuh", "matprog_impl.cuh", "planner.h"]
+HEADERS = ["kf_internal.h", "kf_device.cuh", "matprog_impl.cuh", "planner.h", "grid_sync.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + [

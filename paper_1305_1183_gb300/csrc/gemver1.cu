@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <string>
 
+#include "grid_sync.cuh"
 #include "kf_device.cuh"
 #include "kf_internal.h"
 
@@ -50,38 +51,9 @@ struct GemverArgs {
   uint64_t wait_ns;
 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid-wide barrier number k (1, 2, ...): every block adds one arrival, then
-// waits (bounded) until k * gridDim.x arrivals are in.  Returns false if the
-// wait ran out.
-__device__ bool grid_barrier(const GemverArgs& a, unsigned k) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(&a.bar[0], 1u);
-    const unsigned target = k * gridDim.x;
-    int ok = 1;
-    if (ld_acquire_u32(&a.bar[0]) < target) {
-      const uint64_t t0 = global_ns();
-      while (ld_acquire_u32(&a.bar[0]) < target) {
-        if (global_ns() - t0 > a.wait_ns) {
-          ok = 0;
-          atomicOr(a.err, KF_DEVERR_TIMEOUT);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
+// Grid-wide barrier number k (1, 2, ...) on the workspace's counters.
+__device__ __forceinline__ bool grid_barrier(const GemverArgs& a, unsigned k) {
+  return grid_barrier_bounded(a.bar, k, a.wait_ns, a.err);
 }
 
 __device__ __forceinline__ float4 ld_cg4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
@@ -279,15 +251,7 @@ __global__ void __launch_bounds__(G1_WARPS * 32, 3) gemver_single_kernel(const _
   }
 
   // the last block out leaves the barrier counters at zero for the next launch
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&a.bar[1], 1u) == gridDim.x - 1u) {
-      a.bar[0] = 0u;
-      a.bar[1] = 0u;
-      __threadfence();
-    }
-  }
+  grid_exit(a.bar);
 }
 
 }  // namespace

@@ -159,3 +159,52 @@ def test_tune_on_first_use_atax(built, tmp_path):
     finally:
         kf.kf_set_autotune(0)
         kf.kf_tune_cache_clear()
+
+
+def _force_atax_form(kf, tmp_path, m, n, vec, rp):
+    """Put one ATAX tuning for the size class of (m, n) into the cache: vec
+    1 = cluster reduction, 2 = per-block partials for the finishing kernel."""
+    kf.kf_tune_cache_clear()
+    base = tmp_path / "dev.txt"
+    kf.kf_tune_cache_save(base)
+    dev_line = [ln for ln in open(base) if ln.startswith("device ")][0]
+    f = tmp_path / "atax.txt"
+    f.write_text(dev_line + f"atax {m.bit_length() - 1} {n.bit_length() - 1} : 1 {vec} {rp} 0 0\n")
+    assert kf.kf_tune_cache_load(f) == 1
+
+
+@pytest.mark.parametrize("vec", [1, 2])
+@pytest.mark.parametrize("rp", [1, 2])
+def test_atax_every_form(built, tmp_path, vec, rp):
+    """Each way of adding ATAX's column partials (clusters first, or every
+    block's partial to the finishing kernel) and rows per barrier, fixed
+    through the tuning cache: kf_atax matches the oracle twice in a row on
+    one workspace, and a planner pair with scale 1.5 * -0.5 matches too."""
+    kf = built
+    try:
+        for m, n in [(3000, 4096), (5, 16384), (2000, 1028), (9, 8), (1031, 8192)]:
+            _force_atax_form(kf, tmp_path, m, n, vec, rp)
+            A = synth.uniform((m, n), m, 1, device=dev())
+            x = synth.uniform((n,), m, 3, device=dev())
+            W = kf.workspace(kf.KF_SEQ_ATAX, m, n)
+            Ah, xh = host(A), host(x)
+            yo, _ = oracle.atax(Ah, xh)
+            sy = oracle.abs_gemvt(Ah, oracle.abs_gemv(Ah, xh))
+            for call in range(2):
+                y = torch.full((n,), float("nan"), device=dev())
+                kf.kf_atax(A, x, y, W)
+                check_reduce(host(y), yo, sy, max(m, n), f"atax form {vec}/{rp}, call {call}")
+            kf.kf_workspace_status(W)
+            s = kf.Script()
+            s.matrix("A", m, n); s.vector("x", n); s.vector("t", m); s.vector("y", n)
+            s.input("A", "x"); s.output("y")
+            s.call("GEMV", ["t"], ["A", "x"], [1.5, 0.0])
+            s.call("GEMVT", ["y"], ["A", "t"], [-0.5, 0.0])
+            p = s.plan(kf.KF_PLAN_ANALYTIC)
+            assert [k["kind"] for k in p.describe()["kernels"]] == ["atax"]
+            ws = torch.zeros(max(p.workspace_size(), 256), dtype=torch.uint8, device=dev())
+            bind = {"A": A, "x": x, "t": torch.empty(m, device=dev()), "y": torch.empty(n, device=dev())}
+            p.execute(bind, ws)
+            check_reduce(host(bind["y"]), -0.75 * yo, 0.75 * sy, max(m, n), f"planner atax form {vec}/{rp}")
+    finally:
+        kf.kf_tune_cache_clear()
