@@ -129,6 +129,7 @@ struct VecTune {
 
 // Status codes mirror kf.h.
 int launch_matprog(MatProg& P, const MatTune& t, void* stream, const char** why);
+bool matprog_sig_compiled(const int* kinds, const int* mats, int nops, int fmt);
 // The tuning an automatic launch would take without running a search: the
 // fixed tuning when its warps field is set, else the tuning cache's entry for
 // P's op signature and size class, else the built-in tuning.

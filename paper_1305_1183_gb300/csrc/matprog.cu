@@ -169,6 +169,22 @@ int matprog_bind_workspace(MatProg& P, void* ws, size_t bytes) {
 
 // Op signature (0 when the GEMV results are not numbered in op order) and
 // the compiled op shape a fusion maps to.
+// Is a specialised instance compiled for this op sequence (kinds and matrix
+// slots in kernel order, at most four ops) in format `fmt`?  Host only: the
+// planner's call-order search asks it for each legal order of a fusion.
+bool matprog_sig_compiled(const int* kinds, const int* mats, int nops, int fmt) {
+  if (nops < 1 || nops > 4) return false;
+  int sig = mp::SIG_SPEC;
+  for (int k = 0; k < nops; ++k) {
+    if (mats[k] < 0 || mats[k] > 1) return false;
+    sig |= mp::sig_op(kinds[k], mats[k]) << (3 * k);
+  }
+  ensure_registry();
+  for (const auto& kv : mp::registry())
+    if (kv.second.sig == sig && kv.second.fmt == fmt && kv.second.vec) return true;
+  return false;
+}
+
 void op_shape(const MatProg& P, int* sig, int* shape_nops, int* shape_ng, int* ngemv_out) {
   int ngemv = 0;
   for (int k = 0; k < P.nops; ++k) ngemv += P.ops[k].kind == MOP_GEMV;

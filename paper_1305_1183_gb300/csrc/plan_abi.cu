@@ -407,7 +407,13 @@ kf_status kf_plan_describe(const kf_plan* p, char* buf, size_t cap, size_t* need
     const Kernel& K = p->p.kernels[i];
     o << (i ? "," : "") << "{\"kind\":\"" << (K.is_atax ? "atax" : K.is_mat ? "matrix" : "vector") << "\",\"calls\":[";
     for (size_t j = 0; j < K.calls.size(); ++j) o << (j ? "," : "") << K.calls[j];
-    o << "],\"bytes\":" << K.bytes << ",\"m\":" << K.m << ",\"n\":" << K.n << ",\"bind\":[";
+    o << "]";
+    if (K.is_mat) {
+      o << ",\"order\":[";
+      for (size_t j = 0; j < K.order.size(); ++j) o << (j ? "," : "") << K.order[j];
+      o << "],\"specialised\":" << (K.specialised ? "true" : "false");
+    }
+    o << ",\"bytes\":" << K.bytes << ",\"m\":" << K.m << ",\"n\":" << K.n << ",\"bind\":[";
     for (size_t j = 0; j < K.bind.size(); ++j)
       o << (j ? "," : "") << "[\"" << field_name(K, (size_t)(uintptr_t)K.bind[j].first) << "\"," << K.bind[j].second << "]";
     o << "]}";

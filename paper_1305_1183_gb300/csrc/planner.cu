@@ -513,6 +513,80 @@ static std::string build_vec_kernel(const Script& s, const std::vector<int>& g, 
   return "";
 }
 
+// Call-order search (Section 3.2, fusion variant (i): the order of the
+// calls inside a fusion).  Two matrix calls of a fusion keep their script
+// order when one writes a variable the other reads or writes; a GER
+// rewrites the row values in place, so the calls reading the version it
+// replaces go first even though the script's versions do not depend on
+// each other.  Any other pair may swap, and every order that keeps these
+// pairs computes the same bits for every result (each result is its own
+// sum in its own fixed order).  The order decides the op signature, and
+// with it whether a specialised kernel instance exists: the search takes
+// the script order if it has one, else the first legal permutation in
+// lexicographic order that has one, else the script order.  The linear
+// epilogue maps, which only read the matrix calls' results, follow the
+// matrix calls in script order.
+static std::vector<int> search_call_order(const Script& s, const std::vector<int>& g, bool* specialised) {
+  std::vector<int> M, E;
+  for (int c : g) (s.calls[c].depth == 2 ? M : E).push_back(c);
+  auto touches = [&](int c, int v) {
+    const Call& k = s.calls[c];
+    if (k.outs[0] == v) return true;
+    for (int i : k.ins)
+      if (i == v) return true;
+    return false;
+  };
+  auto conflict = [&](int a, int b) { return touches(b, s.calls[a].outs[0]) || touches(a, s.calls[b].outs[0]); };
+  // kinds and matrix slots of an order, slots by first appearance of each
+  // matrix lineage (a GER's output continues its input's lineage)
+  auto compiled = [&](const std::vector<int>& order) {
+    std::vector<std::pair<int, int>> lin;
+    int kinds[8], mats[8], nops = 0;
+    for (int c : order) {
+      const Call& k = s.calls[c];
+      const std::pair<int, int> av{k.ins[0], k.in_ver[0]};
+      int li = -1;
+      for (size_t q = 0; q < lin.size(); ++q)
+        if (lin[q] == av) li = (int)q;
+      if (li < 0) {
+        lin.push_back(av);
+        li = (int)lin.size() - 1;
+      }
+      if (nops >= 8) return false;
+      kinds[nops] = k.op == OP_GER ? MOP_GER : (k.op == OP_GEMV ? MOP_GEMV : MOP_GEMVT);
+      mats[nops] = li;
+      ++nops;
+      if (k.op == OP_GER) lin[li] = {k.outs[0], k.out_ver};
+    }
+    return matprog_sig_compiled(kinds, mats, nops, FMT_F32);
+  };
+  *specialised = compiled(M);
+  std::vector<int> out = g;
+  if (*specialised || M.size() < 2 || M.size() > 6) return out;
+  // an epilogue result read by a matrix call pins the script order
+  for (int e : E)
+    for (int c : M)
+      if (touches(c, s.calls[e].outs[0])) return out;
+  std::vector<int> perm(M.size());
+  for (size_t i = 0; i < perm.size(); ++i) perm[i] = (int)i;
+  while (std::next_permutation(perm.begin(), perm.end())) {
+    bool legal = true;
+    for (size_t i = 0; i < perm.size() && legal; ++i)
+      for (size_t j = i + 1; j < perm.size() && legal; ++j)
+        if (perm[i] > perm[j] && conflict(M[perm[i]], M[perm[j]])) legal = false;
+    if (!legal) continue;
+    std::vector<int> order;
+    for (int i : perm) order.push_back(M[i]);
+    if (compiled(order)) {
+      *specialised = true;
+      out = order;
+      out.insert(out.end(), E.begin(), E.end());
+      return out;
+    }
+  }
+  return out;
+}
+
 static std::string build_mat_kernel(const Script& s, const std::vector<int>& g, Kernel* K) {
   MatProg& P = K->mp;
   std::memset(&P, 0, sizeof(P));
@@ -521,7 +595,11 @@ static std::string build_mat_kernel(const Script& s, const std::vector<int>& g, 
   std::map<Val, Expr> vexpr;         // row/col values produced in g
   std::map<Val, int> side;           // 0 row 1 col
   std::set<int> ext_vectors;         // distinct external vectors read (bytes)
-  for (int c : g) {
+  bool specialised = false;
+  const std::vector<int> order = search_call_order(s, g, &specialised);
+  K->order = order;
+  K->specialised = specialised;
+  for (int c : order) {
     const Call& k = s.calls[c];
     if (k.depth == 2) {
       const int A = k.ins[0];
@@ -604,7 +682,7 @@ static std::string build_mat_kernel(const Script& s, const std::vector<int>& g, 
   }
   // epilogue outputs
   double vec_bytes = 0.0;
-  for (int c : g) {
+  for (int c : order) {
     const Call& k = s.calls[c];
     if (k.op == OP_GER) continue;
     const Val out{k.outs[0], k.out_ver};

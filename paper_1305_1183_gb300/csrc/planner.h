@@ -64,6 +64,8 @@ struct Script {
 // Kernel produced for one fusion.
 struct Kernel {
   std::vector<int> calls;  // in script order
+  std::vector<int> order;  // matrix pass: the calls in kernel order (call-order search)
+  bool specialised = false;  // matrix pass: a specialised instance exists for that order
   int depth = 1;
   bool is_mat = false;
   // Single-pass ATAX, y = atax_scale * A^T (A x): bind holds A, x, y in that

@@ -18,9 +18,11 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
-from gpu_util import built, dev  # noqa: F401
+from gpu_util import built, dev, host  # noqa: F401
 from oracle import script as oscript
+from tolerance import check_reduce
 from synth import scripts as sscripts
 from test_planner_cpu import atax, axpydot, bicgk, gemver, gesummv, waxpby
 
@@ -188,3 +190,33 @@ def test_planner_single_pass_atax(built, m, n):
     assert [k["kind"] for k in s.plan(kf.KF_PLAN_ANALYTIC).describe()["kernels"]] == ["atax"]
     assert run_plans(kf, sd, integer=False) == 2
     assert run_plans(kf, sd, integer=True) == 2
+
+
+@pytest.mark.parametrize("m,n", [(3000, 2048), (1000, 1003)])
+def test_call_order_search_runs_the_specialised_kernel(built, m, n):
+    """BiCGK written with s = A^T r before q = A p: the call-order search
+    runs the two calls in the specialised BiCGK order, so the plan computes
+    exactly kf_bicgk's bits, and both match the oracle."""
+    kf = built
+    s = kf.Script()
+    s.matrix("A", m, n); s.vector("p", n); s.vector("r", m); s.vector("q", m); s.vector("s", n)
+    s.input("A", "p", "r"); s.output("q", "s")
+    s.call("GEMVT", ["s"], ["A", "r"], [1.0, 0.0])
+    s.call("GEMV", ["q"], ["A", "p"], [1.0, 0.0])
+    p = s.plan(kf.KF_PLAN_ANALYTIC)
+    (k,) = p.describe()["kernels"]
+    assert k["order"] == [1, 0] and k["specialised"] is True
+    A = synth.uniform((m, n), 7, synth.TID["A"], device=dev())
+    pv = synth.uniform((n,), 7, synth.TID["p"], device=dev())
+    rv = synth.uniform((m,), 7, synth.TID["r"], device=dev())
+    bind = {"A": A, "p": pv, "r": rv, "q": torch.empty(m, device=dev()), "s": torch.empty(n, device=dev())}
+    ws = torch.zeros(max(p.workspace_size(), 256), dtype=torch.uint8, device=dev())
+    p.execute(bind, ws)
+    q = torch.empty(m, device=dev()); sv = torch.empty(n, device=dev())
+    kf.kf_bicgk(A, pv, rv, q, sv, kf.workspace(kf.KF_SEQ_BICGK, m, n))
+    torch.cuda.synchronize()
+    assert torch.equal(bind["q"], q) and torch.equal(bind["s"], sv)
+    Ah, ph, rh = host(A), host(pv), host(rv)
+    qo, so = oracle.bicgk(Ah, ph, rh)
+    check_reduce(host(q), qo, oracle.abs_gemv(Ah, ph), n, "q")
+    check_reduce(host(sv), so, oracle.abs_gemvt(Ah, rh), m, "s")

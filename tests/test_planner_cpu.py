@@ -454,3 +454,92 @@ def test_random_scripts_every_plan_is_well_formed(kf):
             assert p.predicted_us() > 0 and p.workspace_size() >= 0 and len(p.features()) == 16
             nplans += 1
     assert nplans > 1000
+
+
+# ------------------------------------------------------------ call-order search (Section 3.2, variant (i))
+
+def bicgk_reversed(kf, m=64, n=48):
+    """BiCGK with its two calls in the other order: s = A^T r first."""
+    s = kf.Script()
+    s.matrix("A", m, n); s.vector("p", n); s.vector("r", m); s.vector("q", m); s.vector("s", n)
+    s.input("A", "p", "r"); s.output("q", "s")
+    s.call("GEMVT", ["s"], ["A", "r"], [1.0, 0.0])
+    s.call("GEMV", ["q"], ["A", "p"], [1.0, 0.0])
+    return s
+
+
+def _matrix_kernels(d):
+    return [k for k in d["kernels"] if k["kind"] == "matrix"]
+
+
+def test_call_order_keeps_a_specialised_script_order(kf):
+    """The canonical scripts already list their calls in the order of a
+    specialised instance: the search keeps script order."""
+    for builder, n_calls in ((bicgk, 2), (gesummv, 3)):
+        (k,) = _matrix_kernels(builder(kf).plan(kf.KF_PLAN_ANALYTIC).describe())
+        assert k["specialised"] is True
+        assert k["order"] == sorted(k["order"]) and len(k["order"]) == n_calls
+    ks = _matrix_kernels(gemver(kf).plan(kf.KF_PLAN_ANALYTIC).describe())
+    assert [k["specialised"] for k in ks] == [True, True]
+    assert ks[0]["order"] == [0, 1, 2, 3] and ks[1]["order"] == [4]
+
+
+def test_call_order_search_reorders_independent_calls(kf):
+    """s = A^T r listed before q = A p: no variable is written by one call
+    and used by the other, so they may swap; the swapped order is the
+    specialised BiCGK signature, which the search picks."""
+    (k,) = _matrix_kernels(bicgk_reversed(kf).plan(kf.KF_PLAN_ANALYTIC).describe())
+    assert k["calls"] == [0, 1]
+    assert k["order"] == [1, 0]
+    assert k["specialised"] is True
+
+
+def test_call_order_search_keeps_ger_fences(kf):
+    """A GEMV of A listed before the GER that rewrites A (in place in the
+    kernel's rows) and a GEMVT of the new version after it: every pair
+    shares A with one writer, so only script order is legal, and no
+    instance is specialised for it."""
+    n = 40
+    s = kf.Script()
+    s.matrix("A", n, n)
+    for v in ("u", "v", "x", "r", "q", "t"):
+        s.vector(v, n)
+    s.input("A", "u", "v", "x", "r"); s.output("A", "q", "t")
+    s.call("GEMV", ["q"], ["A", "x"], [1.0, 0.0])
+    s.call("GER", ["A"], ["A", "u", "v"], [1.0])
+    s.call("GEMVT", ["t"], ["A", "r"], [1.0, 0.0])
+    fused = 0
+    for i in range(s.count_plans()[0]):
+        for k in _matrix_kernels(s.plan(kf.KF_PLAN_INDEX, index=i).describe()):
+            fused += len(k["order"]) > 1
+            pos = {c: j for j, c in enumerate(k["order"])}
+            for a, b in ((0, 1), (1, 2), (0, 2)):
+                if a in pos and b in pos:
+                    assert pos[a] < pos[b], (i, k)
+    assert fused > 0  # some plan fuses the GER with a reader
+
+
+def test_call_order_search_never_crosses_a_fence_for_a_specialised_order(kf):
+    """t = A^T y on the old A, then two GERs rewriting A.  The kinds of
+    (GER, GER, GEMVT) are those of the specialised GEMVER pass 1, but there
+    the GEMVT reads the rewritten rows; here it reads the old version, which
+    after the GERs would be a second matrix (another signature), so no
+    reordering matches an instance: the search keeps script order and
+    reports none.  (The conflict rule also forbids the move: the GERs write
+    the variable the GEMVT reads.)"""
+    n = 40
+    s = kf.Script()
+    s.matrix("A", n, n)
+    for v in ("u1", "v1", "u2", "v2", "y", "t"):
+        s.vector(v, n)
+    s.input("A", "u1", "v1", "u2", "v2", "y"); s.output("A", "t")
+    s.call("GEMVT", ["t"], ["A", "y"], [1.0, 0.0])
+    s.call("GER", ["A"], ["A", "u1", "v1"], [1.0])
+    s.call("GER", ["A"], ["A", "u2", "v2"], [1.0])
+    seen = 0
+    for i in range(s.count_plans()[0]):
+        for k in _matrix_kernels(s.plan(kf.KF_PLAN_INDEX, index=i).describe()):
+            if k["order"] == [0, 1, 2] or sorted(k["order"]) == [0, 1, 2]:
+                assert k["order"] == [0, 1, 2] and k["specialised"] is False, (i, k)
+                seen += 1
+    assert seen > 0  # some plan fuses all three
