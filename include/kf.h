@@ -389,7 +389,14 @@ kf_status kf_plan_features(const kf_script* s, const kf_plan* p, float* out, int
  * output may be NULL). */
 kf_status kf_plan_enumerate_info(const kf_script* s, int cap, float* feats, double* pred_us, int* kernels,
                                  int* count);
-/* JSON: kernels, their calls and bytes, prediction. */
+/* JSON: kernels, their calls (script order) and bytes, prediction.  A matrix
+ * kernel also gives "order", its calls in the order the kernel runs them,
+ * and "specialised", whether a specialised instance exists for that order.
+ * The planner's call-order search (Section 3.2, variant (i)) picks the order:
+ * the first legal one, script order first, whose op signature has a
+ * compiled specialised instance.  Calls that share a variable, one of them
+ * writing it, keep script order (a GER writes the matrix it updates), so
+ * every admissible order gives the same results bit for bit. */
 kf_status kf_plan_describe(const kf_plan* p, char* buf, size_t cap, size_t* needed);
 /* Enqueue the plan's kernels on `stream`.  bindings[var_id] is the device
  * address of each script variable (one device float for a scalar); ws holds
