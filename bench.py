@@ -1205,7 +1205,7 @@ def main():
                          "run with the tunings of an earlier one, without the search's own launches)")
     ap.add_argument("--learned-scripts", type=int, default=80,
                     help="random scripts of the learned-planner run (3/4 train, 1/4 held out; 0: skip)")
-    ap.add_argument("--only", default="", choices=["", "batched", "precision"],
+    ap.add_argument("--only", default="", choices=["", "batched", "precision", "table1"],
                     help="run only this section and print its JSON (profiling)")
     ap.add_argument("--batched-count", type=int, default=4096, help="instances per batched launch")
     ap.add_argument("--precision-n", type=int, default=16384,
@@ -1249,10 +1249,16 @@ def main():
     if args.only:
         d = torch.device("cuda", local)
         st = torch.cuda.Stream()
-        sec = (batched_section(kf, d, st, args.steps, args.warmup, count=args.batched_count)
-               if args.only == "batched" else precision_section(kf, d, st, args.steps, args.warmup, n=args.precision_n))
+        if args.only == "batched":
+            sec = batched_section(kf, d, st, args.steps, args.warmup, count=args.batched_count)
+        elif args.only == "table1":
+            sec = table1_section(kf, d, st, args.steps, args.warmup)
+        else:
+            sec = precision_section(kf, d, st, args.steps, args.warmup, n=args.precision_n)
         if rank == 0:
             print(json.dumps({args.only: sec}), flush=True)
+            if args.tune_cache:
+                kf.kf_tune_cache_save(args.tune_cache)
         return
     suite = Suite(kf, sizes, torch.device("cuda", local), seqs=seqs)
     st = torch.cuda.Stream()
