@@ -361,6 +361,12 @@ kf_status kf_script_create(kf_script** out);
 void kf_script_destroy(kf_script* s);
 kf_status kf_script_vector(kf_script* s, const char* name, int64_t n, int* var_id);
 kf_status kf_script_matrix(kf_script* s, const char* name, int64_t m, int64_t n, int* var_id);
+/* A matrix whose rows are ld elements apart (ld >= n, else KF_ERR_SHAPE):
+ * an m x n view of a wider row-major FP32 array, bound to the pointer of its
+ * first element.  kf_script_matrix is the case ld = n.  Every kernel the
+ * planner emits takes the stride (matrix passes, single-pass ATAX); rows not
+ * 16 bytes apart take the element-wise load path. */
+kf_status kf_script_matrix_ld(kf_script* s, const char* name, int64_t m, int64_t n, int64_t ld, int* var_id);
 kf_status kf_script_scalar(kf_script* s, const char* name, int* var_id);
 kf_status kf_script_input(kf_script* s, int var_id);
 kf_status kf_script_output(kf_script* s, int var_id);

@@ -56,6 +56,7 @@ kf_status add_var(kf_script* sc, const char* name, int kind, int64_t m, int64_t 
   v.kind = kind;
   v.m = m;
   v.n = n;
+  v.ld = n;
   sc->s.vars.push_back(v);
   sc->s.analysed = false;
   *id = (int)sc->s.vars.size() - 1;
@@ -96,7 +97,7 @@ kf_status launch_kernel(const Kernel& K, void* const* bindings, int nb, void* ws
     }
     char* wsm = ws ? static_cast<char*>(ws) + plan_vec_region() : nullptr;
     const size_t wsm_bytes = ws_bytes > plan_vec_region() ? ws_bytes - plan_vec_region() : 0;
-    return atax_run(K.m, K.n, static_cast<const float*>(p[0]), K.n, static_cast<const float*>(p[1]),
+    return atax_run(K.m, K.n, static_cast<const float*>(p[0]), K.lda, static_cast<const float*>(p[1]),
                     static_cast<float*>(p[2]), K.atax_scale, wsm, wsm_bytes, stream);
   }
   if (K.is_mat) {
@@ -266,6 +267,13 @@ kf_status kf_script_vector(kf_script* s, const char* name, int64_t n, int* id) {
 
 kf_status kf_script_matrix(kf_script* s, const char* name, int64_t m, int64_t n, int* id) {
   return add_var(s, name, VK_MATRIX, m, n, id);
+}
+
+kf_status kf_script_matrix_ld(kf_script* s, const char* name, int64_t m, int64_t n, int64_t ld, int* id) {
+  if (ld < n || ld < 1) return err(KF_ERR_SHAPE, "matrix row stride ld must be at least n (and at least 1)");
+  kf_status st = add_var(s, name, VK_MATRIX, m, n, id);
+  if (st == KF_OK) s->s.vars[*id].ld = ld;
+  return st;
 }
 
 kf_status kf_script_scalar(kf_script* s, const char* name, int* id) { return add_var(s, name, VK_SCALAR, 1, 1, id); }

@@ -614,7 +614,7 @@ static std::string build_mat_kernel(const Script& s, const std::vector<int>& g, 
         li = (int)lin.size() - 1;
         P.fmt = FMT_F32;
         K->bind.push_back({(void**)(uintptr_t)off(P, &P.A[li]), A});
-        P.lda[li] = s.vars[A].n;
+        P.lda[li] = s.vars[A].ld;
       }
       MatOp& op = P.ops[P.nops];
       op.mat = lin[li].slot;
@@ -676,7 +676,7 @@ static std::string build_mat_kernel(const Script& s, const std::vector<int>& g, 
     mat_bytes += 4.0 * (double)P.m * (double)P.n;
     if (produced_in(s, g, l.cur.var, l.cur.ver) && live_out(s, g, l.cur.var, l.cur.ver, nullptr)) {
       K->bind.push_back({(void**)(uintptr_t)off(P, &P.Bout[l.slot]), l.cur.var});
-      P.ldb[l.slot] = s.vars[l.cur.var].n;
+      P.ldb[l.slot] = s.vars[l.cur.var].ld;
       mat_bytes += 4.0 * (double)P.m * (double)P.n;
     }
   }
@@ -730,6 +730,7 @@ static std::string build_atax_kernel(const Script& s, const std::vector<int>& g0
   K->bind.push_back({(void**)(uintptr_t)2, b.outs[0]});
   K->m = s.vars[A].m;
   K->n = s.vars[A].n;
+  K->lda = s.vars[A].ld;
   K->bytes = 4.0 * (double)K->m * (double)K->n + 8.0 * (double)K->n;  // A once, x in, y out
   return "";
 }

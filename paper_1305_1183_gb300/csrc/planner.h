@@ -35,7 +35,8 @@ enum Op { OP_AXPBY = 0, OP_SCAL = 1, OP_DOT = 2, OP_VADD = 3, OP_GEMV = 4, OP_GE
 struct Var {
   std::string name;
   int kind;
-  int64_t m, n;  // vector: n; matrix: m x n (contiguous rows); scalar: 1
+  int64_t m, n;  // vector: n; matrix: m x n; scalar: 1
+  int64_t ld = 0;  // matrix: row stride in elements (>= n; n unless declared)
   bool input = false, output = false;
 };
 
@@ -78,6 +79,7 @@ struct Kernel {
   std::vector<std::pair<void**, int>> bind;  // filled per execution on a copy
   double bytes = 0.0;      // bytes moved (model)
   int64_t m = 0, n = 0;
+  int64_t lda = 0;         // single-pass ATAX: row stride of A
 };
 
 struct Plan {

@@ -100,6 +100,7 @@ _SIGS = {
     "kf_script_destroy": ([vp], None),
     "kf_script_vector": ([vp, ctypes.c_char_p, i64, ctypes.POINTER(ci)], ci),
     "kf_script_matrix": ([vp, ctypes.c_char_p, i64, i64, ctypes.POINTER(ci)], ci),
+    "kf_script_matrix_ld": ([vp, ctypes.c_char_p, i64, i64, i64, ctypes.POINTER(ci)], ci),
     "kf_script_scalar": ([vp, ctypes.c_char_p, ctypes.POINTER(ci)], ci),
     "kf_script_input": ([vp, ci], ci),
     "kf_script_output": ([vp, ci], ci),
@@ -490,6 +491,7 @@ class Script:
         self.ids = {}
         self.kinds = {}
         self.shapes = {}
+        self.lds = {}  # matrix row strides as declared
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -502,10 +504,16 @@ class Script:
         self.ids[name] = i.value; self.kinds[name] = "v"; self.shapes[name] = (n,)
         return i.value
 
-    def matrix(self, name, m, n):
+    def matrix(self, name, m, n, ld=None):
+        """An m x n FP32 matrix; ld: its row stride in elements (default n),
+        for a view of a wider array (bind the tensor of the view)."""
         i = ci(0)
-        _ck(lib().kf_script_matrix(self.h, name.encode(), m, n, ctypes.byref(i)))
+        if ld is None:
+            _ck(lib().kf_script_matrix(self.h, name.encode(), m, n, ctypes.byref(i)))
+        else:
+            _ck(lib().kf_script_matrix_ld(self.h, name.encode(), m, n, ld, ctypes.byref(i)))
         self.ids[name] = i.value; self.kinds[name] = "m"; self.shapes[name] = (m, n)
+        self.lds[name] = n if ld is None else ld
         return i.value
 
     def scalar(self, name):
@@ -633,6 +641,10 @@ class Plan:
         nv = len(self.script.ids)
         arr = (vp * nv)()
         for name, t in bindings.items():
+            ld = self.script.lds.get(name)
+            if ld is not None and isinstance(t, torch.Tensor) and t.dim() == 2 and t.shape[0] > 1:
+                if t.stride(1) != 1 or t.stride(0) != ld:
+                    raise ValueError(f"matrix {name}: strides {t.stride()} do not match the declared row stride {ld}")
             arr[self.script.ids[name]] = _p(t)
         return arr, nv
 

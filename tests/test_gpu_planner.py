@@ -220,3 +220,82 @@ def test_call_order_search_runs_the_specialised_kernel(built, m, n):
     qo, so = oracle.bicgk(Ah, ph, rh)
     check_reduce(host(q), qo, oracle.abs_gemv(Ah, ph), n, "q")
     check_reduce(host(sv), so, oracle.abs_gemvt(Ah, rh), m, "s")
+
+
+def _padded(m, n, ld, seed, tid, fill=12345.0):
+    """An m x n view with row stride ld of a sentinel-filled buffer."""
+    buf = torch.full((m * ld + 8,), fill, device=dev())
+    v = buf[:m * ld].view(m, ld)[:, :n]
+    v.copy_(synth.uniform((m, n), seed, tid, device=dev()))
+    return buf, v
+
+
+@pytest.mark.parametrize("ld_pad", [4, 5])
+def test_strided_matrices_in_plans(built, ld_pad):
+    """Scripts over views of wider arrays (kf_script_matrix_ld; rows 16-byte
+    aligned with a pad of 4 floats, not with 5): BiCGK computes kf_bicgk's
+    bits on the same view; GEMVER writes B inside its view only and matches
+    the oracle; the ATAX pair (single pass when aligned, two passes when not)
+    matches the oracle."""
+    kf = built
+    m, n = 1500, 1028
+    ld = n + ld_pad
+    # BiCGK
+    _, A = _padded(m, n, ld, 3, synth.TID["A"])
+    p = synth.uniform((n,), 3, synth.TID["p"], device=dev()); r = synth.uniform((m,), 3, synth.TID["r"], device=dev())
+    s = kf.Script()
+    s.matrix("A", m, n, ld=ld); s.vector("p", n); s.vector("r", m); s.vector("q", m); s.vector("s", n)
+    s.input("A", "p", "r"); s.output("q", "s")
+    s.call("GEMV", ["q"], ["A", "p"], [1.0, 0.0])
+    s.call("GEMVT", ["s"], ["A", "r"], [1.0, 0.0])
+    pl = s.plan(kf.KF_PLAN_ANALYTIC)
+    bind = {"A": A, "p": p, "r": r, "q": torch.empty(m, device=dev()), "s": torch.empty(n, device=dev())}
+    pl.execute(bind, torch.zeros(max(pl.workspace_size(), 256), dtype=torch.uint8, device=dev()))
+    q = torch.empty(m, device=dev()); sv = torch.empty(n, device=dev())
+    kf.kf_bicgk(A, p, r, q, sv, kf.workspace(kf.KF_SEQ_BICGK, m, n))
+    torch.cuda.synchronize()
+    assert torch.equal(bind["q"], q) and torch.equal(bind["s"], sv)
+    Ah = host(A)
+    check_reduce(host(q), oracle.gemv(Ah, host(p)), oracle.abs_gemv(Ah, host(p)), n, "q")
+    # GEMVER (square) with A and B both strided
+    nn = 1028
+    _, A2 = _padded(nn, nn, nn + ld_pad, 4, synth.TID["A"])
+    bufB, B2 = _padded(nn, nn, nn + ld_pad, 4, synth.TID["B"])
+    sc = kf.Script()
+    sc.matrix("A", nn, nn, ld=nn + ld_pad); sc.matrix("B", nn, nn, ld=nn + ld_pad)
+    for v in ("u1", "v1", "u2", "v2", "y", "z", "x", "w", "t"):
+        sc.vector(v, nn)
+    sc.input("A", "u1", "v1", "u2", "v2", "y", "z"); sc.output("B", "x", "w")
+    sc.call("GER", ["B"], ["A", "u1", "v1"], [1.0])
+    sc.call("GER", ["B"], ["B", "u2", "v2"], [1.0])
+    sc.call("GEMVT", ["t"], ["B", "y"], [1.0, 0.0])
+    sc.call("AXPBY", ["x"], ["t", "z"], [1.2, 1.0])
+    sc.call("GEMV", ["w"], ["B", "x"], [1.5, 0.0])
+    vs = {v: synth.uniform((nn,), 4, synth.TID[v], device=dev()) for v in ("u1", "v1", "u2", "v2", "y", "z")}
+    pg = sc.plan(kf.KF_PLAN_ANALYTIC)
+    bg = dict(vs, A=A2, B=B2, x=torch.empty(nn, device=dev()), w=torch.empty(nn, device=dev()),
+              t=torch.empty(nn, device=dev()))
+    pg.execute(bg, torch.zeros(max(pg.workspace_size(), 256), dtype=torch.uint8, device=dev()))
+    torch.cuda.synchronize()
+    Bo, xo, wo = oracle.gemver(host(A2), *[host(vs[k]) for k in ("u1", "v1", "u2", "v2", "y", "z")], 1.5, 1.2)
+    assert np.max(np.abs(host(B2) - Bo)) <= 4 * 2.0 ** -24 * 4.0 * (1 + np.max(np.abs(Bo)))
+    pad = bufB[:nn * (nn + ld_pad)].view(nn, nn + ld_pad)[:, nn:]
+    assert torch.all(pad == 12345.0) and torch.all(bufB[nn * (nn + ld_pad):] == 12345.0)
+    sx = 1.2 * oracle.abs_gemvt(Bo, host(vs["y"])) + np.abs(host(vs["z"]))
+    check_reduce(host(bg["x"]), xo, sx, nn, "x")
+    check_reduce(host(bg["w"]), wo, 1.5 * oracle.abs_gemv(Bo, np.abs(xo) + sx), nn, "w")
+    # ATAX pair on the strided A of the BiCGK case
+    sa = kf.Script()
+    sa.matrix("A", m, n, ld=ld); sa.vector("x", n); sa.vector("t", m); sa.vector("y", n)
+    sa.input("A", "x"); sa.output("y")
+    sa.call("GEMV", ["t"], ["A", "x"], [1.5, 0.0])
+    sa.call("GEMVT", ["y"], ["A", "t"], [-0.5, 0.0])
+    pa = sa.plan(kf.KF_PLAN_ANALYTIC)
+    ba = {"A": A, "x": p, "t": torch.empty(m, device=dev()), "y": torch.empty(n, device=dev())}
+    pa.execute(ba, torch.zeros(max(pa.workspace_size(), 256), dtype=torch.uint8, device=dev()))
+    yo, _ = oracle.atax(Ah, host(p))
+    check_reduce(host(ba["y"]), -0.75 * yo, 0.75 * oracle.abs_gemvt(Ah, oracle.abs_gemv(Ah, host(p))), max(m, n),
+                 "atax strided")
+    with pytest.raises(ValueError):
+        pa.execute(dict(ba, A=A.contiguous()), torch.zeros(max(pa.workspace_size(), 256), dtype=torch.uint8,
+                                                           device=dev()))

@@ -543,3 +543,26 @@ def test_call_order_search_never_crosses_a_fence_for_a_specialised_order(kf):
                 assert k["order"] == [0, 1, 2] and k["specialised"] is False, (i, k)
                 seen += 1
     assert seen > 0  # some plan fuses all three
+
+
+def test_strided_script_matrix(kf):
+    """kf_script_matrix_ld: a row stride below n is refused; a strided
+    matrix plans exactly like a packed one (the stride only changes the
+    kernels' addressing)."""
+    s = kf.Script()
+    with pytest.raises(kf.KFError) as e:
+        s.matrix("A", 8, 16, ld=15)
+    assert e.value.status == kf.KF_ERR_SHAPE
+
+    def build(ld):
+        s = kf.Script()
+        s.matrix("A", 64, 48, ld=ld); s.vector("p", 48); s.vector("r", 64); s.vector("q", 64); s.vector("s", 48)
+        s.input("A", "p", "r"); s.output("q", "s")
+        s.call("GEMV", ["q"], ["A", "p"], [1.0, 0.0])
+        s.call("GEMVT", ["s"], ["A", "r"], [1.0, 0.0])
+        return s.plan(kf.KF_PLAN_ANALYTIC).describe()
+
+    a, b = build(None), build(53)
+    assert [(k["kind"], k["calls"], k["order"]) for k in a["kernels"]] == \
+           [(k["kind"], k["calls"], k["order"]) for k in b["kernels"]]
+    assert a["bytes"] == b["bytes"]
