@@ -144,7 +144,12 @@ kf_status kf_bicgk(int64_t m, int64_t n, const void* A, int64_t lda, kf_dtype fm
 
 /* GEMVER (Table 1): B = A + u1 v1^T + u2 v2^T; x = beta B^T y + z;
  * w = alpha B x.  A, B: n x n (B written, ldb >= n); all vectors length n.
- * Two launches: the second needs all of x (a global barrier, Section 3.2.2). */
+ * w needs all of x (a global barrier, Section 3.2.2).  Two forms: two
+ * launches, the second rereading B from the rows the first wrote last; or
+ * kf_gemver_single's one cooperative launch.  kf_gemver takes the single
+ * launch where its tuning on first use measured it more than 2 % faster at
+ * that size class (tuning cache key "gemver_form log2(n)"), else two
+ * launches. */
 kf_status kf_gemver(int64_t n, const float* A, int64_t lda, const float* u1, const float* v1,
                     const float* u2, const float* v2, const float* y, const float* z, float alpha,
                     float beta, float* B, int64_t ldb, float* x, float* w, void* ws,
